@@ -1,0 +1,159 @@
+"""FP64 CPU oracle of the radar ray-tracing hot path (arXiv 2307.15412).
+
+TEST INFRASTRUCTURE ONLY: the tests, the package smoke check and the
+benchmark's CPU-baseline leg may use this package; the CUDA library never
+does.  It shares no code with the CUDA path.  The heavy loops (brute-force
+tracing, the direct IF sum, the direct DFTs) are plain C in ``rr_oracle.c``;
+this module compiles that file with gcc, loads it with ctypes and adds the
+numpy definitions of the LBVH's integer steps (``bvh.py``) and of the
+surrogate network (``mlp.py``).
+
+Parity status per function is listed in the header of each file; every
+function here is pinned by tests under ``tests/test_oracle_*.py``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+import threading
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "rr_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB = os.path.join(_BUILD, "librr_oracle.so")
+_lock = threading.Lock()
+_lib = None
+C_LIGHT = 299_792_458.0
+
+
+def build(force: bool = False) -> str:
+    """Compile rr_oracle.c with gcc (OpenMP, IEEE double, no FMA contraction)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if (not force and os.path.exists(_LIB)
+            and os.path.getmtime(_LIB) >= os.path.getmtime(_SRC)):
+        return _LIB
+    tmp = _LIB + ".tmp.%d" % os.getpid()
+    cmd = ["gcc", "-O2", "-std=gnu11", "-fPIC", "-shared", "-fopenmp",
+           "-ffp-contract=off", "-fno-fast-math", "-o", tmp, _SRC, "-lm"]
+    subprocess.run(cmd, check=True)
+    os.replace(tmp, _LIB)
+    return _LIB
+
+
+def _load():
+    global _lib
+    with _lock:
+        if _lib is None:
+            lib = ctypes.CDLL(build())
+            P = ctypes.c_void_p
+            I64 = ctypes.c_int64
+            I = ctypes.c_int
+            D = ctypes.c_double
+            lib.rro_ray_dirs.argtypes = [I, I, D, D, P, P, P]
+            lib.rro_trace.argtypes = [P, I64, P, I64, P, P, I64, P, P]
+            lib.rro_echo.argtypes = [I64, P, P, P, P, P, P, P, I, P, P, D, D, I, P, P, P]
+            lib.rro_synth.argtypes = [I64, I, P, P, P, D, D, D, D, I, I, P]
+            lib.rro_range_doppler.argtypes = [I, I, I, P, I, P]
+            lib.rro_num_threads.restype = I
+            _lib = lib
+    return _lib
+
+
+def _p(a: np.ndarray):
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def num_threads() -> int:
+    return int(_load().rro_num_threads())
+
+
+def ray_dirs(grid, frame=None):
+    """Unit ray directions [n_rays, 3] (world frame) and cell solid angles."""
+    lib = _load()
+    R = np.ascontiguousarray(np.eye(3) if frame is None else np.asarray(frame, np.float64).reshape(3, 3))
+    n = grid.n_az * grid.n_el
+    dirs = np.empty((n, 3), np.float64)
+    omega = np.empty(n, np.float64)
+    lib.rro_ray_dirs(grid.n_az, grid.n_el, float(grid.half_az), float(grid.half_el), _p(R), _p(dirs), _p(omega))
+    return dirs, omega
+
+
+def trace(V, F, origin, dirs):
+    """Brute-force closest hit: (tri int32 [n], t float64 [n]); miss = -1."""
+    lib = _load()
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    o = np.ascontiguousarray(origin, np.float64)
+    dirs = np.ascontiguousarray(dirs, np.float64)
+    n = dirs.shape[0]
+    tri = np.empty(n, np.int32)
+    t = np.empty(n, np.float64)
+    lib.rro_trace(_p(V), V.shape[0], _p(F), F.shape[0], _p(o), _p(dirs), n, _p(tri), _p(t))
+    return tri, t
+
+
+def echo(V, F, origin, dirs, t, tri, omega, radar, vel):
+    """Per-hit echo for each RX: d, a, ddot as float64 [n_rx][K]."""
+    lib = _load()
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    K = int(len(t))
+    n_rx = radar.n_rx
+    rx = np.ascontiguousarray(np.asarray(radar.rx, np.float64).reshape(n_rx, 3))
+    d = np.empty((n_rx, K), np.float64)
+    a = np.empty((n_rx, K), np.float64)
+    dd = np.empty((n_rx, K), np.float64)
+    lib.rro_echo(K, _p(np.ascontiguousarray(origin, np.float64)), _p(np.ascontiguousarray(dirs, np.float64)),
+                 _p(np.ascontiguousarray(t, np.float64)), _p(np.ascontiguousarray(tri, np.int32)),
+                 _p(np.ascontiguousarray(omega, np.float64)), _p(V), _p(F), n_rx, _p(rx),
+                 _p(np.ascontiguousarray(vel, np.float64)), float(radar.alpha), float(radar.spec_exp),
+                 int(radar.amp_mode), _p(d), _p(a), _p(dd))
+    return d, a, dd
+
+
+def synth(d, a, ddot, radar):
+    """Direct FP64 IF sum (Eq. 4, FMCW form): complex128 [n_rx][M][N]."""
+    lib = _load()
+    d = np.ascontiguousarray(d, np.float64)
+    a = np.ascontiguousarray(a, np.float64)
+    ddot = np.ascontiguousarray(ddot, np.float64)
+    n_rx, K = d.shape
+    out = np.empty((n_rx, radar.n_chirps, radar.n_samples, 2), np.float64)
+    lib.rro_synth(K, n_rx, _p(d), _p(a), _p(ddot), float(radar.f0), float(radar.slope), float(radar.dt),
+                  float(radar.t_rep), radar.n_chirps, radar.n_samples, _p(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def range_doppler(if_cube, window: int = 0):
+    """Direct 2-D DFT (+ kernel), Doppler fft-shifted: complex128 [n_rx][M][N]."""
+    lib = _load()
+    x = np.asarray(if_cube, np.complex128)
+    n_rx, M, N = x.shape
+    xi = np.ascontiguousarray(np.stack([x.real, x.imag], axis=-1))
+    out = np.empty((n_rx, M, N, 2), np.float64)
+    lib.rro_range_doppler(n_rx, M, N, _p(xi), int(window), _p(out))
+    return out[..., 0] + 1j * out[..., 1]
+
+
+def frame(scene_V, scene_F, vel, radar, grid, rays=None):
+    """Whole single-bounce frame: rays -> closest hits -> echo -> IF.
+
+    rays: optional subset of ray ids (the trace is per ray, so a subset gives
+    exactly those rays' results).  Returns a dict with per-ray tri/t, the hit
+    list in ray order and the IF cube of those hits."""
+    dirs, omega = ray_dirs(grid, radar.frame)
+    if rays is not None:
+        rays = np.asarray(rays, np.int64)
+        dirs, omega = dirs[rays], omega[rays]
+    else:
+        rays = np.arange(dirs.shape[0], dtype=np.int64)
+    origin = np.asarray(radar.tx, np.float64)
+    tri, t = trace(scene_V, scene_F, origin, dirs)
+    hit = tri >= 0
+    d, a, dd = echo(scene_V, scene_F, origin, dirs[hit], t[hit], tri[hit], omega[hit], radar,
+                    np.asarray(vel, np.float64))
+    return dict(ray_ids=rays, tri=tri, t=t, hit_rays=rays[hit], d=d, a=a, ddot=dd,
+                if_cube=synth(d, a, dd, radar))
