@@ -1,0 +1,336 @@
+"""Benchmark of the radar ray-tracing hot path on GB300.
+
+One step = one radar frame of the full-frame workload through the C ABI:
+build_bvh (LBVH of a ~22k-triangle hand), trace_frame (512 x 512 rays,
+echo for 3 receive antennas), synth_if (64 chirps x 256 samples, plain FP32
+path with the FP64 carrier reduction) and range_doppler.  Eight seeded
+scenes (pose, range U(0.2, 0.6) m, radial speed U(-1, 1) m/s) are resident
+in HBM and used in turn; L2 is flushed (256 MiB write) before every timed
+step.  Device time comes from CUDA events on the library's stream.
+
+  python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+Under torchrun every rank runs its own frames (weak scaling, no data
+exchange); rank 0 prints one JSON line.  --impl reference times the FP64
+CPU oracle on the host cores instead (rank 0 only).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "radar frames/s on 1 GB300 (trace+IF synth) vs plain FP32 path at rel-L2<=1e-3"
+WORKLOAD = ("full frame: seeded ~22k-triangle hand, range U(0.2,0.6) m, radial speed U(-1,1) m/s; "
+            "512x512 rays over +-45 deg; 1 TX 3 RX (L, lambda/2); 64 chirps x 256 samples, 60-64 GHz "
+            "in 64 us; LBVH build + trace + echo + FP32 IF synthesis + range-Doppler per frame")
+N_SCENES = 8
+FLUSH_BYTES = 256 << 20
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return json.load(f)
+    except Exception:
+        return {}
+
+
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons while running."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.t0 = self.t1 = None
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", "-i", str(self.index), "--query-gpu=" + self.Q,
+                                          "--format=csv,noheader,nounits", "-lms", "50"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if not self.proc:
+            return {"samples": 0, "note": "nvidia-smi unavailable"}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=5)
+        except Exception:
+            self.proc.kill()
+            out = ""
+        rows = [r.split(",") for r in out.strip().splitlines() if r.count(",") >= 8]
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for k, nm in enumerate(names):
+                if r[5 + k].strip().lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"samples": 0}
+        busy = [x for x in sm if x > 0.5 * max(sm)]
+        return {"sm_mhz": statistics.median(busy or sm), "sm_max_mhz": max(smax), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def make_scenes(rank: int):
+    from paper_2307_15412_gb300 import inputs as I
+    radar, grid, nt = I.workload_full_frame()
+    scenes = [I.hand_scene(1000 * rank + k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+              for k in range(N_SCENES)]
+    return radar, grid, scenes
+
+
+def cpu_oracle_frame_time(scene, radar, grid, frac: int):
+    """Times the FP64 oracle on every frac-th ray of the frame (trace, echo,
+    synthesis of those rays' hits) and scales to a whole frame; the
+    range-Doppler map of the frame's IF cube is timed in full."""
+    import oracle
+    dirs, omega = oracle.ray_dirs(grid, radar.frame)
+    sel = np.arange(0, grid.n_rays, frac)
+    t0 = time.perf_counter()
+    tri, t = oracle.trace(scene.V, scene.F, np.asarray(radar.tx, float), dirs[sel])
+    hit = tri >= 0
+    d, a, dd = oracle.echo(scene.V, scene.F, np.asarray(radar.tx, float), dirs[sel][hit], t[hit], tri[hit],
+                           omega[sel][hit], radar, scene.vel.astype(np.float64))
+    x = oracle.synth(d, a, dd, radar)
+    t1 = time.perf_counter()
+    oracle.range_doppler(x)
+    t2 = time.perf_counter()
+    return (t1 - t0) * frac + (t2 - t1), int(hit.sum()), len(sel)
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    import oracle
+    oracle.build()
+    radar, grid, scenes = make_scenes(0)
+    frac = 32
+    for i in range(args.warmup):
+        cpu_oracle_frame_time(scenes[i % N_SCENES], radar, grid, frac)
+    total = 0.0
+    wall0 = time.perf_counter()
+    for i in range(args.steps):
+        ft, _, _ = cpu_oracle_frame_time(scenes[i % N_SCENES], radar, grid, frac)
+        total += ft
+    wall = time.perf_counter() - wall0
+    value = args.steps / total
+    cores = oracle.num_threads()
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": WORKLOAD, "scenes": N_SCENES},
+            "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
+                             "sample": "every %d-th ray of each frame traced (brute force), echoed and synthesised "
+                                       "in FP64, scaled x%d; range-Doppler of the IF cube in full; %.1f s of "
+                                       "CPU wall time" % (frac, frac, wall)},
+            "e2e": {"value": value, "unit": "frames/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    ctx = rr.Context(local, stream)
+    radar, grid, scenes = make_scenes(rank)
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(k, s.V, s.F, s.vel)
+    n_rx, M, N = radar.n_rx, radar.n_chirps, radar.n_samples
+    if_out = torch.empty((n_rx, M, N, 2), dtype=torch.float32, device=dev)
+    rd_out = torch.empty_like(if_out)
+    flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+
+    # hit counts per scene (deterministic per scene) for the flop count
+    counts = []
+    for k in range(N_SCENES):
+        ctx.build_bvh(k)
+        box = ctx.trace_frame(k, radar, grid)
+        ctx.sync()
+        counts.append(box[0])
+
+    def step(k, ev=None):
+        ctx.build_bvh(k)
+        ctx.trace_frame(k, radar, grid, want_count=False)
+        if ev is not None:
+            ev[0].record(stream)
+        ctx.synth_if(k, radar, if_out)
+        if ev is not None:
+            ev[1].record(stream)
+        ctx.range_doppler(if_out, rd_out)
+
+    for i in range(max(args.warmup, 3)):
+        step(i % N_SCENES)
+    ctx.sync()
+    torch.cuda.synchronize()
+
+    K = args.steps
+    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
+    ev_syn = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    props = torch.cuda.get_device_properties(dev)
+    uuid = getattr(props, "uuid", None)
+    sampler = ClockSampler(("GPU-%s" % uuid) if uuid is not None else local)
+    sampler.start()
+    time.sleep(0.2)
+    if ws > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for i in range(K):
+        flush.zero_()
+        ev_s[i].record(stream)
+        step(i % N_SCENES, ev_syn[i])
+        ev_e[i].record(stream)
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - wall0
+    ctx.sync()
+    if ws > 1:
+        dist.barrier()
+    clocks = sampler.stop()
+    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(K)]
+    syn_ms = [ev_syn[i][0].elapsed_time(ev_syn[i][1]) for i in range(K)]
+    t_dev = sum(step_ms) / 1e3
+    if ws > 1:
+        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_dev = float(tt.item())
+    value = ws * K / t_dev
+
+    # dominant kernel: the IF synthesis (k_synth_fp32 + its split-K sum)
+    flops = sum(8.0 * counts[i % N_SCENES] * n_rx * M * N for i in range(K))
+    achieved = flops / (sum(syn_ms) / 1e3) / 1e12
+    peaks = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "synth_fp32_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            traffic = json.load(open(tfile)).get("bytes_per_launch")
+        except Exception:
+            traffic = None
+
+    # end to end through the public API: pinned host mesh -> device, upload,
+    # frame, range-Doppler cube back to pinned host memory, every step
+    pin = [(torch.from_numpy(s.V).pin_memory(), torch.from_numpy(s.F).pin_memory()) for s in scenes]
+    dV = [torch.empty(p[0].shape, dtype=torch.float32, device=dev) for p in pin]
+    dF = [torch.empty(p[1].shape, dtype=torch.int32, device=dev) for p in pin]
+    rd_host = torch.empty(rd_out.shape, dtype=torch.float32).pin_memory()
+    K_e2e = max(1, min(K, 400))
+
+    def e2e_step(k):
+        dV[k].copy_(pin[k][0], non_blocking=True)
+        dF[k].copy_(pin[k][1], non_blocking=True)
+        ctx.scene_upload(k, dV[k], dF[k], scenes[k].vel)
+        ctx.run_frame(k, radar, grid, rd_out=rd_out)
+        rd_host.copy_(rd_out, non_blocking=True)
+        torch.cuda.current_stream(dev).synchronize()
+
+    for i in range(3):
+        e2e_step(i % N_SCENES)
+    if ws > 1:
+        dist.barrier()
+    t0 = time.perf_counter()
+    for i in range(K_e2e):
+        e2e_step(i % N_SCENES)
+    t_e2e = time.perf_counter() - t0
+    if ws > 1:
+        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
+        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+        t_e2e = float(tt.item())
+    h2d = int(np.mean([s.V.nbytes + s.F.nbytes for s in scenes]))
+    d2h = rd_out.numel() * 4
+    ctx.sync()
+
+    cpu = None
+    if rank == 0 and ws == 1 and not args.no_cpu_baseline:
+        import oracle
+        oracle.build()
+        frac = 8
+        ft, kh, nr = cpu_oracle_frame_time(scenes[0], radar, grid, frac)
+        cpu = {"value": 1.0 / ft, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+               "sample": "scene 0: every %d-th ray (%d rays, %d hits) traced brute force against all "
+                         "triangles, echoed and synthesised in FP64, time x%d; range-Doppler of that IF cube "
+                         "by direct DFT in full" % (frac, nr, kh, frac)}
+
+    if rank == 0:
+        line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
+                "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
+                "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+                "config": {"workload": WORKLOAD, "scenes": N_SCENES, "synth": "fp32",
+                           "mean_hits_per_frame": float(np.mean(counts)),
+                           "l2": "flushed before every timed step (256 MiB write, outside the events)",
+                           "parallelism": "replicas (one frame stream per GPU)"},
+                "roofline": {"bound": "alu", "kernel": "k_synth_fp32 (+ split-K sum)", "achieved": achieved,
+                             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                             "peak_source": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
+                                            % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max)},
+                "cpu_baseline": cpu,
+                "e2e": {"value": ws * K_e2e / t_e2e, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": d2h, "steps": K_e2e},
+                "gpu_launches": 8 * K,
+                "clocks": clocks,
+                "wall_s_timed_region": wall}
+        print(json.dumps(line))
+    ctx.close()
+    if ws > 1:
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_gpu(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,198 @@
+/*
+ * rr.h -- C ABI of the GB300 radar ray-tracing hot path
+ * ("A Realistic Radar Ray Tracing Simulator for Hand Pose Imaging",
+ *  arXiv 2307.15412).
+ *
+ * The library traces rays from a radar into a triangle-mesh scene
+ * (Sec. III), turns every hit into a delayed, attenuated echo using the
+ * specular/diffuse material mixture of Sec. III-A (Eq. 1-3), synthesises the
+ * FMCW intermediate-frequency (IF) signal per receive antenna, chirp and
+ * sample as the coherent sum of Eq. 4, and forms range-Doppler maps.
+ *
+ * General rules
+ *  - Every call is asynchronous on the context's CUDA stream unless stated
+ *    otherwise.  Errors found on the host are returned at once; errors found
+ *    by a kernel (capacity overflow, traversal stack overflow, a bounded wait
+ *    that ran out) are latched in a device error word and returned by the
+ *    next rr_sync(), which also clears it.
+ *  - "device" pointers are CUDA global-memory pointers of the context's
+ *    device (e.g. torch tensors' data_ptr()); "host" pointers are ordinary
+ *    host memory.  Output buffers are allocated and owned by the caller.
+ *  - The context owns its intermediate buffers (scene copies, BVH, hit list,
+ *    split-K partial sums) and frees them in rr_destroy().
+ *  - No call throws, aborts or exits; every failure is a status code with a
+ *    message retrievable through rr_last_error().
+ *  - Complex data are interleaved (re, im) float32 pairs.
+ *  - Units are SI (metres, seconds, hertz, radians).
+ */
+#ifndef RR_H
+#define RR_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  RR_OK = 0,
+  RR_EINVAL = 1,     /* bad argument (null pointer, size out of range, ...) */
+  RR_ENOMEM = 2,     /* device allocation failed */
+  RR_ECUDA = 3,      /* CUDA runtime error (message in rr_last_error) */
+  RR_EOVERFLOW = 4,  /* hit list or traversal stack capacity exceeded */
+  RR_ETIMEOUT = 5,   /* a bounded device-side wait ran out */
+  RR_ENOTREADY = 6   /* call order violated (e.g. trace before build_bvh) */
+} rr_status;
+
+typedef struct rr_ctx rr_ctx;
+
+#define RR_MAX_RX 8
+#define RR_MAX_SCENES 4096
+
+/* Radar description.  Sample n of chirp m sees the instantaneous frequency
+ * f0 + S t_n, S = bandwidth / t_chirp, t_n = n t_chirp / n_samples, which is
+ * Eq. 4's CW term with f0 + n df replaced by the chirp's frequency (Sec.
+ * III-B).  The transmit antenna is the origin of every ray. */
+typedef struct {
+  double frame[9];          /* radar -> world rotation, row-major; identity = boresight +z */
+  double tx[3];             /* transmit antenna position (world) */
+  double rx[RR_MAX_RX][3];  /* receive antenna positions (world) */
+  int32_t n_rx;             /* 1..RR_MAX_RX */
+  int32_t n_samples;        /* N, samples per chirp */
+  int32_t n_chirps;         /* M, chirps per frame */
+  int32_t amp_mode;         /* 0: material-lobe amplitude; 1: unit amplitude per hit (Eq. 4) */
+  double f0;                /* start frequency */
+  double bandwidth;         /* sweep bandwidth B */
+  double t_chirp;           /* chirp duration */
+  double t_rep;             /* chirp repetition interval */
+  double alpha;             /* Eq. 3 mixture weight: 0 specular, 1 diffuse */
+  double spec_exp;          /* exponent of the specular lobe */
+} rr_radar;
+
+/* Uniform azimuth/elevation ray grid of the radar frame: ray (i_az, i_el)
+ * points at the cell centre az = -half_az + (i_az + 1/2) 2 half_az / n_az
+ * (el likewise), direction (cos el sin az, sin el, cos el cos az); ray id =
+ * i_el * n_az + i_az.  Each ray carries its cell's solid angle. */
+typedef struct {
+  int32_t n_az, n_el;
+  double half_az, half_el;
+} rr_raygrid;
+
+typedef enum {
+  RR_SYNTH_FP32 = 0,       /* direct FP32 sum on the CUDA cores */
+  RR_SYNTH_TC_BF16X3 = 1,  /* split-time complex GEMM, tcgen05, split-BF16x3 */
+  RR_SYNTH_TC_TF32 = 2     /* split-time complex GEMM, tcgen05, TF32 */
+} rr_synth_variant;
+
+/* ---- context ----------------------------------------------------------- */
+
+/* Creates a context on CUDA device `device`.  cuda_stream: a cudaStream_t
+ * to issue all work on (not owned), or NULL for a context-owned stream. */
+rr_status rr_create(rr_ctx **out, int device, void *cuda_stream);
+rr_status rr_destroy(rr_ctx *ctx);
+/* Replaces the stream used by later calls (not owned; NULL = own stream). */
+rr_status rr_set_stream(rr_ctx *ctx, void *cuda_stream);
+/* Waits for the stream, returns the first latched device error (and clears
+ * it), and completes pending host outputs such as n_hits_out. */
+rr_status rr_sync(rr_ctx *ctx);
+/* Message of the last failing call on this context (never NULL). */
+const char *rr_last_error(const rr_ctx *ctx);
+/* Version string of the library. */
+const char *rr_version(void);
+
+/* ---- scene (Sec. III: the object is a 3-D triangle mesh) --------------- */
+
+/* Copies the mesh of scene slot `scene` (0 <= scene < RR_MAX_SCENES) into
+ * context memory.  verts: float32 [nv][3] positions (m); tris: int32 [nt][3]
+ * vertex indices; both host pointers if ptr_is_device == 0, else device
+ * pointers of the context's device.  vel: host float[3], the rigid
+ * translation velocity of the scene (m/s), or NULL for a static scene.  The
+ * arrays may be reused by the caller once the call returns (host) or once
+ * the stream has passed this point (device).  nt == 0 is a valid empty
+ * scene.  Indices out of [0, nv) are not checked on the device. */
+rr_status rr_scene_upload(rr_ctx *ctx, int scene, const float *verts, int64_t nv,
+                          const int32_t *tris, int64_t nt, const float *vel, int ptr_is_device);
+
+/* Builds the linear BVH of a scene: triangle bounds, 30-bit Morton codes of
+ * the bounding-box centres, radix sort, binary radix tree (Karras 2012)
+ * with bottom-up bounding boxes.  Must follow every rr_scene_upload. */
+rr_status rr_build_bvh(rr_ctx *ctx, int scene);
+
+/* ---- tracing and echo (Sec. III-A, Eq. 1-3; Sec. III-B path lengths) ---- */
+
+/* Traces every ray of `grid` from radar->tx into the scene (nearest hit,
+ * two-sided faces, lowest triangle id on equal distance) and turns each hit
+ * into an echo per receive antenna j: path length d_j = t + |p - rx_j|,
+ * amplitude a_j (material lobe of Eq. 1-3, or 1 with amp_mode 1) and path
+ * rate d-dot_j = v . (u + u_j).  The hit list (order unspecified) stays in
+ * the context.  hit_capacity: maximum hits kept (<= 0: one per ray).
+ * n_hits_out: optional host pointer, written by the next rr_sync() with
+ * the true hit count; if it exceeds the capacity, rr_sync() returns
+ * RR_EOVERFLOW and only `capacity` hits were kept. */
+rr_status rr_trace_frame(rr_ctx *ctx, int scene, const rr_radar *radar, const rr_raygrid *grid,
+                         int64_t hit_capacity, int64_t *n_hits_out);
+
+/* Copies the scene's hit list into caller device buffers; entries past the
+ * hit count are unspecified.  ray, tri: int32 [capacity]; t: float32
+ * [capacity] (distance from the transmitter); d, amp, ddot: float32
+ * [n_rx][capacity] (row stride = capacity).  Any pointer may be NULL.
+ * capacity must not exceed the capacity of the last trace. */
+rr_status rr_get_hits(rr_ctx *ctx, int scene, int64_t capacity, int32_t *ray, int32_t *tri,
+                      float *t, float *d, float *amp, float *ddot);
+
+/* ---- IF synthesis (Eq. 4, FMCW form) ------------------------------------ */
+
+/* if_out[j][m][n] = sum_k a_kj exp(-j 2 pi (f0 + S t_n)(d_kj + ddot_kj m T_rep) / c)
+ * over the scene's current hit list.  if_out: device complex64
+ * [n_rx][n_chirps][n_samples].  The carrier phase f0 d / c of each hit is
+ * range-reduced in FP64; the rest runs in FP32 (variant RR_SYNTH_FP32) or
+ * on the tensor cores (TC variants).  n_samples must be a power of two in
+ * [16, 1024] and n_chirps in [1, 1024]. */
+rr_status rr_synth_if(rr_ctx *ctx, int scene, const rr_radar *radar, rr_synth_variant variant,
+                      float *if_out);
+
+/* Same synthesis from a caller-supplied hit list of K hits: d, amp, ddot
+ * device float32 [n_rx][K] (row stride K).  K == 0 gives zeros. */
+rr_status rr_synth_if_from_hits(rr_ctx *ctx, const rr_radar *radar, rr_synth_variant variant,
+                                int64_t K, const float *d, const float *amp, const float *ddot,
+                                float *if_out);
+
+/* ---- range-Doppler map --------------------------------------------------- */
+
+/* rd_out[j][q'][k] = sum_m sum_n w(m) w(n) if_in[j][m][n] exp(+j 2 pi (k n / N + q m / M)),
+ * q' = (q + M/2) mod M (Doppler axis fft-shifted).  A path d lands in range
+ * bin B d / c and a path rate d-dot in Doppler bin f0 d-dot T_rep M / c.
+ * window: 0 rectangular, 1 symmetric Hann.  if_in and rd_out: device
+ * complex64 [n_rx][n_chirps][n_samples]; must not overlap.  n_samples and
+ * n_chirps: powers of two, n_samples in [1, 1024], n_chirps in [1, 1024],
+ * n_samples * n_chirps <= 16384. */
+rr_status rr_range_doppler(rr_ctx *ctx, const float *if_in, int n_rx, int n_chirps, int n_samples,
+                           int window, float *rd_out);
+
+/* ---- whole frame --------------------------------------------------------- */
+
+/* One frame of the hot path on a scene already uploaded: build_bvh,
+ * trace_frame, synth_if and, if rd_out != NULL, range_doppler, enqueued in
+ * that order.  if_out may be NULL when rd_out is given (an internal buffer
+ * holds the IF cube then). */
+rr_status rr_run_frame(rr_ctx *ctx, int scene, const rr_radar *radar, const rr_raygrid *grid,
+                       rr_synth_variant variant, int window, float *if_out, float *rd_out);
+
+/* ---- inspection (tests) --------------------------------------------------- */
+
+/* Copies the scene's LBVH into caller device buffers: sorted Morton codes
+ * (uint32 [nt]), sorted triangle ids (int32 [nt]), per internal node
+ * (split position gamma in [0, nt-2]) the left and right child (int32
+ * [nt-1] each; >= 0 internal node, < 0 leaf ~position) and the child boxes
+ * (float32 [nt-1][12]: left lo.x, left hi.x, left lo.y, left hi.y, right
+ * lo.x, right hi.x, right lo.y, right hi.y, left lo.z, left hi.z, right
+ * lo.z, right hi.z).  root_out: host int32 written by the next rr_sync()
+ * (~0 for a single triangle).  Any pointer may be NULL. */
+rr_status rr_get_bvh(rr_ctx *ctx, int scene, uint32_t *codes, int32_t *ids, int32_t *left,
+                     int32_t *right, float *boxes, int32_t *root_out);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* RR_H */

@@ -1,0 +1,490 @@
+// capi.cu -- the rr_* C ABI: context, scene slots, buffer management and
+// argument checking around the kernels of bvh.cu, trace.cu, synth.cu, rd.cu.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdarg.h>
+#include <stdio.h>
+#include <string.h>
+
+#include <new>
+#include <vector>
+
+#include "rr.h"
+#include "rr_internal.cuh"
+
+using rr::SceneDev;
+
+struct rr_ctx {
+  int device = 0;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  std::vector<SceneDev *> scenes;
+  uint32_t *d_err = nullptr;       // device error word
+  uint32_t *h_err = nullptr;       // pinned mirror
+  // host outputs completed by rr_sync
+  struct Pending {
+    int64_t *n_hits_out;
+    int32_t *root_out;
+    int scene;
+    int64_t cap;
+  };
+  std::vector<Pending> pending;
+  uint32_t *h_counts = nullptr;    // pinned, one per scene
+  int32_t *h_roots = nullptr;      // pinned, one per scene
+  // synthesis scratch
+  float *partials = nullptr;
+  int64_t partials_cap = 0;        // floats
+  float *if_tmp = nullptr;         // internal IF cube for rr_run_frame(if_out = NULL)
+  int64_t if_tmp_cap = 0;          // floats
+  char msg[512] = "ok";
+};
+
+namespace {
+
+rr_status fail(rr_ctx *c, rr_status st, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+
+rr_status cuda_fail(rr_ctx *c, cudaError_t e, const char *where) {
+  if (e == cudaErrorMemoryAllocation) return fail(c, RR_ENOMEM, "%s: %s", where, cudaGetErrorString(e));
+  return fail(c, RR_ECUDA, "%s: %s", where, cudaGetErrorString(e));
+}
+
+#define RR_CUDA(c, call, where)                              \
+  do {                                                       \
+    cudaError_t e__ = (call);                                \
+    if (e__ != cudaSuccess) return cuda_fail((c), e__, where); \
+  } while (0)
+
+struct DeviceGuard {
+  int prev = -1;
+  explicit DeviceGuard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+template <typename T>
+cudaError_t grow(T *&p, int64_t &cap, int64_t want) {
+  if (want <= cap && p) return cudaSuccess;
+  if (p) cudaFree(p);
+  p = nullptr;
+  cap = 0;
+  const int64_t n = want < 1 ? 1 : want;
+  cudaError_t e = cudaMalloc((void **)&p, (size_t)n * sizeof(T));
+  if (e == cudaSuccess) cap = n;
+  return e;
+}
+
+void free_scene(SceneDev *s) {
+  if (!s) return;
+  void *ptrs[] = {s->V, s->F, s->cent, s->blockbounds, s->keys, s->keys_alt, s->ids, s->ids_alt,
+                  s->flags, s->nodes, s->tris, s->hdr, s->hit_count, s->hit_ray, s->hit_tri, s->hit_pos,
+                  s->hit_t, s->hit_d, s->hit_a, s->hit_dd};
+  for (void *p : ptrs)
+    if (p) cudaFree(p);
+  delete s;
+}
+
+bool check_radar(rr_ctx *c, const rr_radar *r, rr_status *st) {
+  if (!r) { *st = fail(c, RR_EINVAL, "radar is NULL"); return false; }
+  if (r->n_rx < 1 || r->n_rx > RR_MAX_RX) { *st = fail(c, RR_EINVAL, "n_rx=%d out of [1,%d]", r->n_rx, RR_MAX_RX); return false; }
+  if (r->n_samples < 1 || r->n_chirps < 1) { *st = fail(c, RR_EINVAL, "n_samples/n_chirps must be >= 1"); return false; }
+  if (!(r->t_chirp > 0) || !(r->f0 > 0) || !(r->t_rep >= 0) || !isfinite(r->bandwidth)) {
+    *st = fail(c, RR_EINVAL, "radar timing/frequency parameters invalid");
+    return false;
+  }
+  if (!(r->alpha >= 0 && r->alpha <= 1)) { *st = fail(c, RR_EINVAL, "alpha must be in [0,1]"); return false; }
+  return true;
+}
+
+rr::RadarDev to_dev(const rr_radar *r) {
+  rr::RadarDev d;
+  for (int i = 0; i < 9; ++i) { d.R[i] = r->frame[i]; d.Rf[i] = (float)r->frame[i]; }
+  for (int i = 0; i < 3; ++i) { d.tx[i] = r->tx[i]; d.txf[i] = (float)r->tx[i]; }
+  for (int j = 0; j < RR_MAX_RX; ++j)
+    for (int i = 0; i < 3; ++i) d.rx[j][i] = j < r->n_rx ? r->rx[j][i] : 0.0;
+  d.n_rx = r->n_rx;
+  d.N = r->n_samples;
+  d.M = r->n_chirps;
+  d.amp_mode = r->amp_mode;
+  d.f0 = r->f0;
+  d.slope = r->bandwidth / r->t_chirp;
+  d.dt = r->t_chirp / r->n_samples;
+  d.t_rep = r->t_rep;
+  d.alpha = (float)r->alpha;
+  d.spec_exp = (float)r->spec_exp;
+  return d;
+}
+
+rr::GridDev to_dev(const rr_raygrid *g) {
+  rr::GridDev d;
+  d.n_az = g->n_az;
+  d.n_el = g->n_el;
+  d.half_az = g->half_az;
+  d.half_el = g->half_el;
+  d.daz = 2.0 * g->half_az / g->n_az;
+  d.del = 2.0 * g->half_el / g->n_el;
+  d.az0_pi = (float)((-g->half_az + 0.5 * d.daz) / M_PI);
+  d.daz_pi = (float)(d.daz / M_PI);
+  d.el0_pi = (float)((-g->half_el + 0.5 * d.del) / M_PI);
+  d.del_pi = (float)(d.del / M_PI);
+  d.daz_f = (float)d.daz;
+  d.del_f = (float)d.del;
+  return d;
+}
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+rr_status get_scene(rr_ctx *c, int scene, SceneDev **out) {
+  if (scene < 0 || scene >= RR_MAX_SCENES) return fail(c, RR_EINVAL, "scene %d out of [0,%d)", scene, RR_MAX_SCENES);
+  if ((size_t)scene >= c->scenes.size() || !c->scenes[scene]) return fail(c, RR_ENOTREADY, "scene %d not uploaded", scene);
+  *out = c->scenes[scene];
+  return RR_OK;
+}
+
+rr_status synth_checks(rr_ctx *c, const rr_radar *r, rr_synth_variant v) {
+  rr_status st;
+  if (!check_radar(c, r, &st)) return st;
+  if (!pow2(r->n_samples) || r->n_samples < 16 || r->n_samples > 1024)
+    return fail(c, RR_EINVAL, "n_samples=%d must be a power of two in [16,1024]", r->n_samples);
+  if (r->n_chirps > 1024) return fail(c, RR_EINVAL, "n_chirps=%d > 1024", r->n_chirps);
+  if (v != RR_SYNTH_FP32) return fail(c, RR_EINVAL, "synthesis variant %d is not available in this build", (int)v);
+  return RR_OK;
+}
+
+rr_status run_synth(rr_ctx *c, const rr_radar *r, const uint32_t *count, int64_t kmax, int64_t ld,
+                    const float *d, const float *a, const float *dd, float *out) {
+  const rr::RadarDev rd = to_dev(r);
+  const int64_t need = rr::synth_partial_floats(rd, kmax);
+  RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
+  RR_CUDA(c, rr::launch_synth_fp32(rd, count, kmax, ld, d, a, dd, c->partials, c->partials_cap, out, c->stream),
+          "synth_if launch");
+  return RR_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char *rr_version(void) { return "rr-gb300 0.1 (sm_103a)"; }
+
+rr_status rr_create(rr_ctx **out, int device, void *cuda_stream) {
+  if (!out) return RR_EINVAL;
+  *out = nullptr;
+  int ndev = 0;
+  if (cudaGetDeviceCount(&ndev) != cudaSuccess || device < 0 || device >= ndev) return RR_ECUDA;
+  rr_ctx *c = new (std::nothrow) rr_ctx();
+  if (!c) return RR_ENOMEM;
+  c->device = device;
+  DeviceGuard g(device);
+  cudaError_t e = cudaSuccess;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    e = cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = e == cudaSuccess;
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void **)&c->d_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_err, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_err, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_counts, sizeof(uint32_t) * RR_MAX_SCENES);
+  if (e == cudaSuccess) e = cudaMallocHost((void **)&c->h_roots, sizeof(int32_t) * RR_MAX_SCENES);
+  if (e != cudaSuccess) {
+    rr_destroy(c);
+    return e == cudaErrorMemoryAllocation ? RR_ENOMEM : RR_ECUDA;
+  }
+  c->scenes.assign(RR_MAX_SCENES, nullptr);
+  *out = c;
+  return RR_OK;
+}
+
+rr_status rr_destroy(rr_ctx *c) {
+  if (!c) return RR_EINVAL;
+  DeviceGuard g(c->device);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (SceneDev *s : c->scenes) free_scene(s);
+  if (c->d_err) cudaFree(c->d_err);
+  if (c->h_err) cudaFreeHost(c->h_err);
+  if (c->h_counts) cudaFreeHost(c->h_counts);
+  if (c->h_roots) cudaFreeHost(c->h_roots);
+  if (c->partials) cudaFree(c->partials);
+  if (c->if_tmp) cudaFree(c->if_tmp);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return RR_OK;
+}
+
+rr_status rr_set_stream(rr_ctx *c, void *cuda_stream) {
+  if (!c) return RR_EINVAL;
+  DeviceGuard g(c->device);
+  if (c->own_stream && c->stream) {
+    cudaStreamSynchronize(c->stream);
+    cudaStreamDestroy(c->stream);
+  }
+  c->own_stream = false;
+  if (cuda_stream) {
+    c->stream = (cudaStream_t)cuda_stream;
+  } else {
+    RR_CUDA(c, cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking), "stream create");
+    c->own_stream = true;
+  }
+  return RR_OK;
+}
+
+const char *rr_last_error(const rr_ctx *c) { return c ? c->msg : "null context"; }
+
+rr_status rr_sync(rr_ctx *c) {
+  if (!c) return RR_EINVAL;
+  DeviceGuard g(c->device);
+  RR_CUDA(c, cudaMemcpyAsync(c->h_err, c->d_err, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream), "sync: read error word");
+  RR_CUDA(c, cudaMemsetAsync(c->d_err, 0, sizeof(uint32_t), c->stream), "sync: clear error word");
+  RR_CUDA(c, cudaStreamSynchronize(c->stream), "sync");
+  rr_status st = RR_OK;
+  bool overflow = false;
+  for (const auto &p : c->pending) {
+    if (p.n_hits_out) {
+      *p.n_hits_out = (int64_t)c->h_counts[p.scene];
+      if (*p.n_hits_out > p.cap) overflow = true;
+    }
+    if (p.root_out) *p.root_out = c->h_roots[p.scene];
+  }
+  c->pending.clear();
+  const uint32_t err = *c->h_err;
+  if (err & rr::ERR_TIMEOUT) st = fail(c, RR_ETIMEOUT, "a bounded device wait ran out");
+  else if (err & rr::ERR_STACK_OVERFLOW) st = fail(c, RR_EOVERFLOW, "traversal stack overflow");
+  else if ((err & rr::ERR_HIT_OVERFLOW) || overflow) st = fail(c, RR_EOVERFLOW, "hit list capacity exceeded");
+  else if (err & rr::ERR_BAD_INPUT) st = fail(c, RR_EINVAL, "kernel rejected its input");
+  return st;
+}
+
+rr_status rr_scene_upload(rr_ctx *c, int scene, const float *verts, int64_t nv, const int32_t *tris,
+                          int64_t nt, const float *vel, int ptr_is_device) {
+  if (!c) return RR_EINVAL;
+  if (scene < 0 || scene >= RR_MAX_SCENES) return fail(c, RR_EINVAL, "scene %d out of [0,%d)", scene, RR_MAX_SCENES);
+  if (nv < 0 || nt < 0) return fail(c, RR_EINVAL, "negative sizes");
+  if (nt > (int64_t)1 << 28) return fail(c, RR_EINVAL, "nt=%lld exceeds 2^28", (long long)nt);
+  if (nt > 0 && (!verts || !tris || nv < 3)) return fail(c, RR_EINVAL, "null mesh arrays");
+  DeviceGuard g(c->device);
+  SceneDev *s = c->scenes[scene];
+  if (!s) {
+    s = new (std::nothrow) SceneDev();
+    if (!s) return fail(c, RR_ENOMEM, "host allocation");
+    c->scenes[scene] = s;
+    RR_CUDA(c, cudaMalloc((void **)&s->hdr, sizeof(rr::BvhHeader)), "header");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_count, sizeof(uint32_t)), "hit counter");
+  }
+  if (nv > s->cap_nv || !s->V) {
+    if (s->V) cudaFree(s->V);
+    s->V = nullptr;
+    RR_CUDA(c, cudaMalloc((void **)&s->V, sizeof(float) * 3 * (size_t)(nv > 0 ? nv : 1)), "vertices");
+    s->cap_nv = nv;
+  }
+  if (nt > s->cap_nt || !s->F) {
+    void *old[] = {s->F, s->cent, s->blockbounds, s->keys, s->keys_alt, s->ids, s->ids_alt, s->flags, s->nodes, s->tris};
+    for (void *p : old)
+      if (p) cudaFree(p);
+    const size_t n = (size_t)(nt > 0 ? nt : 1);
+    const size_t nblk = (n + 255) / 256;
+    RR_CUDA(c, cudaMalloc((void **)&s->F, sizeof(int32_t) * 3 * n), "faces");
+    RR_CUDA(c, cudaMalloc((void **)&s->cent, sizeof(float4) * n), "centres");
+    RR_CUDA(c, cudaMalloc((void **)&s->blockbounds, sizeof(float) * 6 * nblk), "block bounds");
+    RR_CUDA(c, cudaMalloc((void **)&s->keys, sizeof(uint32_t) * n), "keys");
+    RR_CUDA(c, cudaMalloc((void **)&s->keys_alt, sizeof(uint32_t) * n), "keys");
+    RR_CUDA(c, cudaMalloc((void **)&s->ids, sizeof(int32_t) * n), "ids");
+    RR_CUDA(c, cudaMalloc((void **)&s->ids_alt, sizeof(int32_t) * n), "ids");
+    RR_CUDA(c, cudaMalloc((void **)&s->flags, sizeof(int32_t) * n), "flags");
+    RR_CUDA(c, cudaMalloc((void **)&s->nodes, sizeof(rr::BvhNode) * n), "nodes");
+    RR_CUDA(c, cudaMalloc((void **)&s->tris, sizeof(float4) * 3 * n), "triangles");
+    s->cap_nt = nt;
+  }
+  const cudaMemcpyKind kind = ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice;
+  if (nt > 0) {
+    RR_CUDA(c, cudaMemcpyAsync(s->V, verts, sizeof(float) * 3 * (size_t)nv, kind, c->stream), "upload vertices");
+    RR_CUDA(c, cudaMemcpyAsync(s->F, tris, sizeof(int32_t) * 3 * (size_t)nt, kind, c->stream), "upload faces");
+  }
+  if (!ptr_is_device) RR_CUDA(c, cudaStreamSynchronize(c->stream), "upload");  // caller may reuse host arrays
+  s->nv = nv;
+  s->nt = nt;
+  for (int i = 0; i < 3; ++i) s->vel[i] = vel ? vel[i] : 0.f;
+  s->built = false;
+  s->traced = false;
+  return RR_OK;
+}
+
+rr_status rr_build_bvh(rr_ctx *c, int scene) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  DeviceGuard g(c->device);
+  RR_CUDA(c, rr::launch_build_bvh(*s, c->stream), "build_bvh launch");
+  s->built = true;
+  s->traced = false;
+  return RR_OK;
+}
+
+rr_status rr_trace_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_raygrid *grid,
+                         int64_t hit_capacity, int64_t *n_hits_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->built) return fail(c, RR_ENOTREADY, "scene %d: build_bvh must follow scene_upload", scene);
+  if (!check_radar(c, radar, &st)) return st;
+  if (!grid || grid->n_az < 1 || grid->n_el < 1 || (int64_t)grid->n_az * grid->n_el > ((int64_t)1 << 30))
+    return fail(c, RR_EINVAL, "ray grid size invalid");
+  if (!(grid->half_az > 0 && grid->half_az < M_PI) || !(grid->half_el > 0 && grid->half_el < 0.5 * M_PI))
+    return fail(c, RR_EINVAL, "ray grid half angles out of range");
+  const int64_t n_rays = (int64_t)grid->n_az * grid->n_el;
+  const int64_t cap = hit_capacity > 0 ? hit_capacity : n_rays;
+  DeviceGuard g(c->device);
+  if (cap > s->hit_cap || !s->hit_ray) {
+    void *old[] = {s->hit_ray, s->hit_tri, s->hit_pos, s->hit_t, s->hit_d, s->hit_a, s->hit_dd};
+    for (void *p : old)
+      if (p) cudaFree(p);
+    s->hit_ray = s->hit_tri = s->hit_pos = nullptr;
+    s->hit_t = s->hit_d = s->hit_a = s->hit_dd = nullptr;
+    s->hit_cap = 0;
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_ray, sizeof(int32_t) * cap), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_tri, sizeof(int32_t) * cap), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_pos, sizeof(int32_t) * cap), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_t, sizeof(float) * cap), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_d, sizeof(float) * cap * RR_MAX_RX), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_a, sizeof(float) * cap * RR_MAX_RX), "hit list");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_dd, sizeof(float) * cap * RR_MAX_RX), "hit list");
+    s->hit_cap = cap;
+  }
+  const rr::RadarDev rd = to_dev(radar);
+  const rr::GridDev gd = to_dev(grid);
+  RR_CUDA(c, rr::launch_trace(*s, rd, gd, cap, c->d_err, c->stream), "trace launch");
+  s->hit_nrx = radar->n_rx;
+  s->hit_used_cap = cap;
+  s->traced = true;
+  if (n_hits_out) {
+    RR_CUDA(c, cudaMemcpyAsync(c->h_counts + scene, s->hit_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream),
+            "hit count readback");
+    c->pending.push_back({n_hits_out, nullptr, scene, cap});
+  }
+  return RR_OK;
+}
+
+rr_status rr_get_hits(rr_ctx *c, int scene, int64_t capacity, int32_t *ray, int32_t *tri, float *t,
+                      float *d, float *amp, float *ddot) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->traced) return fail(c, RR_ENOTREADY, "scene %d has no hit list", scene);
+  if (capacity < 0 || capacity > s->hit_used_cap) return fail(c, RR_EINVAL, "capacity exceeds the trace capacity");
+  if (capacity == 0) return RR_OK;
+  DeviceGuard g(c->device);
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (ray) RR_CUDA(c, cudaMemcpyAsync(ray, s->hit_ray, 4 * capacity, k, c->stream), "get_hits");
+  if (tri) RR_CUDA(c, cudaMemcpyAsync(tri, s->hit_tri, 4 * capacity, k, c->stream), "get_hits");
+  if (t) RR_CUDA(c, cudaMemcpyAsync(t, s->hit_t, 4 * capacity, k, c->stream), "get_hits");
+  const float *src[3] = {s->hit_d, s->hit_a, s->hit_dd};
+  float *dst[3] = {d, amp, ddot};
+  for (int f = 0; f < 3; ++f)
+    if (dst[f])
+      RR_CUDA(c, cudaMemcpy2DAsync(dst[f], 4 * capacity, src[f], 4 * s->hit_used_cap, 4 * capacity, s->hit_nrx, k,
+                                   c->stream),
+              "get_hits");
+  return RR_OK;
+}
+
+rr_status rr_synth_if(rr_ctx *c, int scene, const rr_radar *radar, rr_synth_variant variant, float *if_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->traced) return fail(c, RR_ENOTREADY, "scene %d: trace_frame must come first", scene);
+  if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  if (radar->n_rx != s->hit_nrx) return fail(c, RR_EINVAL, "radar n_rx differs from the traced hit list");
+  if (!if_out) return fail(c, RR_EINVAL, "if_out is NULL");
+  DeviceGuard g(c->device);
+  return run_synth(c, radar, s->hit_count, s->hit_used_cap, s->hit_used_cap, s->hit_d, s->hit_a, s->hit_dd, if_out);
+}
+
+rr_status rr_synth_if_from_hits(rr_ctx *c, const rr_radar *radar, rr_synth_variant variant, int64_t K,
+                                const float *d, const float *amp, const float *ddot, float *if_out) {
+  if (!c) return RR_EINVAL;
+  rr_status st;
+  if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  if (K < 0 || K > ((int64_t)1 << 31)) return fail(c, RR_EINVAL, "K=%lld out of range", (long long)K);
+  if (!if_out || (K > 0 && (!d || !amp || !ddot))) return fail(c, RR_EINVAL, "null pointer");
+  DeviceGuard g(c->device);
+  return run_synth(c, radar, nullptr, K, K, d, amp, ddot, if_out);
+}
+
+rr_status rr_range_doppler(rr_ctx *c, const float *if_in, int n_rx, int n_chirps, int n_samples, int window,
+                           float *rd_out) {
+  if (!c) return RR_EINVAL;
+  if (!if_in || !rd_out) return fail(c, RR_EINVAL, "null pointer");
+  if (if_in == rd_out) return fail(c, RR_EINVAL, "in-place range_doppler is not supported");
+  if (n_rx < 1 || !pow2(n_chirps) || !pow2(n_samples) || n_chirps > 1024 || n_samples > 1024 ||
+      (int64_t)n_chirps * n_samples > 16384)
+    return fail(c, RR_EINVAL, "range_doppler sizes invalid (powers of two, M*N <= 16384)");
+  if (window != 0 && window != 1) return fail(c, RR_EINVAL, "window must be 0 or 1");
+  DeviceGuard g(c->device);
+  RR_CUDA(c, rr::launch_range_doppler(if_in, n_rx, n_chirps, n_samples, window, rd_out, c->stream),
+          "range_doppler launch");
+  return RR_OK;
+}
+
+rr_status rr_run_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_raygrid *grid, rr_synth_variant variant,
+                       int window, float *if_out, float *rd_out) {
+  if (!c) return RR_EINVAL;
+  if (!if_out && !rd_out) return fail(c, RR_EINVAL, "need if_out or rd_out");
+  rr_status st;
+  if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  if ((st = rr_build_bvh(c, scene)) != RR_OK) return st;
+  if ((st = rr_trace_frame(c, scene, radar, grid, 0, nullptr)) != RR_OK) return st;
+  float *ifb = if_out;
+  if (!ifb) {
+    DeviceGuard g(c->device);
+    const int64_t need = (int64_t)2 * radar->n_rx * radar->n_chirps * radar->n_samples;
+    RR_CUDA(c, grow(c->if_tmp, c->if_tmp_cap, need), "frame IF buffer");
+    ifb = c->if_tmp;
+  }
+  if ((st = rr_synth_if(c, scene, radar, variant, ifb)) != RR_OK) return st;
+  if (rd_out) st = rr_range_doppler(c, ifb, radar->n_rx, radar->n_chirps, radar->n_samples, window, rd_out);
+  return st;
+}
+
+rr_status rr_get_bvh(rr_ctx *c, int scene, uint32_t *codes, int32_t *ids, int32_t *left, int32_t *right,
+                     float *boxes, int32_t *root_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->built) return fail(c, RR_ENOTREADY, "scene %d has no BVH", scene);
+  DeviceGuard g(c->device);
+  const int64_t n = s->nt;
+  const cudaMemcpyKind k = cudaMemcpyDeviceToDevice;
+  if (codes && n > 0) RR_CUDA(c, cudaMemcpyAsync(codes, s->keys, 4 * n, k, c->stream), "get_bvh");
+  if (ids && n > 0) RR_CUDA(c, cudaMemcpyAsync(ids, s->ids, 4 * n, k, c->stream), "get_bvh");
+  if (n > 1) {
+    const size_t pitch = sizeof(rr::BvhNode);
+    if (left) RR_CUDA(c, cudaMemcpy2DAsync(left, 4, (const char *)s->nodes + offsetof(rr::BvhNode, kids), pitch, 4, n - 1, k, c->stream), "get_bvh");
+    if (right) RR_CUDA(c, cudaMemcpy2DAsync(right, 4, (const char *)s->nodes + offsetof(rr::BvhNode, kids) + 4, pitch, 4, n - 1, k, c->stream), "get_bvh");
+    if (boxes) RR_CUDA(c, cudaMemcpy2DAsync(boxes, 48, s->nodes, pitch, 48, n - 1, k, c->stream), "get_bvh");
+  }
+  if (root_out) {
+    RR_CUDA(c, cudaMemcpyAsync(c->h_roots + scene, &s->hdr->root, 4, cudaMemcpyDeviceToHost, c->stream), "get_bvh root");
+    c->pending.push_back({nullptr, root_out, scene, 0});
+  }
+  return RR_OK;
+}
+
+}  // extern "C"

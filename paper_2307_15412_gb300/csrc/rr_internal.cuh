@@ -1,0 +1,107 @@
+// rr_internal.cuh -- device data layouts and launch interfaces shared by the
+// CUDA translation units of the radar ray-tracing library.  Not installed.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rr.h"
+
+namespace rr {
+
+// Device error word bits (latched by kernels, read and cleared by rr_sync).
+enum : uint32_t {
+  ERR_HIT_OVERFLOW = 1u << 0,
+  ERR_STACK_OVERFLOW = 1u << 1,
+  ERR_TIMEOUT = 1u << 2,
+  ERR_BAD_INPUT = 1u << 3,
+};
+
+constexpr double kC = 299792458.0;  // speed of light, m/s
+constexpr int kStackDepth = 64;     // traversal stack entries per ray
+
+// Binary BVH node: both child boxes live in the parent, so one 64-byte
+// fetch tests both children.  Children: >= 0 internal node (numbered by
+// split position), < 0 leaf ~position in Morton order.
+struct __align__(16) BvhNode {
+  float4 lxy;  // left  child: lo.x, hi.x, lo.y, hi.y
+  float4 rxy;  // right child: lo.x, hi.x, lo.y, hi.y
+  float4 lrz;  // left lo.z, left hi.z, right lo.z, right hi.z
+  int4 kids;   // left, right, unused, unused
+};
+
+struct BvhHeader {
+  int32_t root;   // root node (>= 0) or ~0 for a single leaf; meaningless when n == 0
+  int32_t n;      // triangle count
+  float lo[3];    // scene box (all triangles)
+  float hi[3];
+};
+
+// Scene arrays on the device (owned by the context).
+struct SceneDev {
+  int64_t nv = 0, nt = 0;
+  float *V = nullptr;            // [nv][3]
+  int32_t *F = nullptr;          // [nt][3]
+  float vel[3] = {0.f, 0.f, 0.f};
+  // LBVH
+  float4 *cent = nullptr;        // [nt] bounding-box centre (w unused)
+  float *blockbounds = nullptr;  // [nblk][6] per-block centre bounds
+  uint32_t *keys = nullptr;      // [nt] Morton codes (sorted after the build)
+  uint32_t *keys_alt = nullptr;  // [nt]
+  int32_t *ids = nullptr;        // [nt] triangle ids (sorted after the build)
+  int32_t *ids_alt = nullptr;    // [nt]
+  int32_t *flags = nullptr;      // [nt] bottom-up visit flags
+  BvhNode *nodes = nullptr;      // [nt-1]
+  float4 *tris = nullptr;        // [nt][3] vertices in Morton order, .w of [0] = triangle id
+  BvhHeader *hdr = nullptr;
+  int64_t cap_nt = 0, cap_nv = 0;
+  bool built = false;
+  // hit list
+  int64_t hit_cap = 0;           // capacity of the arrays below
+  int32_t hit_nrx = 0;           // n_rx of the last trace
+  int64_t hit_used_cap = 0;      // capacity used by the last trace
+  uint32_t *hit_count = nullptr; // device counter (true count, may exceed capacity)
+  int32_t *hit_ray = nullptr;    // [cap]
+  int32_t *hit_tri = nullptr;    // [cap] original triangle id
+  int32_t *hit_pos = nullptr;    // [cap] Morton position of the triangle
+  float *hit_t = nullptr;        // [cap]
+  float *hit_d = nullptr;        // [RR_MAX_RX][cap]
+  float *hit_a = nullptr;
+  float *hit_dd = nullptr;
+  bool traced = false;
+};
+
+// Radar parameters in the form the kernels use.
+struct RadarDev {
+  double R[9];
+  double tx[3];
+  double rx[RR_MAX_RX][3];
+  float Rf[9];
+  float txf[3];
+  int n_rx, N, M, amp_mode;
+  double f0, slope, dt, t_rep;
+  float alpha, spec_exp;
+};
+
+struct GridDev {
+  int n_az, n_el;
+  double half_az, half_el;
+  double daz, del;          // cell sizes (rad)
+  float az0_pi, daz_pi;     // (az of cell 0) / pi and cell size / pi, FP32 ray generation
+  float el0_pi, del_pi;
+  float daz_f, del_f;
+};
+
+// ---- launchers (each returns the launch status) ----
+cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st);
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
+                         uint32_t *err, cudaStream_t st);
+cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,
+                              int64_t ld, const float *d, const float *a, const float *dd,
+                              float *partials, int64_t partial_cap_floats, float *out,
+                              cudaStream_t st);
+int64_t synth_partial_floats(const RadarDev &r, int64_t kmax);
+cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
+                                 cudaStream_t st);
+
+}  // namespace rr

@@ -1,0 +1,299 @@
+// synth.cu -- FMCW IF synthesis on the CUDA cores (plain FP32 path).
+//
+// Eq. 4 (Sec. III-B) sums exp(-j 2 pi f d_i / c) over received rays for
+// every frequency step.  In FMCW form, sample n of chirp m of receive
+// channel j is
+//   s[j][m][n] = sum_k a_kj exp(-j 2 pi (f0 + S t_n)(d_kj + ddot_kj m T_rep) / c).
+// Expanding the phase (in cycles) with t_n = n dt:
+//   phi = f0 d / c  +  m f0 ddot T_rep / c  +  n beta_m,
+//   beta_m = S dt (d + ddot m T_rep) / c.
+// The large term f0 d / c (~100 cycles) is reduced modulo 1 in FP64 -- the
+// only FP64 operation of the synthesis, once per (hit, channel) and chirp
+// group -- and everything else runs in FP32.
+//
+// The sample axis is split n = h LO + l (LO = 16), which turns the sum into
+// an outer product per (j, m):
+//   s[h][l] = sum_k A[h][k] B[k][l],  A = a e^{-j 2 pi (cyc_m + beta_m LO h)},
+//                                     B = e^{-j 2 pi beta_m l}.
+// Per hit and chirp one thread builds the HI + LO phasors by complex
+// recurrences (3 sincospi calls) into shared memory; then every thread
+// accumulates a TH x 4 block of complex outputs: 4 FFMA per complex MAC,
+// 8 flops of algorithmic work.  Hits are split across CTAs (split-K) into
+// partial cubes that a second kernel sums in a fixed order, so results do
+// not depend on scheduling.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rr_internal.cuh"
+
+namespace rr {
+namespace {
+
+constexpr int kSynthThreads = 256;
+constexpr int kLO = 16;
+
+struct SynthParams {
+  const float *d, *a, *dd;
+  int64_t ld;             // row stride of the [n_rx][ld] hit arrays
+  const uint32_t *count;  // device hit count (nullptr: kmax hits)
+  int64_t kmax;
+  int n_rx, M, N;
+  int G, KG, KC, n_mtiles, S;
+  double f0_c;            // f0 / c (1/m)
+  double kb;              // S dt / c = B / (N c) (1/m)
+  float c1k;              // f0 T_rep / c (s/m)
+  float b1k;              // kb T_rep (s/m)
+  float *partials;        // [S][n_rx][M][N] complex
+};
+
+__device__ __forceinline__ float2 cmul(float2 x, float2 y) {
+  return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+}
+
+// e^{-j 2 pi x} for any FP32 x (x is first reduced to [-1/2, 1/2])
+__device__ __forceinline__ float2 expm2pi(float x) {
+  const float r = x - rintf(x);
+  float s, c;
+  sincospif(2.f * r, &s, &c);
+  return make_float2(c, -s);
+}
+
+template <int HI>
+__global__ void __launch_bounds__(kSynthThreads)
+k_synth_fp32(const SynthParams p) {
+  constexpr int TH = HI < 4 ? HI : 4;       // rows of h per thread
+  constexpr int TPC = (HI / TH) * 4;        // threads per chirp tile
+  constexpr int PAIRS = HI <= 16 ? 256 : (HI == 32 ? 128 : 64);
+  constexpr int HIP = HI < 2 ? 2 : HI;       // A block padded to keep B 16-byte aligned
+  constexpr int BOFF = 2 * HIP;             // float offset of the B phasors in a pair
+  constexpr int STRIDE = BOFF + 2 * kLO + 4;  // floats per pair (multiple of 4; padded against bank conflicts)
+  extern __shared__ float4 smem4[];
+  float *ph = reinterpret_cast<float *>(smem4);          // [PAIRS][STRIDE]
+  __shared__ float hc_c0[256], hc_c1[256], hc_b0[256], hc_b1[256], hc_a[256];
+
+  const int j = blockIdx.x % p.n_rx;
+  const int mt = blockIdx.x / p.n_rx;
+  const int s_idx = blockIdx.y;
+  const int tid = threadIdx.x;
+  const int slot = tid / TPC, tile = tid % TPC;
+  const int c = slot % p.G, kg = slot / p.G;
+  const bool active = kg < p.KG;
+  const int m = mt * p.G + c;
+  const bool mvalid = active && m < p.M;
+  const int hb = tile / 4, lb = tile % 4;
+
+  const int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+  const int64_t nchunks = (K + p.KC - 1) / p.KC;
+
+  float2 acc[TH][4];
+#pragma unroll
+  for (int i = 0; i < TH; ++i)
+#pragma unroll
+    for (int q = 0; q < 4; ++q) acc[i][q] = make_float2(0.f, 0.f);
+
+  const float *dj = p.d + (int64_t)j * p.ld;
+  const float *aj = p.a + (int64_t)j * p.ld;
+  const float *ddj = p.dd + (int64_t)j * p.ld;
+
+  for (int64_t ch = s_idx; ch < nchunks; ch += p.S) {
+    const int64_t k0 = ch * p.KC;
+    const int kcount = (int)min((int64_t)p.KC, K - k0);
+    // per-hit constants of this channel; the FP64 carrier reduction
+    if (tid < kcount) {
+      const float d = dj[k0 + tid], dd = ddj[k0 + tid];
+      const double x = p.f0_c * (double)d;
+      hc_c0[tid] = (float)(x - floor(x));
+      hc_c1[tid] = p.c1k * dd;
+      hc_b0[tid] = (float)(p.kb * (double)d);
+      hc_b1[tid] = p.b1k * dd;
+      hc_a[tid] = aj[k0 + tid];
+    }
+    __syncthreads();
+    // phasors of each (hit, chirp) pair
+    if (tid < PAIRS) {
+      const int kk = tid / p.G, cc = tid % p.G;
+      const int mm = mt * p.G + cc;
+      if (kk < kcount && mm < p.M) {
+        const float beta = fmaf((float)mm, hc_b1[kk], hc_b0[kk]);
+        const float cyc = fmaf((float)mm, hc_c1[kk], hc_c0[kk]);
+        float2 A = expm2pi(cyc);
+        A.x *= hc_a[kk];
+        A.y *= hc_a[kk];
+        const float2 W = expm2pi(beta * (float)kLO);
+        const float2 w = expm2pi(beta);
+        float2 *dst = reinterpret_cast<float2 *>(ph + tid * STRIDE);
+#pragma unroll
+        for (int h = 0; h < HI; ++h) {
+          dst[h] = A;
+          A = cmul(A, W);
+        }
+        float2 B = make_float2(1.f, 0.f);
+#pragma unroll
+        for (int l = 0; l < kLO; ++l) {
+          dst[HIP + l] = B;
+          B = cmul(B, w);
+        }
+      }
+    }
+    __syncthreads();
+    if (mvalid) {
+      for (int kk = kg; kk < kcount; kk += p.KG) {
+        const float *src = ph + (kk * p.G + c) * STRIDE;
+        float2 Av[TH], Bv[4];
+#pragma unroll
+        for (int i = 0; i < TH; ++i) Av[i] = reinterpret_cast<const float2 *>(src)[hb * TH + i];
+        const float4 b01 = reinterpret_cast<const float4 *>(src + BOFF + 8 * lb)[0];
+        const float4 b23 = reinterpret_cast<const float4 *>(src + BOFF + 8 * lb)[1];
+        Bv[0] = make_float2(b01.x, b01.y);
+        Bv[1] = make_float2(b01.z, b01.w);
+        Bv[2] = make_float2(b23.x, b23.y);
+        Bv[3] = make_float2(b23.z, b23.w);
+#pragma unroll
+        for (int i = 0; i < TH; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            acc[i][q].x = fmaf(Av[i].x, Bv[q].x, acc[i][q].x);
+            acc[i][q].x = fmaf(-Av[i].y, Bv[q].y, acc[i][q].x);
+            acc[i][q].y = fmaf(Av[i].x, Bv[q].y, acc[i][q].y);
+            acc[i][q].y = fmaf(Av[i].y, Bv[q].x, acc[i][q].y);
+          }
+      }
+    }
+    __syncthreads();
+  }
+
+  // sum the hit groups of this CTA in a fixed order (reuses the phasor buffer)
+  float2 *red = reinterpret_cast<float2 *>(ph);
+  if (p.KG > 1) {
+    if (active) {
+#pragma unroll
+      for (int i = 0; i < TH; ++i)
+#pragma unroll
+        for (int q = 0; q < 4; ++q) red[((kg * p.G + c) * TPC + tile) * (TH * 4) + i * 4 + q] = acc[i][q];
+    }
+    __syncthreads();
+    if (active && kg == 0) {
+      for (int g2 = 1; g2 < p.KG; ++g2)
+#pragma unroll
+        for (int i = 0; i < TH; ++i)
+#pragma unroll
+          for (int q = 0; q < 4; ++q) {
+            const float2 v = red[((g2 * p.G + c) * TPC + tile) * (TH * 4) + i * 4 + q];
+            acc[i][q].x += v.x;
+            acc[i][q].y += v.y;
+          }
+    }
+  }
+  if (mvalid && kg == 0) {
+    float2 *out = reinterpret_cast<float2 *>(p.partials) +
+                  (((int64_t)s_idx * p.n_rx + j) * p.M + m) * (int64_t)p.N;
+#pragma unroll
+    for (int i = 0; i < TH; ++i) {
+      const int h = hb * TH + i;
+      float4 *o4 = reinterpret_cast<float4 *>(out + h * kLO + lb * 4);
+      o4[0] = make_float4(acc[i][0].x, acc[i][0].y, acc[i][1].x, acc[i][1].y);
+      o4[1] = make_float4(acc[i][2].x, acc[i][2].y, acc[i][3].x, acc[i][3].y);
+    }
+  }
+}
+
+__global__ void k_synth_reduce(const float2 *__restrict__ partials, int S, int64_t total, float2 *__restrict__ out) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= total) return;
+  float2 s = partials[i];
+  for (int k = 1; k < S; ++k) {
+    const float2 v = partials[(int64_t)k * total + i];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[i] = s;
+}
+
+struct Plan {
+  int HI, TPC, PAIRS, G, KG, KC, n_mtiles, S;
+  size_t smem;
+};
+
+Plan make_plan(const RadarDev &r, int64_t kmax) {
+  Plan pl;
+  pl.HI = r.N / kLO;
+  const int TH = pl.HI < 4 ? pl.HI : 4;
+  pl.TPC = (pl.HI / TH) * 4;
+  pl.PAIRS = pl.HI <= 16 ? 256 : (pl.HI == 32 ? 128 : 64);
+  const int slots = kSynthThreads / pl.TPC;
+  int G = 1;
+  while (G * 2 <= slots && G * 2 <= r.M && G * 2 <= pl.PAIRS) G *= 2;
+  pl.G = G;
+  pl.KG = slots / G;
+  pl.KC = pl.PAIRS / G;
+  pl.n_mtiles = (r.M + G - 1) / G;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)pl.n_mtiles * r.n_rx;
+  const int64_t chunks = (kmax + pl.KC - 1) / pl.KC;
+  int64_t S = (3 * (int64_t)sms + tiles - 1) / tiles;
+  if (S > chunks) S = chunks;
+  if (S < 1) S = 1;
+  pl.S = (int)S;
+  const int hip = pl.HI < 2 ? 2 : pl.HI;
+  pl.smem = (size_t)pl.PAIRS * (size_t)(2 * hip + 2 * kLO + 4) * sizeof(float);
+  return pl;
+}
+
+template <int HI>
+cudaError_t launch_hi(const SynthParams &p, const Plan &pl, cudaStream_t st) {
+  static bool attr_set = false;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_synth_fp32<HI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid(pl.n_mtiles * p.n_rx, pl.S);
+  k_synth_fp32<HI><<<grid, kSynthThreads, pl.smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+int64_t synth_partial_floats(const RadarDev &r, int64_t kmax) {
+  const Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
+  return (int64_t)pl.S * r.n_rx * r.M * r.N * 2;
+}
+
+cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax, int64_t ld,
+                              const float *d, const float *a, const float *dd, float *partials,
+                              int64_t partial_cap_floats, float *out, cudaStream_t st) {
+  const Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
+  const int64_t total = (int64_t)r.n_rx * r.M * r.N;
+  if ((int64_t)pl.S * total * 2 > partial_cap_floats) return cudaErrorInvalidValue;
+  SynthParams p;
+  p.d = d; p.a = a; p.dd = dd; p.ld = ld;
+  p.count = count; p.kmax = kmax;
+  p.n_rx = r.n_rx; p.M = r.M; p.N = r.N;
+  p.G = pl.G; p.KG = pl.KG; p.KC = pl.KC; p.n_mtiles = pl.n_mtiles; p.S = pl.S;
+  p.f0_c = r.f0 / kC;
+  p.kb = r.slope * r.dt / kC;
+  p.c1k = (float)(r.f0 * r.t_rep / kC);
+  p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
+  p.partials = partials;
+  cudaError_t e;
+  switch (pl.HI) {
+    case 1: e = launch_hi<1>(p, pl, st); break;
+    case 2: e = launch_hi<2>(p, pl, st); break;
+    case 4: e = launch_hi<4>(p, pl, st); break;
+    case 8: e = launch_hi<8>(p, pl, st); break;
+    case 16: e = launch_hi<16>(p, pl, st); break;
+    case 32: e = launch_hi<32>(p, pl, st); break;
+    case 64: e = launch_hi<64>(p, pl, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = (total + threads - 1) / threads;
+  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total,
+                                                        reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace rr

@@ -1,0 +1,274 @@
+// trace.cu -- ray traversal, closest hit and echo.
+//
+// k_trace  one thread per ray of the az/el grid (Sec. III-A: many rays
+//          leave each Tx antenna).  The ray is generated in FP32 in the
+//          kernel, traverses the LBVH with a short per-thread stack (both
+//          child boxes are tested from one node fetch; the nearer child is
+//          followed, the other pushed with its entry distance), and each
+//          leaf triangle is tested with the watertight ray-triangle test of
+//          Woop, Benthin and Wald (JCGT 2013).  Faces are two-sided; equal
+//          distances keep the lowest triangle id.  Hits are appended to the
+//          hit list with one atomic per warp.
+// k_echo   one thread per hit: the hit distance is recomputed in FP64 from
+//          the triangle's plane and the exact ray direction (FP32 traversal
+//          decides *which* triangle; FP64 fixes *where*, so distances agree
+//          with an FP64 reference to ~1e-15 even at grazing incidence), then
+//          the echo per receive antenna (Sec. III-A material model, Eq. 1-3
+//          as expected lobes; Sec. III-B path length): d_j = t + |p - rx_j|,
+//          a_j = Omega g_j / (t r_j), d-dot_j = v . (u + u_j).
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rr_internal.cuh"
+
+namespace rr {
+namespace {
+
+constexpr int kTileAz = 16, kTileEl = 8;  // rays per CTA (4 warps of 8 x 4 rays)
+constexpr int kTraceThreads = kTileAz * kTileEl;
+constexpr float kBoxSlack = 1.0000004f;   // covers FP32 rounding of the slab test
+
+struct RayPre {
+  float ox, oy, oz;
+  float ix, iy, iz;  // 1 / direction
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float safe_inv(float d) {
+  const float a = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+  return 1.0f / a;
+}
+
+// slab test; returns entry distance or +inf
+__device__ __forceinline__ float box_entry(const RayPre &r, float lx, float hx, float ly, float hy,
+                                           float lz, float hz, float tmax) {
+  const float tx0 = (lx - r.ox) * r.ix, tx1 = (hx - r.ox) * r.ix;
+  const float ty0 = (ly - r.oy) * r.iy, ty1 = (hy - r.oy) * r.iy;
+  const float tz0 = (lz - r.oz) * r.iz, tz1 = (hz - r.oz) * r.iz;
+  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+  return (tn <= tf * kBoxSlack && tn <= tmax) ? tn : INFINITY;
+}
+
+__device__ __forceinline__ float sel3(float x, float y, float z, int k) {
+  return k == 0 ? x : (k == 1 ? y : z);
+}
+
+// Watertight ray-triangle test; updates (best_t, best_pos, best_id).
+__device__ __forceinline__ void tri_test(const RayPre &r, const float4 *__restrict__ tris, int pos,
+                                         float &best_t, int &best_pos, int &best_id) {
+  const float4 a = __ldg(tris + 3 * pos), b = __ldg(tris + 3 * pos + 1), c = __ldg(tris + 3 * pos + 2);
+  const int id = __float_as_int(a.w);
+  const float a0 = a.x - r.ox, a1 = a.y - r.oy, a2 = a.z - r.oz;
+  const float b0 = b.x - r.ox, b1 = b.y - r.oy, b2 = b.z - r.oz;
+  const float c0 = c.x - r.ox, c1 = c.y - r.oy, c2 = c.z - r.oz;
+  const float Akz = sel3(a0, a1, a2, r.kz), Bkz = sel3(b0, b1, b2, r.kz), Ckz = sel3(c0, c1, c2, r.kz);
+  const float Ax = sel3(a0, a1, a2, r.kx) - r.Sx * Akz, Ay = sel3(a0, a1, a2, r.ky) - r.Sy * Akz;
+  const float Bx = sel3(b0, b1, b2, r.kx) - r.Sx * Bkz, By = sel3(b0, b1, b2, r.ky) - r.Sy * Bkz;
+  const float Cx = sel3(c0, c1, c2, r.kx) - r.Sx * Ckz, Cy = sel3(c0, c1, c2, r.ky) - r.Sy * Ckz;
+  // edge functions without contraction: a shared edge gives exactly opposite values
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float Vv = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.f || Vv == 0.f || W == 0.f) {
+    // exact sign from double products of the float operands
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    Vv = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.f || Vv < 0.f || W < 0.f) && (U > 0.f || Vv > 0.f || W > 0.f)) return;
+  const float det = U + Vv + W;
+  if (det == 0.f) return;
+  const float T = U * (r.Sz * Akz) + Vv * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+  const float t = T / det;
+  if (!(t > 0.f)) return;
+  if (t < best_t || (t == best_t && id < best_id)) {
+    best_t = t;
+    best_pos = pos;
+    best_id = id;
+  }
+}
+
+__global__ void __launch_bounds__(kTraceThreads)
+k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
+        const BvhHeader *__restrict__ hdr, const RadarDev r, const GridDev g, int64_t cap,
+        uint32_t *__restrict__ count, int32_t *__restrict__ hit_ray, int32_t *__restrict__ hit_tri,
+        int32_t *__restrict__ hit_pos, float *__restrict__ hit_t, uint32_t *__restrict__ err) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i_az = blockIdx.x * kTileAz + (warp & 1) * 8 + (lane & 7);
+  const int i_el = blockIdx.y * kTileEl + (warp >> 1) * 4 + (lane >> 3);
+  const bool valid = i_az < g.n_az && i_el < g.n_el;
+
+  float best_t = INFINITY;
+  int best_pos = -1, best_id = 0x7fffffff;
+  const int n = hdr->n;
+  if (valid && n > 0) {
+    float sa, ca, se, ce;
+    sincospif(fmaf((float)i_az, g.daz_pi, g.az0_pi), &sa, &ca);
+    sincospif(fmaf((float)i_el, g.del_pi, g.el0_pi), &se, &ce);
+    const float ur[3] = {ce * sa, se, ce * ca};
+    float d[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) d[k] = r.Rf[3 * k] * ur[0] + r.Rf[3 * k + 1] * ur[1] + r.Rf[3 * k + 2] * ur[2];
+    RayPre rp;
+    rp.ox = r.txf[0]; rp.oy = r.txf[1]; rp.oz = r.txf[2];
+    rp.ix = safe_inv(d[0]); rp.iy = safe_inv(d[1]); rp.iz = safe_inv(d[2]);
+    int kz = 0;
+    if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+    if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
+    int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+    if (d[kz] < 0.f) { const int tmp = kx; kx = ky; ky = tmp; }
+    rp.kx = kx; rp.ky = ky; rp.kz = kz;
+    rp.Sx = d[kx] / d[kz];
+    rp.Sy = d[ky] / d[kz];
+    rp.Sz = 1.0f / d[kz];
+
+    const float t_root = box_entry(rp, hdr->lo[0], hdr->hi[0], hdr->lo[1], hdr->hi[1], hdr->lo[2], hdr->hi[2], INFINITY);
+    const int root = hdr->root;
+    if (t_root < INFINITY) {
+      if (root < 0) {
+        tri_test(rp, tris, ~root, best_t, best_pos, best_id);
+      } else {
+        int stack_node[kStackDepth];
+        float stack_t[kStackDepth];
+        int sp = 0;
+        int node = root;
+        while (true) {
+          const float4 lxy = __ldg(&nodes[node].lxy);
+          const float4 rxy = __ldg(&nodes[node].rxy);
+          const float4 lrz = __ldg(&nodes[node].lrz);
+          const int4 kids = __ldg(&nodes[node].kids);
+          const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
+          const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
+          bool hl = tl < INFINITY, hr = tr < INFINITY;
+          if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
+          if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
+          if (hl && hr) {
+            const bool lnear = tl <= tr;
+            if (sp == kStackDepth) { atomicOr(err, ERR_STACK_OVERFLOW); break; }
+            stack_node[sp] = lnear ? kids.y : kids.x;
+            stack_t[sp] = lnear ? tr : tl;
+            ++sp;
+            node = lnear ? kids.x : kids.y;
+          } else if (hl) {
+            node = kids.x;
+          } else if (hr) {
+            node = kids.y;
+          } else {
+            bool found = false;
+            while (sp > 0) {
+              --sp;
+              if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
+            }
+            if (!found) break;
+          }
+        }
+      }
+    }
+  }
+  // warp-aggregated append
+  const bool has = best_pos >= 0;
+  const uint32_t mask = __ballot_sync(0xffffffffu, has);
+  if (mask == 0u) return;
+  const int leader = __ffs(mask) - 1;
+  uint32_t base = 0;
+  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+  base = __shfl_sync(0xffffffffu, base, leader);
+  if (has) {
+    const int64_t slot = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+    if (slot < cap) {
+      hit_ray[slot] = i_el * g.n_az + i_az;
+      hit_tri[slot] = best_id;
+      hit_pos[slot] = best_pos;
+      hit_t[slot] = best_t;
+    } else {
+      atomicOr(err, ERR_HIT_OVERFLOW);
+    }
+  }
+}
+
+__global__ void __launch_bounds__(128)
+k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const float3 vel,
+       const uint32_t *__restrict__ count, int64_t cap, const int32_t *__restrict__ hit_ray,
+       const int32_t *__restrict__ hit_pos, float *__restrict__ hit_t, float *__restrict__ hit_d,
+       float *__restrict__ hit_a, float *__restrict__ hit_dd) {
+  const int64_t K = min((int64_t)*count, cap);
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < K; h += (int64_t)gridDim.x * blockDim.x) {
+    const int ray = hit_ray[h];
+    const int pos = hit_pos[h];
+    const int i_el = ray / g.n_az, i_az = ray - i_el * g.n_az;
+    // exact ray direction (FP64), as the grid defines it
+    const double az = -g.half_az + g.daz * (i_az + 0.5);
+    const double el = -g.half_el + g.del * (i_el + 0.5);
+    double sa, ca, se, ce;
+    sincos(az, &sa, &ca);
+    sincos(el, &se, &ce);
+    const double ur[3] = {ce * sa, se, ce * ca};
+    double u[3];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) u[k] = r.R[3 * k] * ur[0] + r.R[3 * k + 1] * ur[1] + r.R[3 * k + 2] * ur[2];
+    const float4 fa = __ldg(tris + 3 * pos), fb = __ldg(tris + 3 * pos + 1), fc = __ldg(tris + 3 * pos + 2);
+    const double v0[3] = {fa.x, fa.y, fa.z};
+    const double e1[3] = {(double)fb.x - v0[0], (double)fb.y - v0[1], (double)fb.z - v0[2]};
+    const double e2[3] = {(double)fc.x - v0[0], (double)fc.y - v0[1], (double)fc.z - v0[2]};
+    double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+    const double un = u[0] * nn[0] + u[1] * nn[1] + u[2] * nn[2];
+    const double num = nn[0] * (v0[0] - r.tx[0]) + nn[1] * (v0[1] - r.tx[1]) + nn[2] * (v0[2] - r.tx[2]);
+    double t = num / un;
+    if (!(t > 0.0)) t = (double)hit_t[h];  // degenerate plane: keep the traversal distance
+    hit_t[h] = (float)t;
+    const double p[3] = {r.tx[0] + t * u[0], r.tx[1] + t * u[1], r.tx[2] + t * u[2]};
+    // unit face normal turned toward the incoming ray (two-sided faces)
+    const double inl = rsqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+    const double sgn = un > 0.0 ? -inl : inl;
+    const float nf[3] = {(float)(nn[0] * sgn), (float)(nn[1] * sgn), (float)(nn[2] * sgn)};
+    const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
+    const float ci = -(uf[0] * nf[0] + uf[1] * nf[1] + uf[2] * nf[2]);
+    // Eq. 2 mirror direction u - 2 (u . n_f) n_f
+    const float mr[3] = {uf[0] + 2.f * ci * nf[0], uf[1] + 2.f * ci * nf[1], uf[2] + 2.f * ci * nf[2]};
+    const float omega = (float)(ce * g.daz * g.del);
+    for (int j = 0; j < r.n_rx; ++j) {
+      const double w[3] = {p[0] - r.rx[j][0], p[1] - r.rx[j][1], p[2] - r.rx[j][2]};
+      const double rj = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+      const float irf = (float)(1.0 / rj);
+      const float uj[3] = {(float)w[0] * irf, (float)w[1] * irf, (float)w[2] * irf};
+      const float co = -(uj[0] * nf[0] + uj[1] * nf[1] + uj[2] * nf[2]);
+      float gj = 0.f;
+      if (co > 0.f) {
+        const float sdot = -(mr[0] * uj[0] + mr[1] * uj[1] + mr[2] * uj[2]);
+        const float s = sdot > 0.f ? powf(sdot, r.spec_exp) : 0.f;
+        gj = (1.f - r.alpha) * s + r.alpha * (ci * co);
+      }
+      const int64_t o = (int64_t)j * cap + h;
+      hit_d[o] = (float)(t + rj);
+      hit_a[o] = r.amp_mode == 1 ? 1.f : (float)((double)omega * gj / (t * rj));
+      hit_dd[o] = vel.x * (uf[0] + uj[0]) + vel.y * (uf[1] + uj[1]) + vel.z * (uf[2] + uj[2]);
+    }
+  }
+}
+
+}  // namespace
+
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
+                         uint32_t *err, cudaStream_t st) {
+  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  dim3 grid((g.n_az + kTileAz - 1) / kTileAz, (g.n_el + kTileEl - 1) / kTileEl);
+  k_trace<<<grid, kTraceThreads, 0, st>>>(s.nodes, s.tris, s.hdr, r, g, cap, s.hit_count, s.hit_ray,
+                                         s.hit_tri, s.hit_pos, s.hit_t, err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  int sms = 152;
+  int dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (cap + 127) / 128;
+  const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
+  const float3 vel = make_float3(s.vel[0], s.vel[1], s.vel[2]);
+  k_echo<<<blocks, 128, 0, st>>>(s.tris, r, g, vel, s.hit_count, cap, s.hit_ray, s.hit_pos, s.hit_t,
+                                 s.hit_d, s.hit_a, s.hit_dd);
+  return cudaGetLastError();
+}
+
+}  // namespace rr

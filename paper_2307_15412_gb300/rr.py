@@ -1,0 +1,238 @@
+"""Thin Python binding of the C ABI declared in include/rr.h.
+
+Argument marshalling only: every step of the hot path runs in the CUDA
+kernels of librr.so.  Device buffers are torch CUDA tensors (PyTorch
+provides device memory and the stream); host buffers are numpy arrays.
+Loading fails loudly when the library has not been built: there is no
+CPU fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from typing import Optional
+
+import numpy as np
+
+from .inputs import Radar, RayGrid
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "librr.so")
+
+RR_OK, RR_EINVAL, RR_ENOMEM, RR_ECUDA, RR_EOVERFLOW, RR_ETIMEOUT, RR_ENOTREADY = range(7)
+RR_MAX_RX = 8
+SYNTH_FP32, SYNTH_TC_BF16X3, SYNTH_TC_TF32 = 0, 1, 2
+
+STATUS_NAMES = {0: "RR_OK", 1: "RR_EINVAL", 2: "RR_ENOMEM", 3: "RR_ECUDA", 4: "RR_EOVERFLOW",
+                5: "RR_ETIMEOUT", 6: "RR_ENOTREADY"}
+
+# every function the header declares, with its ctypes signature
+_P = ctypes.c_void_p
+_I = ctypes.c_int
+_I64 = ctypes.c_int64
+
+
+class rr_radar(ctypes.Structure):
+    _fields_ = [("frame", ctypes.c_double * 9), ("tx", ctypes.c_double * 3),
+                ("rx", (ctypes.c_double * 3) * RR_MAX_RX), ("n_rx", ctypes.c_int32),
+                ("n_samples", ctypes.c_int32), ("n_chirps", ctypes.c_int32), ("amp_mode", ctypes.c_int32),
+                ("f0", ctypes.c_double), ("bandwidth", ctypes.c_double), ("t_chirp", ctypes.c_double),
+                ("t_rep", ctypes.c_double), ("alpha", ctypes.c_double), ("spec_exp", ctypes.c_double)]
+
+
+class rr_raygrid(ctypes.Structure):
+    _fields_ = [("n_az", ctypes.c_int32), ("n_el", ctypes.c_int32),
+                ("half_az", ctypes.c_double), ("half_el", ctypes.c_double)]
+
+
+SIGNATURES = {
+    "rr_create": (_I, [ctypes.POINTER(_P), _I, _P]),
+    "rr_destroy": (_I, [_P]),
+    "rr_set_stream": (_I, [_P, _P]),
+    "rr_sync": (_I, [_P]),
+    "rr_last_error": (ctypes.c_char_p, [_P]),
+    "rr_version": (ctypes.c_char_p, []),
+    "rr_scene_upload": (_I, [_P, _I, _P, _I64, _P, _I64, _P, _I]),
+    "rr_build_bvh": (_I, [_P, _I]),
+    "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
+                            ctypes.POINTER(_I64)]),
+    "rr_get_hits": (_I, [_P, _I, _I64, _P, _P, _P, _P, _P, _P]),
+    "rr_synth_if": (_I, [_P, _I, ctypes.POINTER(rr_radar), _I, _P]),
+    "rr_synth_if_from_hits": (_I, [_P, ctypes.POINTER(rr_radar), _I, _I64, _P, _P, _P, _P]),
+    "rr_range_doppler": (_I, [_P, _P, _I, _I, _I, _I, _P]),
+    "rr_run_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I, _I, _P, _P]),
+    "rr_get_bvh": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Loads librr.so (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(path):
+            raise ImportError("librr.so not built: run __graft_entry__.build() (no CPU fallback exists)")
+        lib = ctypes.CDLL(path)
+        for name, (res, args) in SIGNATURES.items():
+            fn = getattr(lib, name)
+            fn.restype = res
+            fn.argtypes = args
+        _lib = lib
+    return _lib
+
+
+class RRError(RuntimeError):
+    def __init__(self, status: int, msg: str):
+        super().__init__("%s: %s" % (STATUS_NAMES.get(status, str(status)), msg))
+        self.status = status
+
+
+def make_radar(r: Radar) -> rr_radar:
+    s = rr_radar()
+    for i, v in enumerate(r.frame):
+        s.frame[i] = float(v)
+    for i in range(3):
+        s.tx[i] = float(r.tx[i])
+    if not 1 <= len(r.rx) <= RR_MAX_RX:
+        raise ValueError("1..8 receive antennas")
+    for j, p in enumerate(r.rx):
+        for i in range(3):
+            s.rx[j][i] = float(p[i])
+    s.n_rx = len(r.rx)
+    s.n_samples = int(r.n_samples)
+    s.n_chirps = int(r.n_chirps)
+    s.amp_mode = int(r.amp_mode)
+    s.f0, s.bandwidth, s.t_chirp, s.t_rep = float(r.f0), float(r.bandwidth), float(r.t_chirp), float(r.t_rep)
+    s.alpha, s.spec_exp = float(r.alpha), float(r.spec_exp)
+    return s
+
+
+def make_grid(g: RayGrid) -> rr_raygrid:
+    return rr_raygrid(int(g.n_az), int(g.n_el), float(g.half_az), float(g.half_el))
+
+
+def _ptr(x) -> Optional[int]:
+    if x is None:
+        return None
+    if hasattr(x, "data_ptr"):
+        return x.data_ptr()
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return int(x)
+
+
+class Context:
+    """Owns one rr_ctx.  stream: a torch.cuda.Stream, a raw cudaStream_t
+    (int), or None for torch's current stream on `device` at creation."""
+
+    def __init__(self, device: int = 0, stream=None):
+        import torch
+        self.lib = load()
+        self.device = device
+        if stream is None:
+            stream = torch.cuda.current_stream(device)
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        h = _P()
+        st = self.lib.rr_create(ctypes.byref(h), device, raw)
+        if st != RR_OK:
+            raise RRError(st, "rr_create failed")
+        self.h = h
+        self._pending = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.rr_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st: int):
+        if st != RR_OK:
+            raise RRError(st, self.lib.rr_last_error(self.h).decode())
+
+    def set_stream(self, stream):
+        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (0 if stream is None else int(stream))
+        self._check(self.lib.rr_set_stream(self.h, raw))
+
+    def sync(self):
+        """Waits for the stream; raises on a latched device error."""
+        st = self.lib.rr_sync(self.h)
+        for cell, box in self._pending:
+            box[0] = int(cell.value)
+        self._pending = []
+        self._check(st)
+
+    def scene_upload(self, scene: int, V, F, vel=None):
+        """V float32 [nv,3], F int32 [nt,3]: numpy (host) or torch CUDA tensors."""
+        on_dev = hasattr(V, "is_cuda") and V.is_cuda
+        if on_dev:
+            import torch
+            assert V.dtype == torch.float32 and F.dtype == torch.int32
+            V, F = V.contiguous(), F.contiguous()
+        else:
+            V = np.ascontiguousarray(V, np.float32)
+            F = np.ascontiguousarray(F, np.int32)
+        velp = None
+        if vel is not None:
+            self._vel = np.ascontiguousarray(vel, np.float32).reshape(3)
+            velp = self._vel.ctypes.data
+        self._check(self.lib.rr_scene_upload(self.h, scene, _ptr(V), int(V.shape[0]), _ptr(F), int(F.shape[0]),
+                                             velp, 1 if on_dev else 0))
+
+    def build_bvh(self, scene: int):
+        self._check(self.lib.rr_build_bvh(self.h, scene))
+
+    def trace_frame(self, scene: int, radar: Radar, grid: RayGrid, hit_capacity: int = 0, want_count=True):
+        """Returns a one-element list filled with the hit count by the next sync()."""
+        box = [None]
+        cell = _I64(0)
+        rs, gs = make_radar(radar), make_grid(grid)
+        self._check(self.lib.rr_trace_frame(self.h, scene, ctypes.byref(rs), ctypes.byref(gs), int(hit_capacity),
+                                            ctypes.byref(cell) if want_count else None))
+        if want_count:
+            self._pending.append((cell, box))
+        return box
+
+    def get_hits(self, scene: int, capacity: int, ray=None, tri=None, t=None, d=None, amp=None, ddot=None):
+        self._check(self.lib.rr_get_hits(self.h, scene, int(capacity), _ptr(ray), _ptr(tri), _ptr(t), _ptr(d),
+                                         _ptr(amp), _ptr(ddot)))
+
+    def synth_if(self, scene: int, radar: Radar, if_out, variant: int = SYNTH_FP32):
+        rs = make_radar(radar)
+        self._check(self.lib.rr_synth_if(self.h, scene, ctypes.byref(rs), int(variant), _ptr(if_out)))
+
+    def synth_if_from_hits(self, radar: Radar, d, amp, ddot, if_out, variant: int = SYNTH_FP32):
+        """d, amp, ddot: CUDA float32 [n_rx, K] (contiguous)."""
+        rs = make_radar(radar)
+        K = int(d.shape[1])
+        self._check(self.lib.rr_synth_if_from_hits(self.h, ctypes.byref(rs), int(variant), K, _ptr(d), _ptr(amp),
+                                                   _ptr(ddot), _ptr(if_out)))
+
+    def range_doppler(self, if_in, rd_out, window: int = 0):
+        n_rx, M, N = int(if_in.shape[0]), int(if_in.shape[1]), int(if_in.shape[2])
+        self._check(self.lib.rr_range_doppler(self.h, _ptr(if_in), n_rx, M, N, int(window), _ptr(rd_out)))
+
+    def run_frame(self, scene: int, radar: Radar, grid: RayGrid, if_out=None, rd_out=None, window: int = 0,
+                  variant: int = SYNTH_FP32):
+        rs, gs = make_radar(radar), make_grid(grid)
+        self._check(self.lib.rr_run_frame(self.h, scene, ctypes.byref(rs), ctypes.byref(gs), int(variant),
+                                          int(window), _ptr(if_out), _ptr(rd_out)))
+
+    def get_bvh(self, scene: int, codes=None, ids=None, left=None, right=None, boxes=None):
+        box = [None]
+        cell = ctypes.c_int32(0)
+        self._check(self.lib.rr_get_bvh(self.h, scene, _ptr(codes), _ptr(ids), _ptr(left), _ptr(right), _ptr(boxes),
+                                        ctypes.byref(cell)))
+        self._pending.append((cell, box))
+        return box
+
+
+def complex_view(x):
+    """A float32 [..., 2*N] or [..., N, 2] CUDA tensor as complex64 (no copy)."""
+    import torch
+    return torch.view_as_complex(x.view(*x.shape[:-1], -1, 2)) if x.dtype == torch.float32 else x

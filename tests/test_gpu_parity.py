@@ -1,0 +1,369 @@
+"""GPU parity: the CUDA path through the C ABI against the FP64 oracle.
+
+Tolerances (stated per check):
+  * BVH integer outputs (Morton codes, sorted ids, tree children): bit-exact.
+  * Trace: triangle ids identical and hit distances within 1e-6 relative
+    on at least 99.99 % of rays.
+  * IF synthesis on the same hit list (oracle fed the GPU's float32 hits):
+    rel-L2 <= 1e-5 (plain FP32 path).
+  * Range-Doppler on the same IF cube: rel-L2 <= 1e-5.
+  * End to end (oracle trace + echo + synth vs GPU): rel-L2 <= 1e-3.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bvh as obvh
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import gpu_hits, per_ray, rel_l2, to_complex, trace_scene
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def _cplx_buf(shape):
+    return torch.empty(tuple(shape) + (2,), dtype=torch.float32, device="cuda:0")
+
+
+# ---------------------------------------------------------------- LBVH
+
+@pytest.mark.parametrize("nt_target,seed", [(600, 0), (2000, 1), (20000, 2), (50000, 3)])
+def test_bvh_bit_exact(ctx, nt_target, seed):
+    s = I.hand_scene(seed, nt_target)
+    n = s.F.shape[0]
+    ctx.scene_upload(7, s.V, s.F, s.vel)
+    ctx.build_bvh(7)
+    codes = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    left = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
+    right = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
+    boxes = torch.empty((n - 1, 12), dtype=torch.float32, device="cuda:0")
+    root = ctx.get_bvh(7, codes, ids, left, right, boxes)
+    ctx.sync()
+    ref_codes = obvh.morton_codes(s.V, s.F)
+    order = obvh.sorted_order(ref_codes)
+    g_ids = ids.cpu().numpy()
+    assert np.array_equal(g_ids, order)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint32), ref_codes[order])
+    if n <= 5000:  # the pure-Python tree definition is O(n log n) in Python
+        L, R, rl, rr_, rt = obvh.radix_tree(ref_codes[order])
+        assert root[0] == rt
+        assert np.array_equal(left.cpu().numpy(), L) and np.array_equal(right.cpu().numpy(), R)
+    # every child box contains its subtree (checked for leaves exactly)
+    bx = boxes.cpu().numpy()
+    Lg, Rg = left.cpu().numpy(), right.cpu().numpy()
+    tri_lo = s.V[s.F].min(axis=1)
+    tri_hi = s.V[s.F].max(axis=1)
+    for side, kids in ((0, Lg), (1, Rg)):
+        leaf = kids < 0
+        pos = ~kids[leaf]
+        tid = g_ids[pos]
+        off = 4 * side
+        lo = np.stack([bx[leaf, off + 0], bx[leaf, off + 2], bx[leaf, 8 + 2 * side]], 1)
+        hi = np.stack([bx[leaf, off + 1], bx[leaf, off + 3], bx[leaf, 9 + 2 * side]], 1)
+        assert np.array_equal(lo, tri_lo[tid]) and np.array_equal(hi, tri_hi[tid])
+
+
+# ---------------------------------------------------------------- trace + echo
+
+def _trace_parity(ctx, scene, radar, grid, rays=None):
+    h = trace_scene(ctx, 0, scene, radar, grid)
+    n_rays = grid.n_rays
+    gtri, gt = per_ray(n_rays, h)
+    ref = oracle.frame(scene.V, scene.F, scene.vel, radar, grid, rays=rays)
+    rid = ref["ray_ids"]
+    otri, ot = ref["tri"].astype(np.int64), ref["t"]
+    same = gtri[rid] == otri
+    both = same & (otri >= 0)
+    close = np.ones_like(same)
+    close[both] = np.abs(gt[rid][both] - ot[both]) <= 1e-6 * ot[both]
+    ok = same & close
+    return h, ref, ok, both
+
+
+@pytest.mark.parametrize("seed", [0, 1, 2])
+def test_trace_tiny_parity(ctx, seed):
+    radar, grid, nt = I.workload_tiny()
+    s = I.hand_scene(seed, nt)
+    h, ref, ok, both = _trace_parity(ctx, s, radar, grid)
+    assert ok.mean() >= 0.9999, (ok.size - ok.sum())
+    assert both.sum() > 100
+
+
+def test_trace_full_frame_sampled_parity(ctx):
+    """512 x 512 rays at the full-frame hand; the oracle checks a seeded
+    sample of rays plus every ray of one image row through the hand."""
+    radar, grid, nt = I.workload_full_frame()
+    s = I.hand_scene(11, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+    rng = np.random.default_rng(0)
+    rays = np.unique(np.concatenate([rng.choice(grid.n_rays, 3000, replace=False),
+                                     256 * grid.n_az + np.arange(grid.n_az)]))
+    h, ref, ok, both = _trace_parity(ctx, s, radar, grid, rays=rays)
+    assert ok.mean() >= 0.9999, (ok.size - ok.sum())
+    assert both.sum() > 50
+
+
+def test_echo_matches_oracle_on_same_hits(ctx):
+    radar, grid, nt = I.workload_full_frame()
+    radar.n_chirps = 4
+    s = I.hand_scene(5, 4000, range_m=(0.25, 0.35), speed=(-1, 1))
+    h = trace_scene(ctx, 0, s, radar, grid)
+    dirs, omega = oracle.ray_dirs(grid, radar.frame)
+    sel = h["ray"]
+    d, a, dd = oracle.echo(s.V, s.F, np.asarray(radar.tx, float), dirs[sel], h["t"].astype(np.float64),
+                           h["tri"], omega[sel], radar, s.vel.astype(np.float64))
+    # the oracle gets the GPU's float32 t: path lengths follow to float32 rounding
+    np.testing.assert_allclose(h["d"], d, rtol=4e-7)
+    amax = np.abs(a).max()
+    np.testing.assert_allclose(h["a"], a, rtol=2e-5, atol=1e-6 * amax)
+    np.testing.assert_allclose(h["dd"], dd, rtol=0, atol=2e-6)
+
+
+# ---------------------------------------------------------------- synthesis
+
+def _synth_gpu(ctx, radar, d, a, dd):
+    out = _cplx_buf((radar.n_rx, radar.n_chirps, radar.n_samples))
+    dt = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    ctx.synth_if_from_hits(radar, dt(d), dt(a), dt(dd), out)
+    ctx.sync()
+    return to_complex(out)
+
+
+@pytest.mark.parametrize("N,M,n_rx,K", [
+    (16, 1, 1, 1), (32, 3, 2, 257), (64, 1, 1, 300), (64, 5, 3, 1000), (128, 32, 3, 2049),
+    (256, 64, 3, 4000), (256, 1, 1, 6000), (512, 2, 1, 513), (1024, 1, 1, 700), (256, 7, 2, 1)])
+def test_synth_from_hits_fp32_parity(ctx, N, M, n_rx, K):
+    radar = I.Radar(n_samples=N, n_chirps=M, rx=I.rx_l_array()[:n_rx] if n_rx <= 3 else None)
+    d, a, dd = I.random_hits(100 + K, K, n_rx)
+    got = _synth_gpu(ctx, radar, d, a, dd)
+    ref = oracle.synth(d, a, dd, radar)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_synth_empty_hit_list(ctx):
+    radar = I.Radar(n_samples=64, n_chirps=4, rx=I.rx_l_array())
+    out = _cplx_buf((3, 4, 64))
+    out.fill_(7.0)
+    e = torch.empty((3, 0), dtype=torch.float32, device="cuda:0")
+    ctx.synth_if_from_hits(radar, e, e, e, out)
+    ctx.sync()
+    assert torch.count_nonzero(out).item() == 0
+
+
+def test_synth_max_hits(ctx):
+    """2^18 hits into one 256-sample chirp (the precision workload's largest hit list)."""
+    radar = I.Radar(n_samples=256, n_chirps=1)
+    K = 1 << 18
+    d, a, dd = I.random_hits(9, K, 1)
+    got = _synth_gpu(ctx, radar, d, a, dd)
+    ref = oracle.synth(d, a, dd, radar)
+    assert rel_l2(got, ref) <= 1e-5
+
+
+def test_synth_point_target_closed_form(ctx):
+    """GPU synthesis + range-Doppler of a point target at integer bins lands
+    in range bin B d / c and Doppler bin f0 d-dot T_rep M / c."""
+    M, N = 64, 256
+    radar = I.Radar(n_samples=N, n_chirps=M)
+    k0, q0 = 37, 5
+    d = np.array([[k0 * I.C_LIGHT / radar.bandwidth]], np.float32)
+    dd = np.array([[q0 * I.C_LIGHT / (radar.f0 * radar.t_rep * M)]], np.float32)
+    x = _synth_gpu(ctx, radar, d, np.ones((1, 1), np.float32), dd)
+    xin = torch.from_numpy(np.stack([x.real, x.imag], -1).astype(np.float32)).cuda()
+    rd = _cplx_buf((1, M, N))
+    ctx.range_doppler(xin, rd)
+    ctx.sync()
+    X = np.abs(to_complex(rd))[0]
+    q, k = np.unravel_index(np.argmax(X), X.shape)
+    assert (q, k) == (q0 + M // 2, k0)
+
+
+# ---------------------------------------------------------------- range-Doppler
+
+@pytest.mark.parametrize("M,N,n_rx,window", [(1, 16, 1, 0), (1, 64, 1, 0), (8, 16, 2, 1), (64, 256, 3, 0),
+                                             (64, 256, 3, 1), (32, 128, 3, 0), (2, 1024, 1, 0), (16, 1024, 1, 1),
+                                             (1024, 16, 1, 0)])
+def test_range_doppler_parity(ctx, M, N, n_rx, window):
+    rng = np.random.default_rng(M * 1000 + N)
+    x = (rng.normal(size=(n_rx, M, N)) + 1j * rng.normal(size=(n_rx, M, N))).astype(np.complex64)
+    xin = torch.from_numpy(np.stack([x.real, x.imag], -1)).cuda()
+    out = _cplx_buf((n_rx, M, N))
+    ctx.range_doppler(xin, out, window=window)
+    ctx.sync()
+    ref = oracle.range_doppler(x.astype(np.complex128), window=window)
+    assert rel_l2(to_complex(out), ref) <= 1e-5
+
+
+# ---------------------------------------------------------------- whole frame
+
+@pytest.mark.parametrize("seed", [0, 3])
+def test_frame_tiny_end_to_end(ctx, seed):
+    radar, grid, nt = I.workload_tiny()
+    s = I.hand_scene(seed, nt)
+    ctx.scene_upload(1, s.V, s.F, s.vel)
+    if_out = _cplx_buf((1, 1, 64))
+    rd_out = _cplx_buf((1, 1, 64))
+    ctx.run_frame(1, radar, grid, if_out=if_out, rd_out=rd_out)
+    ctx.sync()
+    ref = oracle.frame(s.V, s.F, s.vel, radar, grid)
+    assert rel_l2(to_complex(if_out), ref["if_cube"]) <= 1e-3
+    assert rel_l2(to_complex(rd_out), oracle.range_doppler(ref["if_cube"])) <= 1e-3
+
+
+def test_frame_full_size_same_hit_list(ctx):
+    """Full-frame workload (20k triangles, 512^2 rays, 3 RX, 64 x 256) in the
+    launch configuration the benchmark times: the synthesis and the
+    range-Doppler map are checked against the oracle on the GPU's own hit
+    list and IF cube; the traced hit list against sampled oracle rays."""
+    radar, grid, nt = I.workload_full_frame()
+    s = I.hand_scene(21, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+    ctx.scene_upload(2, s.V, s.F, s.vel)
+    if_out = _cplx_buf((3, 64, 256))
+    rd_out = _cplx_buf((3, 64, 256))
+    # the calls rr_run_frame makes, one by one, to read the hit count
+    ctx.build_bvh(2)
+    cnt = ctx.trace_frame(2, radar, grid)
+    ctx.synth_if(2, radar, if_out)
+    ctx.range_doppler(if_out, rd_out)
+    ctx.sync()
+    h = gpu_hits(ctx, 2, 3, cnt[0])
+    assert h["ray"].size > 1000
+    ref_if = oracle.synth(h["d"], h["a"], h["dd"], radar)
+    got_if = to_complex(if_out)
+    assert rel_l2(got_if, ref_if) <= 1e-5
+    assert rel_l2(to_complex(rd_out), oracle.range_doppler(got_if)) <= 1e-5
+
+
+# ---------------------------------------------------------------- closed forms on the GPU
+
+def test_gpu_plate_hit_set(ctx):
+    D, hx, hy = 0.3, 0.05, 0.03
+    V, F = I.plate((0.0, 0.0, D), hx, hy, nx=8, ny=6)
+    D = float(V[0, 2])
+    radar = I.Radar(n_samples=64)
+    grid = I.RayGrid(64, 64, math.radians(20.0), math.radians(20.0))
+    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.array([0, 0, D]), angles_deg=None)
+    h = trace_scene(ctx, 3, sc, radar, grid)
+    dirs, _ = oracle.ray_dirs(grid)
+    x = D * dirs[:, 0] / dirs[:, 2]
+    y = D * dirs[:, 1] / dirs[:, 2]
+    inside = (np.abs(x) < hx) & (np.abs(y) < hy)
+    gtri, gt = per_ray(grid.n_rays, h)
+    assert np.array_equal(gtri >= 0, inside)
+    np.testing.assert_allclose(gt[inside], D / dirs[inside, 2], rtol=1e-6)
+
+
+def test_gpu_sphere_hit_set(ctx):
+    D, r = 0.3, 0.05
+    V, F = I.icosphere((0.0, 0.0, D), r, subdiv=3)
+    grid = I.RayGrid(96, 96, math.radians(12.0), math.radians(12.0))
+    radar = I.Radar(n_samples=64)
+    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.array([0, 0, D]), angles_deg=None)
+    h = trace_scene(ctx, 3, sc, radar, grid)
+    gtri, _ = per_ray(grid.n_rays, h)
+    otri, _ = oracle.trace(V, F, np.zeros(3), oracle.ray_dirs(grid)[0])
+    assert (gtri == otri).mean() >= 0.9999
+
+
+def test_gpu_lowest_id_on_duplicates(ctx):
+    V = np.array([(-1, -1, 1), (1, -1, 1), (0, 1, 1)], np.float32)
+    F = np.array([(2, 0, 1), (0, 1, 2), (1, 2, 0), (0, 1, 2)], np.int32)
+    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.zeros(3), angles_deg=None)
+    grid = I.RayGrid(4, 4, 0.2, 0.2)
+    h = trace_scene(ctx, 4, sc, I.Radar(n_samples=16), grid)
+    assert h["ray"].size == 16 and (h["tri"] == 0).all()
+
+
+def test_gpu_rotation_invariance_exact(ctx):
+    s = I.hand_scene(3, 2000)
+    R = np.array([[0, 0, 1], [1, 0, 0], [0, 1, 0]], np.float64)
+    grid = I.RayGrid(64, 64, math.radians(30.0), math.radians(30.0))
+    r0 = I.Radar(n_samples=64)
+    r1 = I.Radar(n_samples=64, frame=tuple(R.reshape(-1)))
+    h0 = trace_scene(ctx, 5, s, r0, grid)
+    s1 = I.Scene(V=(s.V.astype(np.float64) @ R.T).astype(np.float32), F=s.F, vel=s.vel, center=s.center,
+                 angles_deg=None)
+    h1 = trace_scene(ctx, 6, s1, r1, grid)
+    t0, d0 = per_ray(grid.n_rays, h0)
+    t1, d1 = per_ray(grid.n_rays, h1)
+    assert (t0 == t1).mean() >= 0.9999
+    both = (t0 == t1) & (t0 >= 0)
+    np.testing.assert_allclose(d1[both], d0[both], rtol=1e-6)
+
+
+# ---------------------------------------------------------------- edge cases and errors
+
+def test_empty_and_single_triangle_scenes(ctx):
+    radar = I.Radar(n_samples=16)
+    grid = I.RayGrid(8, 8, 0.3, 0.3)
+    empty = I.Scene(V=np.zeros((3, 3), np.float32), F=np.zeros((0, 3), np.int32), vel=np.zeros(3, np.float32),
+                    center=np.zeros(3), angles_deg=None)
+    h = trace_scene(ctx, 8, empty, radar, grid)
+    assert h["ray"].size == 0
+    out = _cplx_buf((1, 1, 16))
+    out.fill_(3.0)
+    ctx.synth_if(8, radar, out)
+    ctx.sync()
+    assert torch.count_nonzero(out).item() == 0
+    V = np.array([(-1, -1, 1), (1, -1, 1), (0, 1, 1)], np.float32)
+    one = I.Scene(V=V, F=np.array([(0, 1, 2)], np.int32), vel=np.zeros(3, np.float32), center=np.zeros(3),
+                  angles_deg=None)
+    h = trace_scene(ctx, 9, one, radar, grid)
+    otri, ot = oracle.trace(V, one.F, np.zeros(3), oracle.ray_dirs(grid)[0])
+    gtri, gt = per_ray(grid.n_rays, h)
+    assert np.array_equal(gtri, otri)
+    np.testing.assert_allclose(gt[otri >= 0], ot[otri >= 0], rtol=1e-6)
+
+
+def test_hit_capacity_overflow_reports_true_count(ctx):
+    from paper_2307_15412_gb300 import rr
+    radar, grid, nt = I.workload_tiny()
+    s = I.hand_scene(0, nt)
+    ctx.scene_upload(10, s.V, s.F, s.vel)
+    ctx.build_bvh(10)
+    cnt = ctx.trace_frame(10, radar, grid, hit_capacity=20)
+    with pytest.raises(rr.RRError) as e:
+        ctx.sync()
+    assert e.value.status == rr.RR_EOVERFLOW
+    assert cnt[0] > 20
+    # the context stays usable
+    cnt = ctx.trace_frame(10, radar, grid)
+    ctx.sync()
+    assert cnt[0] > 20
+
+
+def test_invalid_arguments_are_rejected(ctx):
+    from paper_2307_15412_gb300 import rr
+    radar = I.Radar(n_samples=48)
+    out = _cplx_buf((1, 1, 48))
+    z = torch.zeros((1, 4), dtype=torch.float32, device="cuda:0")
+    with pytest.raises(rr.RRError) as e:
+        ctx.synth_if_from_hits(radar, z, z, z, out)
+    assert e.value.status == rr.RR_EINVAL
+    with pytest.raises(rr.RRError) as e:
+        ctx.build_bvh(4000)
+    assert e.value.status == rr.RR_ENOTREADY
+    s = I.hand_scene(0, 600)
+    ctx.scene_upload(11, s.V, s.F, s.vel)
+    with pytest.raises(rr.RRError) as e:
+        ctx.trace_frame(11, I.Radar(), I.RayGrid(8, 8, 0.2, 0.2))
+    assert e.value.status == rr.RR_ENOTREADY
+    with pytest.raises(rr.RRError) as e:
+        ctx.range_doppler(_cplx_buf((1, 3, 16)), _cplx_buf((1, 3, 16)))
+    assert e.value.status == rr.RR_EINVAL
