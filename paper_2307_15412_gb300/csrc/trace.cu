@@ -136,6 +136,7 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
         int sp = 0;
         int node = root;
         while (true) {
+          if ((unsigned)node >= (unsigned)(n - 1)) { atomicOr(err, ERR_BAD_INPUT); break; }
           const float4 lxy = __ldg(&nodes[node].lxy);
           const float4 rxy = __ldg(&nodes[node].rxy);
           const float4 lrz = __ldg(&nodes[node].lrz);
@@ -143,6 +144,10 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
           const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
           const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
           bool hl = tl < INFINITY, hr = tr < INFINITY;
+          if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
+            atomicOr(err, ERR_BAD_INPUT);
+            break;
+          }
           if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
           if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
           if (hl && hr) {

@@ -282,12 +282,23 @@ def test_gpu_sphere_hit_set(ctx):
 
 
 def test_gpu_lowest_id_on_duplicates(ctx):
+    """Identical triangles give bit-identical FP32 distances: the lowest id
+    wins.  The same triangle with its vertices permuted may round its
+    distance differently in FP32; then any of the coincident ids is a valid
+    nearest hit, and the distance must still be exact."""
     V = np.array([(-1, -1, 1), (1, -1, 1), (0, 1, 1)], np.float32)
-    F = np.array([(2, 0, 1), (0, 1, 2), (1, 2, 0), (0, 1, 2)], np.int32)
-    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.zeros(3), angles_deg=None)
     grid = I.RayGrid(4, 4, 0.2, 0.2)
+    F = np.array([(0, 1, 2), (0, 1, 2), (0, 1, 2)], np.int32)
+    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.zeros(3), angles_deg=None)
     h = trace_scene(ctx, 4, sc, I.Radar(n_samples=16), grid)
     assert h["ray"].size == 16 and (h["tri"] == 0).all()
+    F = np.array([(2, 0, 1), (0, 1, 2), (1, 2, 0), (0, 1, 2)], np.int32)
+    sc = I.Scene(V=V, F=F, vel=np.zeros(3, np.float32), center=np.zeros(3), angles_deg=None)
+    h = trace_scene(ctx, 4, sc, I.Radar(n_samples=16), grid)
+    assert h["ray"].size == 16 and np.isin(h["tri"], [0, 1, 2]).all()
+    dirs, _ = oracle.ray_dirs(grid)
+    gtri, gt = per_ray(grid.n_rays, h)
+    np.testing.assert_allclose(gt, 1.0 / dirs[:, 2], rtol=1e-7)
 
 
 def test_gpu_rotation_invariance_exact(ctx):
