@@ -178,6 +178,37 @@ rr_status rr_range_doppler(rr_ctx *ctx, const float *if_in, int n_rx, int n_chir
 rr_status rr_run_frame(rr_ctx *ctx, int scene, const rr_radar *radar, const rr_raygrid *grid,
                        rr_synth_variant variant, int window, float *if_out, float *rd_out);
 
+/* ---- allocation-free synthesis ------------------------------------------- */
+
+/* Size of the fixed device scratch used by rr_synth_if_from_hits_noalloc. */
+#define RR_NOALLOC_SCRATCH_BYTES (8 << 20)
+
+/* Synthesis from a caller-supplied hit list that allocates nothing: no
+ * context, no cudaMalloc/cudaFree, no allocating library call.  The paper
+ * has no counterpart; this exists for callers that must not allocate device
+ * memory at run time -- pipelines with a fixed memory budget reserved at
+ * start-up, or code hosted inside another runtime that owns the device
+ * allocator -- and for callers with nowhere to keep an rr_ctx.
+ *
+ * Same arguments and result as rr_synth_if_from_hits (d, amp, ddot: device
+ * float32 [n_rx][K]; if_out: device complex64 [n_rx][n_chirps][n_samples]),
+ * enqueued on cuda_stream (a cudaStream_t of the current device, or NULL for
+ * the legacy default stream).  The split-K partial sums live in one static
+ * device array of RR_NOALLOC_SCRATCH_BYTES, reserved on every GPU that loads
+ * the library until the process exits; the call lowers its split count
+ * until the partial cubes fit and returns RR_EINVAL when even one cube
+ * (8 * n_rx * n_chirps * n_samples bytes) exceeds it.  Work runs on the
+ * calling thread's current device.  The first call on a device looks up the
+ * array's device address (cudaGetSymbolAddress); make that first call
+ * before any stream capture.  All calls share the one array and each call
+ * overwrites every part of it that it later reads, so no clearing is
+ * needed, but calls that overlap on the GPU (other streams, other threads)
+ * race on it: serialise them.  Only RR_SYNTH_FP32 is accepted.  Returns
+ * RR_EINVAL for bad arguments, RR_ECUDA for a CUDA error. */
+rr_status rr_synth_if_from_hits_noalloc(const rr_radar *radar, rr_synth_variant variant, int64_t K,
+                                        const float *d, const float *amp, const float *ddot,
+                                        float *if_out, void *cuda_stream);
+
 /* ---- inspection (tests) --------------------------------------------------- */
 
 /* Copies the scene's LBVH into caller device buffers: sorted Morton codes

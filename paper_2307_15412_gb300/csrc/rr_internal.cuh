@@ -101,6 +101,12 @@ cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t 
                               float *partials, int64_t partial_cap_floats, float *out,
                               cudaStream_t st);
 int64_t synth_partial_floats(const RadarDev &r, int64_t kmax);
+// Same synthesis from K caller hits with the split-K partials in a fixed
+// scratch buffer of scratch_floats floats: the split count is lowered until
+// the partial cubes fit (cudaErrorInvalidValue if even one does not).
+cudaError_t launch_synth_fp32_bounded(const RadarDev &r, int64_t K, const float *d, const float *a,
+                                      const float *dd, float *scratch, int64_t scratch_floats, float *out,
+                                      cudaStream_t st);
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st);
 

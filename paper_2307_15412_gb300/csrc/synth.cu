@@ -261,6 +261,43 @@ int64_t synth_partial_floats(const RadarDev &r, int64_t kmax) {
   return (int64_t)pl.S * r.n_rx * r.M * r.N * 2;
 }
 
+cudaError_t launch_synth_fp32_bounded(const RadarDev &r, int64_t K, const float *d, const float *a,
+                                      const float *dd, float *scratch, int64_t scratch_floats, float *out,
+                                      cudaStream_t st) {
+  Plan pl = make_plan(r, K < 1 ? 1 : K);
+  const int64_t total = (int64_t)r.n_rx * r.M * r.N;
+  const int64_t fit = scratch_floats / (2 * total);
+  if (fit < 1) return cudaErrorInvalidValue;
+  if (pl.S > fit) pl.S = (int)fit;
+  SynthParams p;
+  p.d = d; p.a = a; p.dd = dd; p.ld = K;
+  p.count = nullptr; p.kmax = K;
+  p.n_rx = r.n_rx; p.M = r.M; p.N = r.N;
+  p.G = pl.G; p.KG = pl.KG; p.KC = pl.KC; p.n_mtiles = pl.n_mtiles; p.S = pl.S;
+  p.f0_c = r.f0 / kC;
+  p.kb = r.slope * r.dt / kC;
+  p.c1k = (float)(r.f0 * r.t_rep / kC);
+  p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
+  p.partials = scratch;
+  cudaError_t e;
+  switch (pl.HI) {
+    case 1: e = launch_hi<1>(p, pl, st); break;
+    case 2: e = launch_hi<2>(p, pl, st); break;
+    case 4: e = launch_hi<4>(p, pl, st); break;
+    case 8: e = launch_hi<8>(p, pl, st); break;
+    case 16: e = launch_hi<16>(p, pl, st); break;
+    case 32: e = launch_hi<32>(p, pl, st); break;
+    case 64: e = launch_hi<64>(p, pl, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = (total + threads - 1) / threads;
+  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(scratch), pl.S, total,
+                                                        reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax, int64_t ld,
                               const float *d, const float *a, const float *dd, float *partials,
                               int64_t partial_cap_floats, float *out, cudaStream_t st) {

@@ -1,0 +1,92 @@
+// synth_noalloc.cu -- IF synthesis from a caller-supplied hit list that
+// allocates no memory at all.
+//
+// The ordinary entry points keep their intermediate buffers in an rr_ctx
+// and grow them with cudaMalloc.  Some callers cannot allow that: code that
+// runs under a fixed, pre-reserved device-memory budget (embedded or
+// real-time pipelines that forbid allocation after start-up), plug-ins
+// hosted inside another runtime that owns the device allocator and does
+// not want a library to call cudaMalloc/cudaFree behind its back (both may
+// synchronise the device and fragment the host's memory pool), and callers
+// that have no place to keep a context object.  For them this file offers
+// rr_synth_if_from_hits_noalloc: the same kernels as rr_synth_if_from_hits,
+// with the split-K partial sums kept in one statically sized device array
+// that is part of the library image instead of allocated memory.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <mutex>
+
+#include "rr.h"
+#include "rr_internal.cuh"
+
+namespace {
+
+// 8 MiB of split-K partial sums per device, reserved when the library's
+// device code is loaded onto a GPU and held until the process exits.
+constexpr int64_t kNoallocScratchFloats = RR_NOALLOC_SCRATCH_BYTES / (int64_t)sizeof(float);
+static __device__ __align__(256) float g_synth_scratch[kNoallocScratchFloats];
+
+constexpr int kMaxDevices = 64;
+std::mutex g_mu;
+float *g_scratch_ptr[kMaxDevices] = {};
+
+bool pow2(int x) { return x > 0 && (x & (x - 1)) == 0; }
+
+// Device address of the scratch array on the current device; looked up once
+// per device (host code cannot use the array's name as a device pointer).
+cudaError_t scratch_for_current_device(float **out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= kMaxDevices) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    e = cudaGetSymbolAddress(&p, g_synth_scratch);
+    if (e != cudaSuccess) return e;
+    g_scratch_ptr[dev] = static_cast<float *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return cudaSuccess;
+}
+
+}  // namespace
+
+extern "C" rr_status rr_synth_if_from_hits_noalloc(const rr_radar *radar, rr_synth_variant variant, int64_t K,
+                                                   const float *d, const float *amp, const float *ddot,
+                                                   float *if_out, void *cuda_stream) {
+  if (!radar || !if_out) return RR_EINVAL;
+  if (variant != RR_SYNTH_FP32) return RR_EINVAL;
+  if (radar->n_rx < 1 || radar->n_rx > RR_MAX_RX) return RR_EINVAL;
+  if (!pow2(radar->n_samples) || radar->n_samples < 16 || radar->n_samples > 1024) return RR_EINVAL;
+  if (radar->n_chirps < 1 || radar->n_chirps > 1024) return RR_EINVAL;
+  if (!(radar->t_chirp > 0) || !(radar->f0 > 0) || !(radar->t_rep >= 0)) return RR_EINVAL;
+  if (K < 0 || K > ((int64_t)1 << 31)) return RR_EINVAL;
+  if (K > 0 && (!d || !amp || !ddot)) return RR_EINVAL;
+  const int64_t cube_floats = (int64_t)2 * radar->n_rx * radar->n_chirps * radar->n_samples;
+  if (cube_floats > kNoallocScratchFloats) return RR_EINVAL;  // one partial cube must fit the scratch
+  float *scratch = nullptr;
+  if (scratch_for_current_device(&scratch) != cudaSuccess) return RR_ECUDA;
+
+  rr::RadarDev r;
+  for (int i = 0; i < 9; ++i) { r.R[i] = radar->frame[i]; r.Rf[i] = (float)radar->frame[i]; }
+  for (int i = 0; i < 3; ++i) { r.tx[i] = radar->tx[i]; r.txf[i] = (float)radar->tx[i]; }
+  for (int j = 0; j < RR_MAX_RX; ++j)
+    for (int i = 0; i < 3; ++i) r.rx[j][i] = j < radar->n_rx ? radar->rx[j][i] : 0.0;
+  r.n_rx = radar->n_rx;
+  r.N = radar->n_samples;
+  r.M = radar->n_chirps;
+  r.amp_mode = radar->amp_mode;
+  r.f0 = radar->f0;
+  r.slope = radar->bandwidth / radar->t_chirp;
+  r.dt = radar->t_chirp / radar->n_samples;
+  r.t_rep = radar->t_rep;
+  r.alpha = (float)radar->alpha;
+  r.spec_exp = (float)radar->spec_exp;
+  // Every partial slot the reduction reads is written by this call's
+  // synthesis kernel first, so the scratch needs no clearing.
+  const cudaError_t e = rr::launch_synth_fp32_bounded(r, K, d, amp, ddot, scratch, kNoallocScratchFloats, if_out,
+                                                      (cudaStream_t)cuda_stream);
+  return e == cudaSuccess ? RR_OK : RR_ECUDA;
+}

@@ -62,6 +62,7 @@ SIGNATURES = {
     "rr_range_doppler": (_I, [_P, _P, _I, _I, _I, _I, _P]),
     "rr_run_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I, _I, _P, _P]),
     "rr_get_bvh": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
+    "rr_synth_if_from_hits_noalloc": (_I, [ctypes.POINTER(rr_radar), _I, _I64, _P, _P, _P, _P, _P]),
 }
 
 _lib = None
