@@ -37,6 +37,9 @@ WORKLOAD = ("full frame: seeded ~22k-triangle hand, range U(0.2,0.6) m, radial s
 N_SCENES = 8
 FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
+# kernels per frame: LBVH build (one cluster launch), traversal, echo,
+# IF synthesis, split-K sum, range FFT rows, Doppler FFT columns
+LAUNCHES_PER_FRAME = 7
 
 
 def _peaks():
@@ -189,15 +192,10 @@ def run_gpu(args):
         ctx.sync()
         counts.append(box[0])
 
-    def step(k, ev=None):
-        ctx.build_bvh(k)
-        ctx.trace_frame(k, radar, grid, want_count=False)
-        if ev is not None:
-            ev[0].record(stream)
-        ctx.synth_if(k, radar, if_out)
-        if ev is not None:
-            ev[1].record(stream)
-        ctx.range_doppler(if_out, rd_out)
+    rs, gs = rr.make_radar(radar), rr.make_grid(grid)
+
+    def step(k):
+        ctx.run_frame(k, rs, gs, if_out=if_out, rd_out=rd_out)
 
     for i in range(max(args.warmup, 3)):
         step(i % N_SCENES)
@@ -205,9 +203,7 @@ def run_gpu(args):
     torch.cuda.synchronize()
 
     K = args.steps
-    ev_s = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev_e = [torch.cuda.Event(enable_timing=True) for _ in range(K)]
-    ev_syn = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    ctx.timing_enable(K)
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(("GPU-%s" % uuid) if uuid is not None else local)
@@ -218,19 +214,19 @@ def run_gpu(args):
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(K):
-        flush.zero_()
-        ev_s[i].record(stream)
-        step(i % N_SCENES, ev_syn[i])
-        ev_e[i].record(stream)
+        flush.zero_()  # L2 flush, outside the frame's events
+        step(i % N_SCENES)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     ctx.sync()
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    step_ms = [ev_s[i].elapsed_time(ev_e[i]) for i in range(K)]
-    syn_ms = [ev_syn[i][0].elapsed_time(ev_syn[i][1]) for i in range(K)]
-    t_dev = sum(step_ms) / 1e3
+    stages = np.array([ctx.timing_read(i) for i in range(K)])  # build, trace, synth, rd, frame (ms)
+    ctx.timing_enable(0)
+    step_ms = stages[:, 4]
+    syn_ms = stages[:, 2]
+    t_dev = float(step_ms.sum()) / 1e3
     if ws > 1:
         tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
@@ -239,7 +235,7 @@ def run_gpu(args):
 
     # dominant kernel: the IF synthesis (k_synth_fp32 + its split-K sum)
     flops = sum(8.0 * counts[i % N_SCENES] * n_rx * M * N for i in range(K))
-    achieved = flops / (sum(syn_ms) / 1e3) / 1e12
+    achieved = flops / (float(syn_ms.sum()) / 1e3) / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -263,7 +259,7 @@ def run_gpu(args):
         dV[k].copy_(pin[k][0], non_blocking=True)
         dF[k].copy_(pin[k][1], non_blocking=True)
         ctx.scene_upload(k, dV[k], dF[k], scenes[k].vel)
-        ctx.run_frame(k, radar, grid, rd_out=rd_out)
+        ctx.run_frame(k, rs, gs, rd_out=rd_out)
         rd_host.copy_(rd_out, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
 
@@ -309,7 +305,9 @@ def run_gpu(args):
                 "cpu_baseline": cpu,
                 "e2e": {"value": ws * K_e2e / t_e2e, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": K_e2e},
-                "gpu_launches": 8 * K,
+                "stage_ms_mean": {"build_bvh": float(stages[:, 0].mean()), "trace_frame": float(stages[:, 1].mean()),
+                                  "synth_if": float(stages[:, 2].mean()), "range_doppler": float(stages[:, 3].mean())},
+                "gpu_launches": LAUNCHES_PER_FRAME * K,
                 "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line))

@@ -300,6 +300,9 @@ __global__ void k_empty_header(BvhHeader *hdr) {
 
 cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st) {
   const int n = (int)s.nt;
+  bool used = false;
+  cudaError_t ce = launch_build_bvh_cluster(s, st, &used);
+  if (ce != cudaSuccess || used) return ce;
   if (n == 0) {
     k_empty_header<<<1, 1, 0, st>>>(s.hdr);
     return cudaGetLastError();

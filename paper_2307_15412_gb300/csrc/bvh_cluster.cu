@@ -1,0 +1,429 @@
+// bvh_cluster.cu -- single-launch LBVH builder on one thread-block cluster.
+//
+// The same LBVH as bvh.cu (30-bit Morton codes of the triangles'
+// bounding-box centres quantised on the centre bounds, stable radix sort of
+// (code, id), binary radix tree of Karras (HPG 2012) numbered by split
+// position, boxes merged bottom up with the parent rule of Apetrei (EG 2014))
+// built by one cluster of C CTAs (C = 8 or 16, 1024 threads each) whose
+// shared memories together hold the whole problem:
+//   - CTA c owns sorted positions [c cap, (c+1) cap) (cap = ceil(n / C));
+//   - centre bounds are reduced across the cluster through distributed
+//     shared memory (DSMEM);
+//   - each of the four 8-bit LSD passes ranks keys stably inside a CTA
+//     (warp match + per-(digit, warp) scan), pushes its 256 digit counts
+//     into every CTA's count table through DSMEM and scatters each key
+//     straight into the owning CTA's next buffer;
+//   - the bottom-up climb keeps its visit flags and the child boxes a
+//     sibling needs in DSMEM and synchronises with cluster-scope fences and
+//     atomics instead of device-wide ones; the final nodes go to global
+//     memory as they are completed.
+// Meshes too large for one cluster use the three-kernel path of bvh.cu.
+#include <cooperative_groups.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "rr_internal.cuh"
+
+namespace cg = cooperative_groups;
+
+namespace rr {
+namespace {
+
+constexpr int kThreads = 1024;
+constexpr int kWarps = kThreads / 32;
+constexpr int kItems = 4;       // keys per thread and pass (cap <= 4096)
+constexpr int kCnt = 33;        // padded [digit][warp] counter row
+constexpr int kMaxCap = 3700;   // keys per CTA that fit the shared-memory plan below
+
+__device__ __forceinline__ uint32_t spread10(uint32_t v) {
+  v &= 0x3FFu;
+  v = (v | (v << 16)) & 0x030000FFu;
+  v = (v | (v << 8)) & 0x0300F00Fu;
+  v = (v | (v << 4)) & 0x030C30C3u;
+  v = (v | (v << 2)) & 0x09249249u;
+  return v;
+}
+
+// Exchange with release + acquire semantics at cluster scope: the child box
+// stored before it is visible to the sibling thread that reads the flag.
+__device__ __forceinline__ int exch_acq_rel_cluster(int *p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.cluster.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
+// Shared-memory plan (4-byte words): keyA[cap] idA[cap] | region R, where R
+// holds keyB[cap] idB[cap] cnt[256*33] dtot[16][256] during the sort and
+// nbox[12][cap] nflag[cap] hb[cap bytes] during the climb.  hb[x] is the
+// index of the highest bit in which the augmented keys at x and x + 1
+// differ; comparing two of them decides the parent (the two boundary
+// differences of a tree node never share their highest bit).
+struct Plan {
+  uint32_t *keyA;
+  int32_t *idA;
+  uint32_t *keyB;
+  int32_t *idB;
+  uint32_t *cnt;
+  uint32_t *dtot;
+  float *nbox;
+  int32_t *nflag;
+  uint8_t *hb;
+};
+
+__device__ __forceinline__ Plan plan(uint32_t *base, int cap) {
+  Plan p;
+  p.keyA = base;
+  p.idA = reinterpret_cast<int32_t *>(base + cap);
+  uint32_t *R = base + 2 * cap;
+  p.keyB = R;
+  p.idB = reinterpret_cast<int32_t *>(R + cap);
+  p.cnt = R + 2 * cap;
+  p.dtot = p.cnt + 256 * kCnt;
+  p.nbox = reinterpret_cast<float *>(R);
+  p.nflag = reinterpret_cast<int32_t *>(R + 12 * cap);
+  p.hb = reinterpret_cast<uint8_t *>(R + 13 * cap);
+  return p;
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+k_build_cluster(const float *__restrict__ V, const int32_t *__restrict__ F, int n, int cap,
+                BvhNode *__restrict__ nodes, float4 *__restrict__ tris, uint32_t *__restrict__ keys_out,
+                int32_t *__restrict__ ids_out, BvhHeader *__restrict__ hdr) {
+  extern __shared__ uint4 smem_u4[];
+  uint32_t *base = reinterpret_cast<uint32_t *>(smem_u4);
+  __shared__ float s_red[kWarps][6];
+  __shared__ float s_bnd[6];        // this CTA's centre bounds, read by the others
+  __shared__ float s_glob[6];       // cluster-wide centre bounds
+  __shared__ uint32_t s_run[256];
+  __shared__ uint32_t s_wsum[kWarps];
+
+  cg::cluster_group cluster = cg::this_cluster();
+  const int C = (int)cluster.num_blocks();
+  const int crank = (int)cluster.block_rank();
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const uint32_t lt = (1u << lane) - 1u;
+  Plan P = plan(base, cap);
+  const int first = crank * cap;
+  const int mine = max(0, min(cap, n - first));  // keys owned by this CTA
+
+  // 1. centres of this CTA's triangles (ids first .. first + mine) and their bounds
+  float cx[kItems], cy[kItems], cz[kItems];
+  float lo[3] = {INFINITY, INFINITY, INFINITY}, hi[3] = {-INFINITY, -INFINITY, -INFINITY};
+#pragma unroll
+  for (int j = 0; j < kItems; ++j) {
+    const int e = tid + j * kThreads;
+    cx[j] = cy[j] = cz[j] = 0.f;
+    if (e < mine) {
+      const int t = first + e;
+      const int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
+      float cc[3];
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        const float va = V[3 * a + x], vb = V[3 * b + x], vc = V[3 * c + x];
+        cc[x] = __fmul_rn(__fadd_rn(fminf(va, fminf(vb, vc)), fmaxf(va, fmaxf(vb, vc))), 0.5f);
+        lo[x] = fminf(lo[x], cc[x]);
+        hi[x] = fmaxf(hi[x], cc[x]);
+      }
+      cx[j] = cc[0]; cy[j] = cc[1]; cz[j] = cc[2];
+    }
+  }
+#pragma unroll
+  for (int x = 0; x < 3; ++x)
+    for (int o = 16; o > 0; o >>= 1) {
+      lo[x] = fminf(lo[x], __shfl_xor_sync(0xffffffffu, lo[x], o));
+      hi[x] = fmaxf(hi[x], __shfl_xor_sync(0xffffffffu, hi[x], o));
+    }
+  if (lane == 0)
+    for (int x = 0; x < 3; ++x) { s_red[warp][x] = lo[x]; s_red[warp][3 + x] = hi[x]; }
+  __syncthreads();
+  if (tid < 6) {
+    float v = s_red[0][tid];
+    for (int w = 1; w < kWarps; ++w) v = tid < 3 ? fminf(v, s_red[w][tid]) : fmaxf(v, s_red[w][tid]);
+    s_bnd[tid] = v;
+  }
+  cluster.sync();
+  if (tid < 6) {
+    float v = tid < 3 ? INFINITY : -INFINITY;
+    for (int r = 0; r < C; ++r) {
+      const float o = *cluster.map_shared_rank(&s_bnd[tid], r);
+      v = tid < 3 ? fminf(v, o) : fmaxf(v, o);
+    }
+    s_glob[tid] = v;
+  }
+  __syncthreads();
+
+  // 2. Morton codes (same float32 quantisation as the three-kernel path)
+  {
+    float glo[3], ext[3];
+#pragma unroll
+    for (int x = 0; x < 3; ++x) { glo[x] = s_glob[x]; ext[x] = __fsub_rn(s_glob[3 + x], s_glob[x]); }
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int e = tid + j * kThreads;
+      if (e < mine) {
+        const float cc[3] = {cx[j], cy[j], cz[j]};
+        uint32_t q[3];
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          if (ext[x] > 0.f) {
+            float u = __fdiv_rn(__fsub_rn(cc[x], glo[x]), ext[x]);
+            u = __fmul_rn(u, 1024.f);
+            q[x] = (uint32_t)min(max((int)floorf(u), 0), 1023);
+          } else {
+            q[x] = 0u;
+          }
+        }
+        P.keyA[e] = (spread10(q[0]) << 2) | (spread10(q[1]) << 1) | spread10(q[2]);
+        P.idA[e] = first + e;
+      }
+    }
+  }
+  __syncthreads();
+
+  // 3. four stable LSD passes across the cluster
+  uint32_t *srcK = P.keyA, *dstK = P.keyB;
+  int32_t *srcI = P.idA, *dstI = P.idB;
+  for (int pass = 0; pass < 4; ++pass) {
+    const int shift = 8 * pass;
+    for (int x = tid; x < 256 * kCnt; x += kThreads) P.cnt[x] = 0;
+    __syncthreads();
+    uint32_t k[kItems], rank[kItems];
+    int32_t id[kItems];
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int e = (warp * kItems + j) * 32 + lane;
+      const bool ok = e < mine;
+      k[j] = ok ? srcK[e] : 0u;
+      id[j] = ok ? srcI[e] : 0;
+      const uint32_t dg = ok ? ((k[j] >> shift) & 255u) : 256u + lane;
+      const uint32_t peers = __match_any_sync(0xffffffffu, dg);
+      uint32_t before = 0;
+      if (ok) before = P.cnt[dg * kCnt + warp];
+      __syncwarp();
+      if (ok && (peers & lt) == 0u) P.cnt[dg * kCnt + warp] = before + __popc(peers);
+      __syncwarp();
+      rank[j] = before + __popc(peers & lt);
+    }
+    __syncthreads();
+    {  // exclusive scan of the counters in (digit, warp) order
+      const int dg = tid >> 2, w0 = (tid & 3) * 8;
+      uint32_t v[8], s = 0;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { v[q] = P.cnt[dg * kCnt + w0 + q]; s += v[q]; }
+      uint32_t incl = s;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_wsum[warp] = incl;
+      __syncthreads();
+      if (warp == 0) {
+        const uint32_t x = s_wsum[lane];
+        uint32_t xi = x;
+        for (int o = 1; o < 32; o <<= 1) {
+          const uint32_t t = __shfl_up_sync(0xffffffffu, xi, o);
+          if (lane >= o) xi += t;
+        }
+        s_wsum[lane] = xi - x;
+      }
+      __syncthreads();
+      uint32_t run = s_wsum[warp] + incl - s;
+#pragma unroll
+      for (int q = 0; q < 8; ++q) { P.cnt[dg * kCnt + w0 + q] = run; run += v[q]; }
+    }
+    __syncthreads();
+    // push this CTA's 256 digit counts into row crank of every CTA's table
+    for (int x = tid; x < 256 * C; x += kThreads) {
+      const int d = x & 255, r = x >> 8;
+      const uint32_t next = d < 255 ? P.cnt[(d + 1) * kCnt] : (uint32_t)mine;
+      *cluster.map_shared_rank(&P.dtot[crank * 256 + d], r) = next - P.cnt[d * kCnt];
+    }
+    cluster.sync();
+    // global start of (this CTA, digit): keys of smaller digits anywhere plus
+    // keys of this digit in lower-ranked CTAs
+    if (warp < 8) {
+      const int d = tid;  // 0 .. 255
+      uint32_t before = 0, total = 0;
+      for (int r = 0; r < C; ++r) {
+        const uint32_t t = P.dtot[r * 256 + d];
+        total += t;
+        if (r < crank) before += t;
+      }
+      uint32_t incl = total;
+      for (int o = 1; o < 32; o <<= 1) {
+        const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+        if (lane >= o) incl += t;
+      }
+      if (lane == 31) s_wsum[warp] = incl;
+      s_run[d] = incl - total + before;  // warp-local exclusive part, completed below
+    }
+    __syncthreads();
+    if (warp < 8) {
+      uint32_t off = 0;
+      for (int w = 0; w < warp; ++w) off += s_wsum[w];
+      s_run[tid] += off;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int j = 0; j < kItems; ++j) {
+      const int e = (warp * kItems + j) * 32 + lane;
+      if (e < mine) {
+        const uint32_t dg = (k[j] >> shift) & 255u;
+        const uint32_t dest = s_run[dg] + (P.cnt[dg * kCnt + warp] - P.cnt[dg * kCnt]) + rank[j];
+        const int tr = (int)(dest / (uint32_t)cap), slot = (int)(dest - (uint32_t)tr * (uint32_t)cap);
+        *cluster.map_shared_rank(&dstK[slot], tr) = k[j];
+        *cluster.map_shared_rank(&dstI[slot], tr) = id[j];
+      }
+    }
+    cluster.sync();
+    uint32_t *tk = srcK; srcK = dstK; dstK = tk;
+    int32_t *ti = srcI; srcI = dstI; dstI = ti;
+  }
+  // sorted keys and ids are back in keyA / idA
+
+  // 4. bottom-up hierarchy with merged boxes
+  for (int e = tid; e < mine; e += kThreads) {
+    keys_out[first + e] = P.keyA[e];
+    ids_out[first + e] = P.idA[e];
+  }
+  for (int e = tid; e < cap; e += kThreads) P.nflag[e] = -1;
+  for (int e = tid; e < mine; e += kThreads) {
+    const int x = first + e;
+    if (x < n - 1) {
+      const uint32_t k1 = (e + 1 < mine) ? P.keyA[e + 1] : *cluster.map_shared_rank(&P.keyA[0], crank + 1);
+      const uint64_t dx = ((uint64_t)(P.keyA[e] ^ k1) << 32) | (uint32_t)(x ^ (x + 1));
+      P.hb[e] = (uint8_t)(63 - __clzll((long long)dx));
+    }
+  }
+  cluster.sync();
+
+  auto hb_at = [&](int x) -> int {
+    const int r = x / cap;
+    return *cluster.map_shared_rank(&P.hb[x - r * cap], r);
+  };
+
+  for (int e = tid; e < mine; e += kThreads) {
+    const int i = first + e;
+    const int t = P.idA[e];
+    const int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
+    const float3 v0 = make_float3(V[3 * a], V[3 * a + 1], V[3 * a + 2]);
+    const float3 v1 = make_float3(V[3 * b], V[3 * b + 1], V[3 * b + 2]);
+    const float3 v2 = make_float3(V[3 * c], V[3 * c + 1], V[3 * c + 2]);
+    tris[3 * i + 0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(t));
+    tris[3 * i + 1] = make_float4(v1.x, v1.y, v1.z, 0.f);
+    tris[3 * i + 2] = make_float4(v2.x, v2.y, v2.z, 0.f);
+    float bl[3] = {fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z))};
+    float bh[3] = {fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z))};
+    int cur = ~i, l = i, r = i;
+    for (int guard = 0; guard < 2 * n + 64; ++guard) {
+      bool as_left;
+      if (l == 0) as_left = true;
+      else if (r == n - 1) as_left = false;
+      else as_left = hb_at(r) < hb_at(l - 1);
+      const int p = as_left ? r : l - 1;
+      // final node fields straight to global memory
+      BvhNode *np = nodes + p;
+      if (as_left) {
+        np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+        reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
+        np->kids.x = cur;
+      } else {
+        np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+        reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
+        np->kids.y = cur;
+      }
+      // this child's box for the sibling, in the parent's owner CTA
+      const int owner = p / cap, slot = p - owner * cap;
+      const int side = as_left ? 0 : 1;
+      float *nb = cluster.map_shared_rank(P.nbox, owner);
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        nb[(side * 6 + x) * cap + slot] = bl[x];
+        nb[(side * 6 + 3 + x) * cap + slot] = bh[x];
+      }
+      const int other = exch_acq_rel_cluster(cluster.map_shared_rank(&P.nflag[slot], owner), as_left ? l : r);
+      if (other < 0) break;  // first to arrive: the sibling's thread goes on
+#pragma unroll
+      for (int x = 0; x < 3; ++x) {
+        bl[x] = fminf(bl[x], nb[((1 - side) * 6 + x) * cap + slot]);
+        bh[x] = fmaxf(bh[x], nb[((1 - side) * 6 + 3 + x) * cap + slot]);
+      }
+      if (as_left) r = other; else l = other;
+      cur = p;
+      if (l == 0 && r == n - 1) {
+        hdr->root = p;
+        hdr->n = n;
+        for (int x = 0; x < 3; ++x) { hdr->lo[x] = bl[x]; hdr->hi[x] = bh[x]; }
+        break;
+      }
+    }
+  }
+  // no CTA may leave while others still touch its shared memory
+  cluster.sync();
+}
+
+int g_cluster_ok[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
+
+size_t smem_bytes(int cap) {
+  const size_t sortR = (size_t)2 * cap + 256 * kCnt + 16 * 256;
+  const size_t hierR = (size_t)13 * cap + (cap + 3) / 4;
+  return 4 * ((size_t)2 * cap + (sortR > hierR ? sortR : hierR));
+}
+
+}  // namespace
+
+int cluster_build_capacity() { return 16 * kMaxCap; }
+
+cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used) {
+  *used = false;
+  const int n = (int)s.nt;
+  if (n < 2 || n > 16 * kMaxCap) return cudaSuccess;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  if (dev < 0 || dev >= 64) return cudaSuccess;
+  const int C = n <= 8 * 2048 ? 8 : 16;
+  const int cap = (n + C - 1) / C;
+  const size_t smem = smem_bytes(cap);
+  if (g_cluster_ok[dev] == 0) {
+    g_cluster_ok[dev] = -1;
+    if (cudaFuncSetAttribute(k_build_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             (int)smem_bytes(kMaxCap)) == cudaSuccess &&
+        cudaFuncSetAttribute(k_build_cluster, cudaFuncAttributeNonPortableClusterSizeAllowed, 1) == cudaSuccess) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = 16;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(16);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem_bytes(kMaxCap);
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nclusters = 0;
+      if (cudaOccupancyMaxActiveClusters(&nclusters, k_build_cluster, &cfg) == cudaSuccess && nclusters > 0)
+        g_cluster_ok[dev] = 1;
+    }
+    cudaGetLastError();  // clear a refused query
+  }
+  if (g_cluster_ok[dev] != 1) return cudaSuccess;
+  cudaLaunchConfig_t cfg = {};
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeClusterDimension;
+  attr[0].val.clusterDim.x = C;
+  attr[0].val.clusterDim.y = 1;
+  attr[0].val.clusterDim.z = 1;
+  cfg.gridDim = dim3(C);
+  cfg.blockDim = dim3(kThreads);
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  e = cudaLaunchKernelEx(&cfg, k_build_cluster, (const float *)s.V, (const int32_t *)s.F, n, cap, s.nodes, s.tris,
+                         s.keys, s.ids, s.hdr);
+  if (e == cudaSuccess) *used = true;
+  return e;
+}
+
+}  // namespace rr

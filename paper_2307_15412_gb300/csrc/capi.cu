@@ -36,6 +36,10 @@ struct rr_ctx {
   int64_t partials_cap = 0;        // floats
   float *if_tmp = nullptr;         // internal IF cube for rr_run_frame(if_out = NULL)
   int64_t if_tmp_cap = 0;          // floats
+  // stage timing ring: 5 events per slot
+  std::vector<cudaEvent_t> tev;
+  std::vector<char> tev_used;
+  int tslots = 0, tnext = 0;
   char msg[512] = "ok";
 };
 
@@ -220,6 +224,7 @@ rr_status rr_destroy(rr_ctx *c) {
   if (c->h_roots) cudaFreeHost(c->h_roots);
   if (c->partials) cudaFree(c->partials);
   if (c->if_tmp) cudaFree(c->if_tmp);
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return RR_OK;
@@ -282,7 +287,7 @@ rr_status rr_scene_upload(rr_ctx *c, int scene, const float *verts, int64_t nv, 
     if (!s) return fail(c, RR_ENOMEM, "host allocation");
     c->scenes[scene] = s;
     RR_CUDA(c, cudaMalloc((void **)&s->hdr, sizeof(rr::BvhHeader)), "header");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_count, sizeof(uint32_t)), "hit counter");
+    RR_CUDA(c, cudaMalloc((void **)&s->hit_count, 2 * sizeof(uint32_t)), "hit counter");
   }
   if (nv > s->cap_nv || !s->V) {
     if (s->V) cudaFree(s->V);
@@ -442,23 +447,68 @@ rr_status rr_range_doppler(rr_ctx *c, const float *if_in, int n_rx, int n_chirps
   return RR_OK;
 }
 
+rr_status rr_timing_enable(rr_ctx *c, int n_slots) {
+  if (!c) return RR_EINVAL;
+  if (n_slots < 0 || n_slots > 1 << 20) return fail(c, RR_EINVAL, "n_slots out of range");
+  DeviceGuard g(c->device);
+  for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  c->tev.clear();
+  c->tev_used.assign(n_slots, 0);
+  c->tslots = 0;
+  c->tnext = 0;
+  for (int i = 0; i < 5 * n_slots; ++i) {
+    cudaEvent_t e;
+    RR_CUDA(c, cudaEventCreate(&e), "timing events");
+    c->tev.push_back(e);
+  }
+  c->tslots = n_slots;
+  return RR_OK;
+}
+
+rr_status rr_timing_read(rr_ctx *c, int slot, float *ms) {
+  if (!c || !ms) return RR_EINVAL;
+  if (slot < 0 || slot >= c->tslots) return fail(c, RR_EINVAL, "slot out of range");
+  if (!c->tev_used[slot]) return fail(c, RR_ENOTREADY, "timing slot %d not recorded", slot);
+  DeviceGuard g(c->device);
+  cudaEvent_t *e = &c->tev[5 * slot];
+  RR_CUDA(c, cudaEventSynchronize(e[4]), "timing read");
+  RR_CUDA(c, cudaEventElapsedTime(&ms[0], e[0], e[1]), "timing read");
+  RR_CUDA(c, cudaEventElapsedTime(&ms[1], e[1], e[2]), "timing read");
+  RR_CUDA(c, cudaEventElapsedTime(&ms[2], e[2], e[3]), "timing read");
+  RR_CUDA(c, cudaEventElapsedTime(&ms[3], e[3], e[4]), "timing read");
+  RR_CUDA(c, cudaEventElapsedTime(&ms[4], e[0], e[4]), "timing read");
+  return RR_OK;
+}
+
 rr_status rr_run_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_raygrid *grid, rr_synth_variant variant,
                        int window, float *if_out, float *rd_out) {
   if (!c) return RR_EINVAL;
   if (!if_out && !rd_out) return fail(c, RR_EINVAL, "need if_out or rd_out");
   rr_status st;
   if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  cudaEvent_t *ev = nullptr;
+  if (c->tslots > 0) {
+    const int slot = c->tnext;
+    c->tnext = (c->tnext + 1) % c->tslots;
+    c->tev_used[slot] = 1;
+    ev = &c->tev[5 * slot];
+  }
+  DeviceGuard g(c->device);
+  if (ev) RR_CUDA(c, cudaEventRecord(ev[0], c->stream), "timing");
   if ((st = rr_build_bvh(c, scene)) != RR_OK) return st;
+  if (ev) RR_CUDA(c, cudaEventRecord(ev[1], c->stream), "timing");
   if ((st = rr_trace_frame(c, scene, radar, grid, 0, nullptr)) != RR_OK) return st;
+  if (ev) RR_CUDA(c, cudaEventRecord(ev[2], c->stream), "timing");
   float *ifb = if_out;
   if (!ifb) {
-    DeviceGuard g(c->device);
     const int64_t need = (int64_t)2 * radar->n_rx * radar->n_chirps * radar->n_samples;
     RR_CUDA(c, grow(c->if_tmp, c->if_tmp_cap, need), "frame IF buffer");
     ifb = c->if_tmp;
   }
   if ((st = rr_synth_if(c, scene, radar, variant, ifb)) != RR_OK) return st;
+  if (ev) RR_CUDA(c, cudaEventRecord(ev[3], c->stream), "timing");
   if (rd_out) st = rr_range_doppler(c, ifb, radar->n_rx, radar->n_chirps, radar->n_samples, window, rd_out);
+  if (ev) RR_CUDA(c, cudaEventRecord(ev[4], c->stream), "timing");
   return st;
 }
 

@@ -1,11 +1,13 @@
 // rd.cu -- range-Doppler map of the IF cube.
 //
-// One CTA per receive channel holds the whole M x N chirp/sample plane in
-// shared memory (rows padded by one complex against bank conflicts) and
-// runs in-place radix-2 decimation-in-time FFTs with the + kernel: first
-// along samples (range), then along chirps (Doppler).  The window is
-// applied at load, the Doppler axis is fft-shifted at store.  Twiddles come
-// from sincospi on exact dyadic arguments.
+// Two passes of in-place radix-2 decimation-in-time FFTs with the + kernel
+// in shared memory, spread over many CTAs:
+//   k_rd_rows  one CTA per (channel, chirp) row: window, FFT over the N
+//              samples (range), written to the output cube;
+//   k_rd_cols  one CTA per (channel, group of columns): FFT over the M
+//              chirps (Doppler) of each column, in place, with the Doppler
+//              axis fft-shifted on the way out.
+// Twiddles come from sincospi on exact dyadic arguments.
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -14,8 +16,6 @@
 namespace rr {
 namespace {
 
-constexpr int kRdThreads = 1024;
-
 __device__ __forceinline__ int bitrev(int x, int bits) { return bits == 0 ? 0 : (int)(__brev((unsigned)x) >> (32 - bits)); }
 
 __device__ __forceinline__ float hann(int i, int L) {
@@ -23,63 +23,70 @@ __device__ __forceinline__ float hann(int i, int L) {
   return 0.5f - 0.5f * cospif(2.f * (float)i / (float)(L - 1));
 }
 
-__global__ void __launch_bounds__(kRdThreads)
-k_range_doppler(const float2 *__restrict__ in, int M, int N, int lm, int ln, int window,
-                float2 *__restrict__ out) {
-  extern __shared__ float2 sm[];
-  const int j = blockIdx.x;
-  const int ld = N + 1;
-  const float2 *src = in + (int64_t)j * M * N;
-  const int tot = M * N;
-  // load rows in bit-reversed sample order, windowed
-  for (int e = threadIdx.x; e < tot; e += kRdThreads) {
-    const int m = e / N, n = e - m * N;
+__device__ __forceinline__ void butterfly(float2 *a, float2 *b, int pos, int len) {
+  float s, c;
+  sincospif(2.f * (float)pos / (float)len, &s, &c);
+  const float2 u = *a, x = *b;
+  const float2 v = make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
+  *a = make_float2(u.x + v.x, u.y + v.y);
+  *b = make_float2(u.x - v.x, u.y - v.y);
+}
+
+__global__ void k_rd_rows(const float2 *__restrict__ in, int M, int N, int ln, int window, float2 *__restrict__ out) {
+  extern __shared__ float2 row[];
+  const int rix = blockIdx.x;  // j * M + m
+  const int m = rix % M;
+  const float wm = window == 1 ? hann(m, M) : 1.f;
+  const float2 *src = in + (int64_t)rix * N;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) {
     float2 v = src[e];
     if (window == 1) {
-      const float w = hann(n, N) * hann(m, M);
+      const float w = wm * hann(e, N);
       v.x *= w;
       v.y *= w;
     }
-    sm[bitrev(m, lm) * ld + bitrev(n, ln)] = v;  // rows also bit-reversed for the Doppler pass
+    row[bitrev(e, ln)] = v;
   }
   __syncthreads();
-  // range FFT along n on every row
   for (int len = 2; len <= N; len <<= 1) {
     const int half = len >> 1;
-    for (int b = threadIdx.x; b < M * (N >> 1); b += kRdThreads) {
-      const int row = b / (N >> 1), q = b - row * (N >> 1);
-      const int grp = q / half, pos = q - grp * half;
-      const int i0 = row * ld + grp * len + pos, i1 = i0 + half;
-      float s, c;
-      sincospif(2.f * (float)pos / (float)len, &s, &c);
-      const float2 u = sm[i0], x = sm[i1];
-      const float2 v = make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
-      sm[i0] = make_float2(u.x + v.x, u.y + v.y);
-      sm[i1] = make_float2(u.x - v.x, u.y - v.y);
+    for (int b = threadIdx.x; b < (N >> 1); b += blockDim.x) {
+      const int grp = b / half, pos = b - grp * half;
+      const int i0 = grp * len + pos;
+      butterfly(&row[i0], &row[i0 + half], pos, len);
     }
     __syncthreads();
   }
-  // Doppler FFT along m on every column
+  float2 *dst = out + (int64_t)rix * N;
+  for (int e = threadIdx.x; e < N; e += blockDim.x) dst[e] = row[e];
+}
+
+__global__ void k_rd_cols(float2 *__restrict__ io, int M, int N, int lm, int CW) {
+  extern __shared__ float2 col[];  // [M][CW]
+  const int groups = (N + CW - 1) / CW;
+  const int j = blockIdx.x / groups;
+  const int c0 = (blockIdx.x % groups) * CW;
+  const int cw = min(CW, N - c0);
+  float2 *base = io + (int64_t)j * M * N + c0;
+  for (int e = threadIdx.x; e < M * cw; e += blockDim.x) {
+    const int m = e / cw, c = e - m * cw;
+    col[bitrev(m, lm) * CW + c] = base[(int64_t)m * N + c];
+  }
+  __syncthreads();
   for (int len = 2; len <= M; len <<= 1) {
     const int half = len >> 1;
-    for (int b = threadIdx.x; b < N * (M >> 1); b += kRdThreads) {
-      const int col = b % N, q = b / N;
+    for (int b = threadIdx.x; b < (M >> 1) * cw; b += blockDim.x) {
+      const int q = b / cw, c = b - q * cw;
       const int grp = q / half, pos = q - grp * half;
-      const int i0 = (grp * len + pos) * ld + col, i1 = i0 + half * ld;
-      float s, c;
-      sincospif(2.f * (float)pos / (float)len, &s, &c);
-      const float2 u = sm[i0], x = sm[i1];
-      const float2 v = make_float2(x.x * c - x.y * s, x.x * s + x.y * c);
-      sm[i0] = make_float2(u.x + v.x, u.y + v.y);
-      sm[i1] = make_float2(u.x - v.x, u.y - v.y);
+      const int i0 = grp * len + pos;
+      butterfly(&col[i0 * CW + c], &col[(i0 + half) * CW + c], pos, len);
     }
     __syncthreads();
   }
-  float2 *dst = out + (int64_t)j * M * N;
-  for (int e = threadIdx.x; e < tot; e += kRdThreads) {
-    const int q = e / N, k = e - q * N;
+  for (int e = threadIdx.x; e < M * cw; e += blockDim.x) {
+    const int q = e / cw, c = e - q * cw;
     const int qs = (q + (M >> 1)) & (M - 1);
-    dst[qs * N + k] = sm[q * ld + k];
+    base[(int64_t)qs * N + c] = col[q * CW + c];
   }
 }
 
@@ -93,15 +100,18 @@ int ilog2(int x) {
 
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st) {
-  const size_t smem = (size_t)M * (N + 1) * sizeof(float2);
-  static size_t attr = 0;
-  if (smem > 48 * 1024 && smem > attr) {
-    cudaError_t e = cudaFuncSetAttribute(k_range_doppler, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr = smem;
-  }
-  k_range_doppler<<<n_rx, kRdThreads, smem, st>>>(reinterpret_cast<const float2 *>(in), M, N, ilog2(M), ilog2(N),
-                                                  window, reinterpret_cast<float2 *>(out));
+  const int rthreads = N / 2 < 32 ? 32 : (N / 2 > 512 ? 512 : N / 2);
+  k_rd_rows<<<n_rx * M, rthreads, N * sizeof(float2), st>>>(reinterpret_cast<const float2 *>(in), M, N, ilog2(N),
+                                                            window, reinterpret_cast<float2 *>(out));
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess || M == 1) return e;
+  int CW = 4096 / M;  // <= 32 KB of shared memory per CTA
+  if (CW > 32) CW = 32;
+  if (CW < 1) CW = 1;
+  if (CW > N) CW = N;
+  const int groups = (N + CW - 1) / CW;
+  k_rd_cols<<<n_rx * groups, 256, (size_t)M * CW * sizeof(float2), st>>>(reinterpret_cast<float2 *>(out), M, N,
+                                                                         ilog2(M), CW);
   return cudaGetLastError();
 }
 

@@ -60,7 +60,7 @@ struct SceneDev {
   int64_t hit_cap = 0;           // capacity of the arrays below
   int32_t hit_nrx = 0;           // n_rx of the last trace
   int64_t hit_used_cap = 0;      // capacity used by the last trace
-  uint32_t *hit_count = nullptr; // device counter (true count, may exceed capacity)
+  uint32_t *hit_count = nullptr; // [0] hit count (true count, may exceed capacity), [1] ray-tile counter
   int32_t *hit_ray = nullptr;    // [cap]
   int32_t *hit_tri = nullptr;    // [cap] original triangle id
   int32_t *hit_pos = nullptr;    // [cap] Morton position of the triangle
@@ -94,6 +94,10 @@ struct GridDev {
 
 // ---- launchers (each returns the launch status) ----
 cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st);
+// Single-launch cluster builder for 2 <= n <= cluster_build_capacity();
+// sets *used = false (and launches nothing) when it does not apply.
+cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used);
+int cluster_build_capacity();
 cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
                          uint32_t *err, cudaStream_t st);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,

@@ -25,8 +25,7 @@
 namespace rr {
 namespace {
 
-constexpr int kTileAz = 16, kTileEl = 8;  // rays per CTA (4 warps of 8 x 4 rays)
-constexpr int kTraceThreads = kTileAz * kTileEl;
+constexpr int kTraceThreads = 128;        // 4 warps, each tracing 8 x 4 ray tiles
 constexpr float kBoxSlack = 1.0000004f;   // covers FP32 rounding of the slab test
 
 struct RayPre {
@@ -91,105 +90,171 @@ __device__ __forceinline__ void tri_test(const RayPre &r, const float4 *__restri
   }
 }
 
+// Conservative index rectangle [i0, i1) x [j0, j1) of the rays that can meet
+// the scene box: the box corners in the radar frame bound azimuth exactly
+// (x/z is extremal at a corner of a convex set in front of the radar) and
+// elevation through y / sqrt(x^2 + z^2) with the radial distance bounded over
+// the box.  Two cells of margin absorb FP32 rounding.  If the box reaches
+// behind the radar's boresight plane the whole grid is used.
+__device__ void ray_rect(const BvhHeader *hdr, const RadarDev &r, const GridDev &g, int *rect) {
+  rect[0] = 0; rect[1] = g.n_az; rect[2] = 0; rect[3] = g.n_el;
+  float pmin[3], pmax[3];
+  for (int k = 0; k < 3; ++k) { pmin[k] = hdr->lo[k] - r.txf[k]; pmax[k] = hdr->hi[k] - r.txf[k]; }
+  float xr[8], yr[8], zr[8];
+  for (int c = 0; c < 8; ++c) {
+    const float p[3] = {(c & 1) ? pmax[0] : pmin[0], (c & 2) ? pmax[1] : pmin[1], (c & 4) ? pmax[2] : pmin[2]};
+    // world -> radar frame: R^T p
+    xr[c] = r.Rf[0] * p[0] + r.Rf[3] * p[1] + r.Rf[6] * p[2];
+    yr[c] = r.Rf[1] * p[0] + r.Rf[4] * p[1] + r.Rf[7] * p[2];
+    zr[c] = r.Rf[2] * p[0] + r.Rf[5] * p[1] + r.Rf[8] * p[2];
+    if (!(zr[c] > 1e-6f)) return;
+  }
+  float azl = INFINITY, azh = -INFINITY, rho_max = 0.f, ylo = INFINITY, yhi = -INFINITY;
+  float xlo = INFINITY, xhi = -INFINITY, zlo = INFINITY;
+  for (int c = 0; c < 8; ++c) {
+    const float az = atan2f(xr[c], zr[c]);
+    azl = fminf(azl, az); azh = fmaxf(azh, az);
+    rho_max = fmaxf(rho_max, sqrtf(xr[c] * xr[c] + zr[c] * zr[c]));
+    ylo = fminf(ylo, yr[c]); yhi = fmaxf(yhi, yr[c]);
+    xlo = fminf(xlo, xr[c]); xhi = fmaxf(xhi, xr[c]);
+    zlo = fminf(zlo, zr[c]);
+  }
+  // the rotated box is enclosed by the axis-aligned box of its corners in the
+  // radar frame; its distance to the y axis is at least the (x, z) distance
+  // from the origin to that box's (x, z) rectangle
+  const float dx = (xlo > 0.f) ? xlo : ((xhi < 0.f) ? -xhi : 0.f);
+  const float rho_min = sqrtf(dx * dx + zlo * zlo);
+  const float ell = (ylo >= 0.f) ? atanf(ylo / rho_max) : atanf(ylo / rho_min);
+  const float elh = (yhi >= 0.f) ? atanf(yhi / rho_min) : atanf(yhi / rho_max);
+  const float fa0 = (azl + (float)g.half_az) / g.daz_f - 0.5f, fa1 = (azh + (float)g.half_az) / g.daz_f - 0.5f;
+  const float fe0 = (ell + (float)g.half_el) / g.del_f - 0.5f, fe1 = (elh + (float)g.half_el) / g.del_f - 0.5f;
+  rect[0] = max(0, (int)floorf(fa0) - 2);
+  rect[1] = min(g.n_az, (int)ceilf(fa1) + 3);
+  rect[2] = max(0, (int)floorf(fe0) - 2);
+  rect[3] = min(g.n_el, (int)ceilf(fe1) + 3);
+  if (rect[1] < rect[0]) rect[1] = rect[0];
+  if (rect[3] < rect[2]) rect[3] = rect[2];
+}
+
+// Persistent traversal: warps take the 8 x 4 ray tiles of the candidate
+// rectangle in a fixed interleaved order (a shared tile counter serialised
+// on one L2 address and cost more than the traversal), so the few tiles that
+// contain the object are spread over every SM.
 __global__ void __launch_bounds__(kTraceThreads)
 k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
         const BvhHeader *__restrict__ hdr, const RadarDev r, const GridDev g, int64_t cap,
-        uint32_t *__restrict__ count, int32_t *__restrict__ hit_ray, int32_t *__restrict__ hit_tri,
+        uint32_t *__restrict__ counters, int32_t *__restrict__ hit_ray, int32_t *__restrict__ hit_tri,
         int32_t *__restrict__ hit_pos, float *__restrict__ hit_t, uint32_t *__restrict__ err) {
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int i_az = blockIdx.x * kTileAz + (warp & 1) * 8 + (lane & 7);
-  const int i_el = blockIdx.y * kTileEl + (warp >> 1) * 4 + (lane >> 3);
-  const bool valid = i_az < g.n_az && i_el < g.n_el;
-
-  float best_t = INFINITY;
-  int best_pos = -1, best_id = 0x7fffffff;
+  __shared__ int rect[4];
   const int n = hdr->n;
-  if (valid && n > 0) {
-    float sa, ca, se, ce;
-    sincospif(fmaf((float)i_az, g.daz_pi, g.az0_pi), &sa, &ca);
-    sincospif(fmaf((float)i_el, g.del_pi, g.el0_pi), &se, &ce);
-    const float ur[3] = {ce * sa, se, ce * ca};
-    float d[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) d[k] = r.Rf[3 * k] * ur[0] + r.Rf[3 * k + 1] * ur[1] + r.Rf[3 * k + 2] * ur[2];
-    RayPre rp;
-    rp.ox = r.txf[0]; rp.oy = r.txf[1]; rp.oz = r.txf[2];
-    rp.ix = safe_inv(d[0]); rp.iy = safe_inv(d[1]); rp.iz = safe_inv(d[2]);
-    int kz = 0;
-    if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
-    if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
-    int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
-    if (d[kz] < 0.f) { const int tmp = kx; kx = ky; ky = tmp; }
-    rp.kx = kx; rp.ky = ky; rp.kz = kz;
-    rp.Sx = d[kx] / d[kz];
-    rp.Sy = d[ky] / d[kz];
-    rp.Sz = 1.0f / d[kz];
+  if (n <= 0) return;
+  if (threadIdx.x == 0) ray_rect(hdr, r, g, rect);
+  __syncthreads();
+  const int lane = threadIdx.x & 31;
+  const int tiles_az = (rect[1] - rect[0] + 7) / 8, tiles_el = (rect[3] - rect[2] + 3) / 4;
+  const int ntiles = tiles_az * tiles_el;
+  const int root = hdr->root;
+  const float blo[3] = {hdr->lo[0], hdr->lo[1], hdr->lo[2]}, bhi[3] = {hdr->hi[0], hdr->hi[1], hdr->hi[2]};
+  uint32_t *count = counters;
 
-    const float t_root = box_entry(rp, hdr->lo[0], hdr->hi[0], hdr->lo[1], hdr->hi[1], hdr->lo[2], hdr->hi[2], INFINITY);
-    const int root = hdr->root;
-    if (t_root < INFINITY) {
-      if (root < 0) {
-        tri_test(rp, tris, ~root, best_t, best_pos, best_id);
-      } else {
-        int stack_node[kStackDepth];
-        float stack_t[kStackDepth];
-        int sp = 0;
-        int node = root;
-        while (true) {
-          if ((unsigned)node >= (unsigned)(n - 1)) { atomicOr(err, ERR_BAD_INPUT); break; }
-          const float4 lxy = __ldg(&nodes[node].lxy);
-          const float4 rxy = __ldg(&nodes[node].rxy);
-          const float4 lrz = __ldg(&nodes[node].lrz);
-          const int4 kids = __ldg(&nodes[node].kids);
-          const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
-          const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
-          bool hl = tl < INFINITY, hr = tr < INFINITY;
-          if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
-            atomicOr(err, ERR_BAD_INPUT);
-            break;
-          }
-          if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
-          if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
-          if (hl && hr) {
-            const bool lnear = tl <= tr;
-            if (sp == kStackDepth) { atomicOr(err, ERR_STACK_OVERFLOW); break; }
-            stack_node[sp] = lnear ? kids.y : kids.x;
-            stack_t[sp] = lnear ? tr : tl;
-            ++sp;
-            node = lnear ? kids.x : kids.y;
-          } else if (hl) {
-            node = kids.x;
-          } else if (hr) {
-            node = kids.y;
-          } else {
-            bool found = false;
-            while (sp > 0) {
-              --sp;
-              if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
+  const int gw = blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5);
+  const int nw = gridDim.x * (kTraceThreads / 32);
+  for (int tile = gw; tile < ntiles; tile += nw) {
+    const int i_az = rect[0] + (tile % tiles_az) * 8 + (lane & 7);
+    const int i_el = rect[2] + (tile / tiles_az) * 4 + (lane >> 3);
+    const bool valid = i_az < rect[1] && i_el < rect[3];
+
+    float best_t = INFINITY;
+    int best_pos = -1, best_id = 0x7fffffff;
+    if (valid) {
+      float sa, ca, se, ce;
+      sincospif(fmaf((float)i_az, g.daz_pi, g.az0_pi), &sa, &ca);
+      sincospif(fmaf((float)i_el, g.del_pi, g.el0_pi), &se, &ce);
+      const float ur[3] = {ce * sa, se, ce * ca};
+      float d[3];
+#pragma unroll
+      for (int k = 0; k < 3; ++k) d[k] = r.Rf[3 * k] * ur[0] + r.Rf[3 * k + 1] * ur[1] + r.Rf[3 * k + 2] * ur[2];
+      RayPre rp;
+      rp.ox = r.txf[0]; rp.oy = r.txf[1]; rp.oz = r.txf[2];
+      rp.ix = safe_inv(d[0]); rp.iy = safe_inv(d[1]); rp.iz = safe_inv(d[2]);
+      int kz = 0;
+      if (fabsf(d[1]) > fabsf(d[kz])) kz = 1;
+      if (fabsf(d[2]) > fabsf(d[kz])) kz = 2;
+      int kx = kz == 2 ? 0 : kz + 1, ky = kx == 2 ? 0 : kx + 1;
+      if (d[kz] < 0.f) { const int tmp = kx; kx = ky; ky = tmp; }
+      rp.kx = kx; rp.ky = ky; rp.kz = kz;
+      rp.Sx = d[kx] / d[kz];
+      rp.Sy = d[ky] / d[kz];
+      rp.Sz = 1.0f / d[kz];
+
+      const float t_root = box_entry(rp, blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2], INFINITY);
+      if (t_root < INFINITY) {
+        if (root < 0) {
+          tri_test(rp, tris, ~root, best_t, best_pos, best_id);
+        } else {
+          int stack_node[kStackDepth];
+          float stack_t[kStackDepth];
+          int sp = 0;
+          int node = root;
+          // a tree of n - 1 internal nodes is walked in at most n - 1 node
+          // visits; more means a malformed tree, reported instead of looping
+          for (int visits = 0;; ++visits) {
+            if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) { atomicOr(err, ERR_BAD_INPUT); break; }
+            const float4 lxy = __ldg(&nodes[node].lxy);
+            const float4 rxy = __ldg(&nodes[node].rxy);
+            const float4 lrz = __ldg(&nodes[node].lrz);
+            const int4 kids = __ldg(&nodes[node].kids);
+            const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
+            const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
+            bool hl = tl < INFINITY, hr = tr < INFINITY;
+            if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
+              atomicOr(err, ERR_BAD_INPUT);
+              break;
             }
-            if (!found) break;
+            if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
+            if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
+            if (hl && hr) {
+              const bool lnear = tl <= tr;
+              if (sp == kStackDepth) { atomicOr(err, ERR_STACK_OVERFLOW); break; }
+              stack_node[sp] = lnear ? kids.y : kids.x;
+              stack_t[sp] = lnear ? tr : tl;
+              ++sp;
+              node = lnear ? kids.x : kids.y;
+            } else if (hl) {
+              node = kids.x;
+            } else if (hr) {
+              node = kids.y;
+            } else {
+              bool found = false;
+              while (sp > 0) {
+                --sp;
+                if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
+              }
+              if (!found) break;
+            }
           }
         }
       }
     }
-  }
-  // warp-aggregated append
-  const bool has = best_pos >= 0;
-  const uint32_t mask = __ballot_sync(0xffffffffu, has);
-  if (mask == 0u) return;
-  const int leader = __ffs(mask) - 1;
-  uint32_t base = 0;
-  if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
-  base = __shfl_sync(0xffffffffu, base, leader);
-  if (has) {
-    const int64_t slot = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-    if (slot < cap) {
-      hit_ray[slot] = i_el * g.n_az + i_az;
-      hit_tri[slot] = best_id;
-      hit_pos[slot] = best_pos;
-      hit_t[slot] = best_t;
-    } else {
-      atomicOr(err, ERR_HIT_OVERFLOW);
+    // warp-aggregated append
+    const bool has = best_pos >= 0;
+    const uint32_t mask = __ballot_sync(0xffffffffu, has);
+    if (mask != 0u) {
+      const int leader = __ffs(mask) - 1;
+      uint32_t base = 0;
+      if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+      base = __shfl_sync(0xffffffffu, base, leader);
+      if (has) {
+        const int64_t slot = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
+        if (slot < cap) {
+          hit_ray[slot] = i_el * g.n_az + i_az;
+          hit_tri[slot] = best_id;
+          hit_pos[slot] = best_pos;
+          hit_t[slot] = best_t;
+        } else {
+          atomicOr(err, ERR_HIT_OVERFLOW);
+        }
+      }
     }
   }
 }
@@ -258,16 +323,14 @@ k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const
 
 cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
                          uint32_t *err, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, sizeof(uint32_t), st);
+  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, 2 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
-  dim3 grid((g.n_az + kTileAz - 1) / kTileAz, (g.n_el + kTileEl - 1) / kTileEl);
-  k_trace<<<grid, kTraceThreads, 0, st>>>(s.nodes, s.tris, s.hdr, r, g, cap, s.hit_count, s.hit_ray,
-                                         s.hit_tri, s.hit_pos, s.hit_t, err);
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(s.nodes, s.tris, s.hdr, r, g, cap, s.hit_count, s.hit_ray,
+                                            s.hit_tri, s.hit_pos, s.hit_t, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  int sms = 152;
-  int dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t want = (cap + 127) / 128;
   const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
   const float3 vel = make_float3(s.vel[0], s.vel[1], s.vel[2]);

@@ -63,6 +63,8 @@ SIGNATURES = {
     "rr_run_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I, _I, _P, _P]),
     "rr_get_bvh": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "rr_synth_if_from_hits_noalloc": (_I, [ctypes.POINTER(rr_radar), _I, _I64, _P, _P, _P, _P, _P]),
+    "rr_timing_enable": (_I, [_P, _I]),
+    "rr_timing_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_float)]),
 }
 
 _lib = None
@@ -89,7 +91,9 @@ class RRError(RuntimeError):
         self.status = status
 
 
-def make_radar(r: Radar) -> rr_radar:
+def make_radar(r) -> rr_radar:
+    if isinstance(r, rr_radar):
+        return r
     s = rr_radar()
     for i, v in enumerate(r.frame):
         s.frame[i] = float(v)
@@ -109,7 +113,9 @@ def make_radar(r: Radar) -> rr_radar:
     return s
 
 
-def make_grid(g: RayGrid) -> rr_raygrid:
+def make_grid(g) -> rr_raygrid:
+    if isinstance(g, rr_raygrid):
+        return g
     return rr_raygrid(int(g.n_az), int(g.n_el), float(g.half_az), float(g.half_el))
 
 
@@ -223,6 +229,15 @@ class Context:
         rs, gs = make_radar(radar), make_grid(grid)
         self._check(self.lib.rr_run_frame(self.h, scene, ctypes.byref(rs), ctypes.byref(gs), int(variant),
                                           int(window), _ptr(if_out), _ptr(rd_out)))
+
+    def timing_enable(self, n_slots: int):
+        self._check(self.lib.rr_timing_enable(self.h, int(n_slots)))
+
+    def timing_read(self, slot: int):
+        """(build_bvh, trace_frame, synth_if, range_doppler, frame) in ms."""
+        out = (ctypes.c_float * 5)()
+        self._check(self.lib.rr_timing_read(self.h, int(slot), out))
+        return tuple(float(x) for x in out)
 
     def get_bvh(self, scene: int, codes=None, ids=None, left=None, right=None, boxes=None):
         box = [None]
