@@ -166,6 +166,8 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
 
     float best_t = INFINITY;
     int best_pos = -1, best_id = 0x7fffffff;
+    RayPre rp;
+    bool active = false;  // this lane still walks the tree
     if (valid) {
       float sa, ca, se, ce;
       sincospif(fmaf((float)i_az, g.daz_pi, g.az0_pi), &sa, &ca);
@@ -174,7 +176,6 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
       float d[3];
 #pragma unroll
       for (int k = 0; k < 3; ++k) d[k] = r.Rf[3 * k] * ur[0] + r.Rf[3 * k + 1] * ur[1] + r.Rf[3 * k + 2] * ur[2];
-      RayPre rp;
       rp.ox = r.txf[0]; rp.oy = r.txf[1]; rp.oz = r.txf[2];
       rp.ix = safe_inv(d[0]); rp.iy = safe_inv(d[1]); rp.iz = safe_inv(d[2]);
       int kz = 0;
@@ -189,51 +190,63 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
 
       const float t_root = box_entry(rp, blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2], INFINITY);
       if (t_root < INFINITY) {
-        if (root < 0) {
-          tri_test(rp, tris, ~root, best_t, best_pos, best_id);
-        } else {
-          int stack_node[kStackDepth];
-          float stack_t[kStackDepth];
-          int sp = 0;
-          int node = root;
-          // a tree of n - 1 internal nodes is walked in at most n - 1 node
-          // visits; more means a malformed tree, reported instead of looping
-          for (int visits = 0;; ++visits) {
-            if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) { atomicOr(err, ERR_BAD_INPUT); break; }
-            const float4 lxy = __ldg(&nodes[node].lxy);
-            const float4 rxy = __ldg(&nodes[node].rxy);
-            const float4 lrz = __ldg(&nodes[node].lrz);
-            const int4 kids = __ldg(&nodes[node].kids);
-            const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
-            const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
-            bool hl = tl < INFINITY, hr = tr < INFINITY;
-            if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
-              atomicOr(err, ERR_BAD_INPUT);
-              break;
-            }
-            if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
-            if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
-            if (hl && hr) {
-              const bool lnear = tl <= tr;
-              if (sp == kStackDepth) { atomicOr(err, ERR_STACK_OVERFLOW); break; }
-              stack_node[sp] = lnear ? kids.y : kids.x;
-              stack_t[sp] = lnear ? tr : tl;
-              ++sp;
-              node = lnear ? kids.x : kids.y;
-            } else if (hl) {
-              node = kids.x;
-            } else if (hr) {
-              node = kids.y;
-            } else {
-              bool found = false;
-              while (sp > 0) {
-                --sp;
-                if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
-              }
-              if (!found) break;
-            }
-          }
+        if (root < 0) tri_test(rp, tris, ~root, best_t, best_pos, best_id);
+        else active = true;
+      }
+    }
+    // Warp-uniform traversal: every iteration each still-active lane takes
+    // one node step and the warp reconverges at the vote, so a warp costs
+    // the longest of its rays' walks, not the sum of its lanes' walks (a
+    // per-lane loop lets divergent lanes run their iterations one after the
+    // other).  A tree of n - 1 internal nodes is walked in at most n - 1
+    // steps; more means a malformed tree, reported instead of looping.
+    int stack_node[kStackDepth];
+    float stack_t[kStackDepth];
+    int sp = 0, node = root, visits = 0;
+    while (__any_sync(0xffffffffu, active)) {
+      if (!active) continue;
+      if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) {
+        atomicOr(err, ERR_BAD_INPUT);
+        active = false;
+        continue;
+      }
+      ++visits;
+      const float4 lxy = __ldg(&nodes[node].lxy);
+      const float4 rxy = __ldg(&nodes[node].rxy);
+      const float4 lrz = __ldg(&nodes[node].lrz);
+      const int4 kids = __ldg(&nodes[node].kids);
+      const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
+      const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
+      bool hl = tl < INFINITY, hr = tr < INFINITY;
+      if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
+        atomicOr(err, ERR_BAD_INPUT);
+        active = false;
+        continue;
+      }
+      if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
+      if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
+      if (hl && hr) {
+        const bool lnear = tl <= tr;
+        if (sp == kStackDepth) {
+          atomicOr(err, ERR_STACK_OVERFLOW);
+          active = false;
+          continue;
         }
+        stack_node[sp] = lnear ? kids.y : kids.x;
+        stack_t[sp] = lnear ? tr : tl;
+        ++sp;
+        node = lnear ? kids.x : kids.y;
+      } else if (hl) {
+        node = kids.x;
+      } else if (hr) {
+        node = kids.y;
+      } else {
+        bool found = false;
+        while (sp > 0) {
+          --sp;
+          if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
+        }
+        if (!found) active = false;
       }
     }
     // warp-aggregated append
