@@ -178,6 +178,46 @@ rr_status rr_range_doppler(rr_ctx *ctx, const float *if_in, int n_rx, int n_chir
 rr_status rr_run_frame(rr_ctx *ctx, int scene, const rr_radar *radar, const rr_raygrid *grid,
                        rr_synth_variant variant, int window, float *if_out, float *rd_out);
 
+/* ---- batches of frames ----------------------------------------------------- */
+
+/* One frame of a batch: an uploaded scene slot and its ray grid. */
+typedef struct {
+  int32_t scene;
+  int32_t reserved;   /* set to 0 */
+  rr_raygrid grid;
+} rr_job;
+
+#define RR_BATCH_GRAPH 1     /* run the batch as a CUDA graph (captured on first use, replayed after) */
+#define RR_BATCH_AUTOTUNE 2  /* pick ray-tile shape and split-K factor by timing them on first use */
+
+/* Runs the whole hot path -- build_bvh, trace_frame (ray generation,
+ * traversal, echo of Sec. III-A, path lengths of Sec. III-B), synth_if
+ * (Eq. 4, FMCW form) and, if rd_out != NULL, range_doppler -- for n_jobs
+ * frames of independent scenes with one launch per stage instead of one
+ * per frame: every frame's LBVH is built by its own thread-block cluster
+ * of one builder launch, the ray tiles of all frames go to one persistent
+ * traversal launch, the hits of all frames to one echo launch and one
+ * synthesis launch.  This is the paper's per-frame method applied to many
+ * hand poses at once; frames share the radar but may differ in mesh size
+ * and ray grid.
+ *
+ * jobs: host array of n_jobs (1..RR_MAX_SCENES) entries with distinct,
+ * uploaded scenes.  if_out: device complex64 [n_jobs][n_rx][n_chirps]
+ * [n_samples] (may be NULL when rd_out is given); rd_out: device complex64
+ * of the same shape (fft-shifted Doppler axis, see rr_range_doppler) or
+ * NULL.  Sizes as for rr_synth_if / rr_range_doppler; only RR_SYNTH_FP32.
+ * flags: RR_BATCH_GRAPH captures the enqueued work as a CUDA graph on the
+ * first call of a batch (after one eager run) and replays it on later calls
+ * with identical jobs, radar, outputs and scene buffers (any change
+ * re-captures); RR_BATCH_AUTOTUNE times the candidate ray-tile shapes and
+ * split-K factors once per batch shape and keeps the fastest (results are
+ * the same up to FP32 summation order).  The hit lists of a batch live in
+ * the context (one segment of n_az * n_el hits per frame), not in the
+ * scenes: rr_get_hits does not see them.  Errors as for the single-frame
+ * calls; device-side errors surface at rr_sync. */
+rr_status rr_batch_run(rr_ctx *ctx, const rr_job *jobs, int n_jobs, const rr_radar *radar,
+                       rr_synth_variant variant, int window, float *if_out, float *rd_out, int flags);
+
 /* ---- allocation-free synthesis ------------------------------------------- */
 
 /* Size of the fixed device scratch used by rr_synth_if_from_hits_noalloc. */

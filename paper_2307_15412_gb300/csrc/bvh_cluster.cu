@@ -86,9 +86,7 @@ __device__ __forceinline__ Plan plan(uint32_t *base, int cap) {
 }
 
 __global__ void __launch_bounds__(kThreads, 1)
-k_build_cluster(const float *__restrict__ V, const int32_t *__restrict__ F, int n, int cap,
-                BvhNode *__restrict__ nodes, float4 *__restrict__ tris, uint32_t *__restrict__ keys_out,
-                int32_t *__restrict__ ids_out, BvhHeader *__restrict__ hdr) {
+k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
   extern __shared__ uint4 smem_u4[];
   uint32_t *base = reinterpret_cast<uint32_t *>(smem_u4);
   __shared__ float s_red[kWarps][6];
@@ -100,6 +98,17 @@ k_build_cluster(const float *__restrict__ V, const int32_t *__restrict__ F, int 
   cg::cluster_group cluster = cg::this_cluster();
   const int C = (int)cluster.num_blocks();
   const int crank = (int)cluster.block_rank();
+  // one scene per cluster: the launch's single job, or entry blockIdx.x / C
+  // of a batch table
+  const BuildJob J = table ? table[blockIdx.x / C] : one;
+  const float *__restrict__ V = J.V;
+  const int32_t *__restrict__ F = J.F;
+  BvhNode *__restrict__ nodes = J.nodes;
+  float4 *__restrict__ tris = J.tris;
+  uint32_t *__restrict__ keys_out = J.keys;
+  int32_t *__restrict__ ids_out = J.ids;
+  BvhHeader *__restrict__ hdr = J.hdr;
+  const int n = J.n, cap = J.cap;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const uint32_t lt = (1u << lane) - 1u;
   Plan P = plan(base, cap);
@@ -370,21 +379,10 @@ size_t smem_bytes(int cap) {
   return 4 * ((size_t)2 * cap + (sortR > hierR ? sortR : hierR));
 }
 
-}  // namespace
-
-int cluster_build_capacity() { return 16 * kMaxCap; }
-
-cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used) {
-  *used = false;
-  const int n = (int)s.nt;
-  if (n < 2 || n > 16 * kMaxCap) return cudaSuccess;
+// Whether this device runs 16-CTA clusters of the builder (checked once).
+bool cluster_usable() {
   int dev = 0;
-  cudaError_t e = cudaGetDevice(&dev);
-  if (e != cudaSuccess) return e;
-  if (dev < 0 || dev >= 64) return cudaSuccess;
-  const int C = n <= 8 * 2048 ? 8 : 16;
-  const int cap = (n + C - 1) / C;
-  const size_t smem = smem_bytes(cap);
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return false;
   if (g_cluster_ok[dev] == 0) {
     g_cluster_ok[dev] = -1;
     if (cudaFuncSetAttribute(k_build_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -407,23 +405,66 @@ cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used) {
     }
     cudaGetLastError();  // clear a refused query
   }
-  if (g_cluster_ok[dev] != 1) return cudaSuccess;
+  return g_cluster_ok[dev] == 1;
+}
+
+cudaError_t launch_clusters(const BuildJob &one, const BuildJob *table, int n_jobs, int C, int max_cap,
+                            cudaStream_t st) {
   cudaLaunchConfig_t cfg = {};
   cudaLaunchAttribute attr[1];
   attr[0].id = cudaLaunchAttributeClusterDimension;
   attr[0].val.clusterDim.x = C;
   attr[0].val.clusterDim.y = 1;
   attr[0].val.clusterDim.z = 1;
-  cfg.gridDim = dim3(C);
+  cfg.gridDim = dim3(C * n_jobs);
   cfg.blockDim = dim3(kThreads);
-  cfg.dynamicSmemBytes = smem;
+  cfg.dynamicSmemBytes = smem_bytes(max_cap);
   cfg.stream = st;
   cfg.attrs = attr;
   cfg.numAttrs = 1;
-  e = cudaLaunchKernelEx(&cfg, k_build_cluster, (const float *)s.V, (const int32_t *)s.F, n, cap, s.nodes, s.tris,
-                         s.keys, s.ids, s.hdr);
+  return cudaLaunchKernelEx(&cfg, k_build_cluster, one, table);
+}
+
+}  // namespace
+
+int cluster_build_capacity() { return 16 * kMaxCap; }
+
+bool cluster_build_usable() { return cluster_usable(); }
+
+int cluster_size_for(int n) { return n <= 8 * 2048 ? 8 : 16; }
+
+BuildJob build_job_for(const SceneDev &s) {
+  BuildJob j;
+  j.V = s.V;
+  j.F = s.F;
+  j.nodes = s.nodes;
+  j.tris = s.tris;
+  j.keys = s.keys;
+  j.ids = s.ids;
+  j.hdr = s.hdr;
+  j.n = (int)s.nt;
+  const int C = cluster_size_for(j.n);
+  j.cap = (j.n + C - 1) / C;
+  return j;
+}
+
+cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used) {
+  *used = false;
+  const int n = (int)s.nt;
+  if (n < 2 || n > 16 * kMaxCap) return cudaSuccess;
+  if (!cluster_usable()) return cudaSuccess;
+  const BuildJob j = build_job_for(s);
+  const cudaError_t e = launch_clusters(j, nullptr, 1, cluster_size_for(n), j.cap, st);
   if (e == cudaSuccess) *used = true;
   return e;
+}
+
+cudaError_t launch_build_bvh_cluster_table(const BuildJob *table, int n_jobs, int C, int max_cap,
+                                           cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  if (!cluster_usable()) return cudaErrorNotSupported;
+  BuildJob none = {};
+  return launch_clusters(none, table, n_jobs, C, max_cap, st);
 }
 
 }  // namespace rr

@@ -6,6 +6,7 @@
 #include <stdio.h>
 #include <string.h>
 
+#include <map>
 #include <new>
 #include <vector>
 
@@ -36,6 +37,30 @@ struct rr_ctx {
   int64_t partials_cap = 0;        // floats
   float *if_tmp = nullptr;         // internal IF cube for rr_run_frame(if_out = NULL)
   int64_t if_tmp_cap = 0;          // floats
+  // batches (rr_batch_run): hit-list segments, tables and scratch
+  struct Batch {
+    int32_t *ray = nullptr, *tri = nullptr, *pos = nullptr;
+    float *t = nullptr, *d = nullptr, *a = nullptr, *dd = nullptr;
+    int64_t cap = 0;                        // hits (sum of the frames' segments)
+    uint32_t *counts = nullptr;             // [n_jobs]
+    rr::FrameJob *ftab = nullptr;           // device tables
+    rr::BuildJob *btab = nullptr;
+    rr::JobTiles *jt = nullptr;
+    int64_t *prefix = nullptr;
+    int64_t jobs_cap = 0;
+    rr::FrameJob *h_ftab = nullptr;         // pinned staging of the tables
+    rr::BuildJob *h_btab = nullptr;
+    cudaEvent_t staged = nullptr;           // the last copy out of the staging buffers
+    float *partials = nullptr;
+    int64_t partials_cap = 0;
+    float *if_tmp = nullptr;
+    int64_t if_tmp_cap = 0;
+    // CUDA graph of the last batch
+    cudaGraphExec_t exec = nullptr;
+    uint64_t key = 0;
+    // autotuner choices per batch shape: (ray-tile width log2, split-K)
+    std::map<uint64_t, std::pair<int, int>> tuned;
+  } batch;
   // stage timing ring: 5 events per slot
   std::vector<cudaEvent_t> tev;
   std::vector<char> tev_used;
@@ -225,6 +250,17 @@ rr_status rr_destroy(rr_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->if_tmp) cudaFree(c->if_tmp);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
+  {
+    auto &b = c->batch;
+    void *dev[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd, b.counts, b.ftab, b.btab, b.jt, b.prefix,
+                   b.partials, b.if_tmp};
+    for (void *p : dev)
+      if (p) cudaFree(p);
+    if (b.h_ftab) cudaFreeHost(b.h_ftab);
+    if (b.h_btab) cudaFreeHost(b.h_btab);
+    if (b.staged) cudaEventDestroy(b.staged);
+    if (b.exec) cudaGraphExecDestroy(b.exec);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return RR_OK;
@@ -538,3 +574,301 @@ rr_status rr_get_bvh(rr_ctx *c, int scene, uint32_t *codes, int32_t *ids, int32_
 }
 
 }  // extern "C"
+
+// ---------------------------------------------------------------------------
+// Batches of frames (rr_batch_run)
+// ---------------------------------------------------------------------------
+
+namespace {
+
+uint64_t fnv(uint64_t h, const void *p, size_t n) {
+  const unsigned char *b = static_cast<const unsigned char *>(p);
+  for (size_t i = 0; i < n; ++i) {
+    h ^= b[i];
+    h *= 1099511628211ull;
+  }
+  return h;
+}
+
+// Everything a batch enqueues, decided on the host before any work is issued.
+struct BatchPlan {
+  int n_jobs = 0;
+  int n8 = 0, n16 = 0;              // cluster-built frames (table order: 8-CTA group, 16-CTA group)
+  int max_cap8 = 0, max_cap16 = 0;
+  std::vector<SceneDev *> others;   // frames built by the per-scene path (fewer than 2 or very many triangles)
+  int64_t kmax = 0;                 // largest hit segment
+  rr::RadarDev rd;
+  int tw = 3, split = 0;
+  float *ifb = nullptr, *rd_out = nullptr;
+  int window = 0;
+};
+
+// Enqueues one batch on the context stream: no allocation, no host wait, so
+// the same sequence runs eagerly and under stream capture.
+cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P) {
+  auto &b = c->batch;
+  cudaStream_t st = c->stream;
+  cudaError_t e;
+  if ((e = cudaMemcpyAsync(b.ftab, b.h_ftab, sizeof(rr::FrameJob) * P.n_jobs, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
+  if (P.n8 + P.n16 > 0 &&
+      (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+    return e;
+  if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) return e;
+  if (P.n8 && (e = rr::launch_build_bvh_cluster_table(b.btab, P.n8, 8, P.max_cap8, st)) != cudaSuccess) return e;
+  if (P.n16 && (e = rr::launch_build_bvh_cluster_table(b.btab + P.n8, P.n16, 16, P.max_cap16, st)) != cudaSuccess) return e;
+  for (SceneDev *s : P.others)
+    if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
+  if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
+  if ((e = rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, P.split, b.partials, b.partials_cap, P.ifb, st)) !=
+      cudaSuccess)
+    return e;
+  if (P.rd_out &&
+      (e = rr::launch_range_doppler(P.ifb, P.n_jobs * P.rd.n_rx, P.rd.M, P.rd.N, P.window, P.rd_out, st)) != cudaSuccess)
+    return e;
+  return cudaSuccess;
+}
+
+// Times the candidate ray-tile widths and split-K factors on this batch and
+// returns the fastest of each (eager runs; the outputs are overwritten).
+cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) {
+  auto &b = c->batch;
+  cudaStream_t st = c->stream;
+  cudaEvent_t e0, e1;
+  cudaError_t e = cudaEventCreate(&e0);
+  if (e != cudaSuccess) return e;
+  if ((e = cudaEventCreate(&e1)) != cudaSuccess) { cudaEventDestroy(e0); return e; }
+  float best = INFINITY;
+  int best_tw = 3, best_split = 0;
+  // builds and tables once, then each traversal tile shape twice (the second run is timed)
+  P.tw = 3;
+  P.split = 0;
+  e = batch_enqueue(c, P);
+  const int tws[3] = {2, 3, 4};
+  for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, tws[k])) != cudaSuccess) break;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1 && ms < best) { best = ms; best_tw = tws[k]; }
+    }
+  }
+  // split-K candidates on the hit lists of the chosen shape
+  if (e == cudaSuccess) {
+    e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st);
+    if (e == cudaSuccess) e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, best_tw);
+  }
+  best = INFINITY;
+  const int splits[4] = {0, 1, 2, 4};
+  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+    if (rr::synth_batch_partial_floats(P.rd, P.kmax, P.n_jobs, splits[k]) > b.partials_cap) continue;
+    for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+      if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
+      if ((e = rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, splits[k], b.partials, b.partials_cap, P.ifb,
+                                           st)) != cudaSuccess)
+        break;
+      if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
+      if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, e0, e1);
+      if (rep == 1 && ms < best) { best = ms; best_split = splits[k]; }
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  *tw_out = best_tw;
+  *split_out = best_split;
+  return e;
+}
+
+}  // namespace
+
+extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, const rr_radar *radar,
+                                  rr_synth_variant variant, int window, float *if_out, float *rd_out, int flags) {
+  if (!c) return RR_EINVAL;
+  if (!jobs || n_jobs < 1 || n_jobs > RR_MAX_SCENES) return fail(c, RR_EINVAL, "n_jobs=%d out of [1,%d]", n_jobs, RR_MAX_SCENES);
+  rr_status st;
+  if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  if (!if_out && !rd_out) return fail(c, RR_EINVAL, "need if_out or rd_out");
+  if (window != 0 && window != 1) return fail(c, RR_EINVAL, "window must be 0 or 1");
+  if (flags & ~(RR_BATCH_GRAPH | RR_BATCH_AUTOTUNE)) return fail(c, RR_EINVAL, "unknown batch flags 0x%x", flags);
+  if (rd_out && (int64_t)radar->n_chirps * radar->n_samples > 16384)
+    return fail(c, RR_EINVAL, "range_doppler needs n_chirps * n_samples <= 16384");
+  DeviceGuard g(c->device);
+  auto &b = c->batch;
+
+  // per frame: scene, grid, hit segment
+  std::vector<char> seen(RR_MAX_SCENES, 0);
+  std::vector<SceneDev *> sc(n_jobs);
+  std::vector<int64_t> seg(n_jobs + 1, 0);
+  const bool clusters = rr::cluster_build_usable();
+  BatchPlan P;
+  P.n_jobs = n_jobs;
+  for (int j = 0; j < n_jobs; ++j) {
+    if ((st = get_scene(c, jobs[j].scene, &sc[j])) != RR_OK) return st;
+    if (seen[jobs[j].scene]) return fail(c, RR_EINVAL, "scene %d appears twice in the batch", jobs[j].scene);
+    seen[jobs[j].scene] = 1;
+    const rr_raygrid &gr = jobs[j].grid;
+    if (gr.n_az < 1 || gr.n_el < 1 || (int64_t)gr.n_az * gr.n_el > ((int64_t)1 << 30))
+      return fail(c, RR_EINVAL, "job %d: ray grid size invalid", j);
+    if (!(gr.half_az > 0 && gr.half_az < M_PI) || !(gr.half_el > 0 && gr.half_el < 0.5 * M_PI))
+      return fail(c, RR_EINVAL, "job %d: ray grid half angles out of range", j);
+    seg[j + 1] = seg[j] + (int64_t)gr.n_az * gr.n_el;
+    P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
+    const int n = (int)sc[j]->nt;
+    const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
+    if (cl && rr::cluster_size_for(n) == 8) ++P.n8;
+    else if (cl) ++P.n16;
+    else P.others.push_back(sc[j]);
+  }
+  const int64_t total = seg[n_jobs];
+  const int n_rx = radar->n_rx;
+  P.rd = to_dev(radar);
+  P.window = window;
+  P.rd_out = rd_out;
+
+  // buffers (grown before anything is enqueued or captured)
+  if (total > b.cap || !b.ray) {
+    void *old[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd};
+    for (void *p : old)
+      if (p) cudaFree(p);
+    b.ray = b.tri = b.pos = nullptr;
+    b.t = b.d = b.a = b.dd = nullptr;
+    b.cap = 0;
+    RR_CUDA(c, cudaMalloc((void **)&b.ray, sizeof(int32_t) * total), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.tri, sizeof(int32_t) * total), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.pos, sizeof(int32_t) * total), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.t, sizeof(float) * total), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.d, sizeof(float) * total * RR_MAX_RX), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.a, sizeof(float) * total * RR_MAX_RX), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.dd, sizeof(float) * total * RR_MAX_RX), "batch hit list");
+    b.cap = total;
+    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  }
+  if (n_jobs > b.jobs_cap || !b.counts) {
+    if (b.staged) RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
+    void *old[] = {b.counts, b.ftab, b.btab, b.jt, b.prefix};
+    for (void *p : old)
+      if (p) cudaFree(p);
+    if (b.h_ftab) cudaFreeHost(b.h_ftab);
+    if (b.h_btab) cudaFreeHost(b.h_btab);
+    b.counts = nullptr; b.ftab = nullptr; b.btab = nullptr; b.jt = nullptr; b.prefix = nullptr;
+    b.h_ftab = nullptr; b.h_btab = nullptr;
+    b.jobs_cap = 0;
+    const size_t nj = (size_t)n_jobs;
+    RR_CUDA(c, cudaMalloc((void **)&b.counts, sizeof(uint32_t) * nj), "batch tables");
+    RR_CUDA(c, cudaMalloc((void **)&b.ftab, sizeof(rr::FrameJob) * nj), "batch tables");
+    RR_CUDA(c, cudaMalloc((void **)&b.btab, sizeof(rr::BuildJob) * nj), "batch tables");
+    RR_CUDA(c, cudaMalloc((void **)&b.jt, sizeof(rr::JobTiles) * (nj + 1)), "batch tables");
+    RR_CUDA(c, cudaMalloc((void **)&b.prefix, sizeof(int64_t) * (nj + 1)), "batch tables");
+    RR_CUDA(c, cudaMallocHost((void **)&b.h_ftab, sizeof(rr::FrameJob) * nj), "batch tables");
+    RR_CUDA(c, cudaMallocHost((void **)&b.h_btab, sizeof(rr::BuildJob) * nj), "batch tables");
+    b.jobs_cap = n_jobs;
+    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  }
+  if (!b.staged) RR_CUDA(c, cudaEventCreateWithFlags(&b.staged, cudaEventDisableTiming), "batch event");
+  const int64_t cube = (int64_t)2 * n_rx * radar->n_chirps * radar->n_samples;
+  P.ifb = if_out;
+  if (!P.ifb) {
+    if (cube * n_jobs > b.if_tmp_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    RR_CUDA(c, grow(b.if_tmp, b.if_tmp_cap, cube * n_jobs), "batch IF buffer");
+    P.ifb = b.if_tmp;
+  }
+
+  // tuning of this batch shape
+  uint64_t shape = 1469598103934665603ull;
+  shape = fnv(shape, &n_jobs, sizeof(n_jobs));
+  shape = fnv(shape, &total, sizeof(total));
+  const int dims[3] = {n_rx, radar->n_chirps, radar->n_samples};
+  shape = fnv(shape, dims, sizeof(dims));
+  auto it = b.tuned.find(shape);
+  const bool tune = (flags & RR_BATCH_AUTOTUNE) && it == b.tuned.end();
+  if (it != b.tuned.end()) { P.tw = it->second.first; P.split = it->second.second; }
+  int64_t need = rr::synth_batch_partial_floats(P.rd, P.kmax, n_jobs, P.split);
+  if (tune)
+    for (int sp : {1, 2, 4}) need = std::max(need, rr::synth_batch_partial_floats(P.rd, P.kmax, n_jobs, sp));
+  if (need > b.partials_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  RR_CUDA(c, grow(b.partials, b.partials_cap, need), "batch partials");
+
+  // device tables, staged in pinned memory (wait until the last copy out of it is done)
+  RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
+  int i8 = 0, i16 = P.n8;
+  for (int j = 0; j < n_jobs; ++j) {
+    SceneDev *s = sc[j];
+    rr::FrameJob f = rr::frame_job_for(*s, to_dev(&jobs[j].grid), seg[j + 1] - seg[j]);
+    f.ld = total;
+    f.count = b.counts + j;
+    f.hit_ray = b.ray + seg[j];
+    f.hit_tri = b.tri + seg[j];
+    f.hit_pos = b.pos + seg[j];
+    f.hit_t = b.t + seg[j];
+    f.hit_d = b.d + seg[j];
+    f.hit_a = b.a + seg[j];
+    f.hit_dd = b.dd + seg[j];
+    b.h_ftab[j] = f;
+    const int n = (int)s->nt;
+    if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
+      const rr::BuildJob bj = rr::build_job_for(*s);
+      if (rr::cluster_size_for(n) == 8) {
+        b.h_btab[i8++] = bj;
+        P.max_cap8 = std::max(P.max_cap8, bj.cap);
+      } else {
+        b.h_btab[i16++] = bj;
+        P.max_cap16 = std::max(P.max_cap16, bj.cap);
+      }
+    }
+  }
+
+  if (tune) {
+    int tw = 3, sp = 0;
+    RR_CUDA(c, batch_autotune(c, P, &tw, &sp), "batch autotune");
+    b.tuned[shape] = {tw, sp};
+    P.tw = tw;
+    P.split = sp;
+  }
+
+  // the graph key: everything the enqueued work depends on
+  uint64_t key = shape;
+  key = fnv(key, jobs, sizeof(rr_job) * n_jobs);
+  key = fnv(key, radar, sizeof(rr_radar));
+  key = fnv(key, &variant, sizeof(variant));
+  key = fnv(key, &window, sizeof(window));
+  key = fnv(key, &P.ifb, sizeof(P.ifb));
+  key = fnv(key, &rd_out, sizeof(rd_out));
+  key = fnv(key, &P.tw, sizeof(P.tw));
+  key = fnv(key, &P.split, sizeof(P.split));
+  key = fnv(key, b.h_ftab, sizeof(rr::FrameJob) * n_jobs);
+  key = fnv(key, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16));
+  for (SceneDev *s : P.others) {
+    key = fnv(key, &s, sizeof(s));
+    key = fnv(key, &s->nt, sizeof(s->nt));
+  }
+
+  if ((flags & RR_BATCH_GRAPH) && b.exec && b.key == key) {
+    RR_CUDA(c, cudaGraphLaunch(b.exec, c->stream), "batch graph launch");
+  } else {
+    RR_CUDA(c, batch_enqueue(c, P), "batch launch");
+    if (flags & RR_BATCH_GRAPH) {
+      if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+      cudaGraph_t graph = nullptr;
+      RR_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "batch capture");
+      const cudaError_t ee = batch_enqueue(c, P);
+      const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+      if (ee != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(c, ee, "batch capture"); }
+      RR_CUDA(c, ec, "batch capture");
+      const cudaError_t ei = cudaGraphInstantiate(&b.exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (ei != cudaSuccess) { b.exec = nullptr; return cuda_fail(c, ei, "batch graph instantiate"); }
+      b.key = key;
+    }
+  }
+  RR_CUDA(c, cudaEventRecord(b.staged, c->stream), "batch event");
+  for (SceneDev *s : sc) {
+    s->built = true;
+    s->traced = false;  // the frames' hits are in the batch lists, not in the scenes
+  }
+  return RR_OK;
+}

@@ -30,6 +30,19 @@ struct __align__(16) BvhNode {
   int4 kids;   // left, right, unused, unused
 };
 
+// One scene of a cluster LBVH build (see bvh_cluster.cu).
+struct BuildJob {
+  const float *V;
+  const int32_t *F;
+  BvhNode *nodes;
+  float4 *tris;
+  uint32_t *keys;
+  int32_t *ids;
+  struct BvhHeader *hdr;
+  int32_t n;    // triangles (2 <= n <= cluster_build_capacity())
+  int32_t cap;  // keys per CTA: ceil(n / cluster size)
+};
+
 struct BvhHeader {
   int32_t root;   // root node (>= 0) or ~0 for a single leaf; meaningless when n == 0
   int32_t n;      // triangle count
@@ -92,14 +105,54 @@ struct GridDev {
   float daz_f, del_f;
 };
 
+// One frame of a trace launch: the scene's BVH, the ray grid and the
+// frame's segment of a hit list.  d/a/dd hold n_rx rows of stride ld
+// starting at the segment.
+struct FrameJob {
+  const BvhNode *nodes;
+  const float4 *tris;
+  const BvhHeader *hdr;
+  GridDev g;
+  float vel[3];
+  int64_t cap;       // hits the segment holds
+  int64_t ld;        // row stride of hit_d / hit_a / hit_dd
+  uint32_t *count;   // the frame's hit counter (true count, may exceed cap)
+  int32_t *hit_ray, *hit_tri, *hit_pos;
+  float *hit_t, *hit_d, *hit_a, *hit_dd;
+};
+
+// Per-frame tile numbering of a batched trace (written on the device).
+struct JobTiles {
+  int rect[4];  // candidate rays [rect0, rect1) x [rect2, rect3) (azimuth x elevation index)
+  int tile0;    // first global tile of the frame; entry n_jobs holds the total
+  int pad;
+};
+
 // ---- launchers (each returns the launch status) ----
 cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st);
 // Single-launch cluster builder for 2 <= n <= cluster_build_capacity();
 // sets *used = false (and launches nothing) when it does not apply.
 cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used);
 int cluster_build_capacity();
+// Whether the current device runs the 16-CTA cluster builder (checked once per device).
+bool cluster_build_usable();
+// Cluster size (8 or 16 CTAs) the builder uses for n triangles.
+int cluster_size_for(int n);
+BuildJob build_job_for(const SceneDev &s);
+// One launch building every job of a device table, all with cluster size C
+// (jobs with cluster_size_for(n) == C) and dynamic shared memory for
+// max_cap keys per CTA.  cudaErrorNotSupported if clusters are unusable.
+cudaError_t launch_build_bvh_cluster_table(const BuildJob *table, int n_jobs, int C, int max_cap,
+                                           cudaStream_t st);
+FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap);
+// tw_log2: log2 of the ray-tile width in azimuth (tiles are 2^tw_log2 x 2^(5 - tw_log2))
 cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
-                         uint32_t *err, cudaStream_t st);
+                         uint32_t *err, cudaStream_t st, int tw_log2 = 3);
+// Trace + echo of n_jobs frames in three launches plus two one-CTA scans.
+// table: device FrameJob[n_jobs] (counters zeroed by the caller); jt: device
+// JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1].
+cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix,
+                               const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,
                               int64_t ld, const float *d, const float *a, const float *dd,
                               float *partials, int64_t partial_cap_floats, float *out,
@@ -111,6 +164,10 @@ int64_t synth_partial_floats(const RadarDev &r, int64_t kmax);
 cudaError_t launch_synth_fp32_bounded(const RadarDev &r, int64_t K, const float *d, const float *a,
                                       const float *dd, float *scratch, int64_t scratch_floats, float *out,
                                       cudaStream_t st);
+// Batched synthesis over the hit lists of a FrameJob table (see synth.cu).
+int64_t synth_batch_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int n_jobs, int64_t kmax, int split,
+                                    float *partials, int64_t partial_cap_floats, float *out, cudaStream_t st);
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st);
 

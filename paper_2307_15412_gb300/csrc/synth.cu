@@ -44,7 +44,8 @@ struct SynthParams {
   double kb;              // S dt / c = B / (N c) (1/m)
   float c1k;              // f0 T_rep / c (s/m)
   float b1k;              // kb T_rep (s/m)
-  float *partials;        // [S][n_rx][M][N] complex
+  float *partials;        // [jobs][S][n_rx][M][N] complex
+  const FrameJob *jobs;   // batch: per-frame hit lists (blockIdx.z = frame); nullptr: d, a, dd above
 };
 
 __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
@@ -83,7 +84,18 @@ k_synth_fp32(const SynthParams p) {
   const bool mvalid = active && m < p.M;
   const int hb = tile / 4, lb = tile % 4;
 
-  const int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+  const int job = blockIdx.z;
+  const float *dbase = p.d, *abase = p.a, *ddbase = p.dd;
+  int64_t ld = p.ld;
+  int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+  if (p.jobs) {
+    const FrameJob &J = p.jobs[job];
+    dbase = J.hit_d;
+    abase = J.hit_a;
+    ddbase = J.hit_dd;
+    ld = J.ld;
+    K = min((int64_t)*J.count, J.cap);
+  }
   const int64_t nchunks = (K + p.KC - 1) / p.KC;
 
   float2 acc[TH][4];
@@ -92,9 +104,9 @@ k_synth_fp32(const SynthParams p) {
 #pragma unroll
     for (int q = 0; q < 4; ++q) acc[i][q] = make_float2(0.f, 0.f);
 
-  const float *dj = p.d + (int64_t)j * p.ld;
-  const float *aj = p.a + (int64_t)j * p.ld;
-  const float *ddj = p.dd + (int64_t)j * p.ld;
+  const float *dj = dbase + (int64_t)j * ld;
+  const float *aj = abase + (int64_t)j * ld;
+  const float *ddj = ddbase + (int64_t)j * ld;
 
   for (int64_t ch = s_idx; ch < nchunks; ch += p.S) {
     const int64_t k0 = ch * p.KC;
@@ -187,7 +199,7 @@ k_synth_fp32(const SynthParams p) {
   }
   if (mvalid && kg == 0) {
     float2 *out = reinterpret_cast<float2 *>(p.partials) +
-                  (((int64_t)s_idx * p.n_rx + j) * p.M + m) * (int64_t)p.N;
+                  ((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) * (int64_t)p.N;
 #pragma unroll
     for (int i = 0; i < TH; ++i) {
       const int h = hb * TH + i;
@@ -198,16 +210,20 @@ k_synth_fp32(const SynthParams p) {
   }
 }
 
-__global__ void k_synth_reduce(const float2 *__restrict__ partials, int S, int64_t total, float2 *__restrict__ out) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= total) return;
-  float2 s = partials[i];
+// out[job][i] = sum over s of partials[job][s][i], s in order (i < total per frame)
+__global__ void k_synth_reduce(const float2 *__restrict__ partials, int S, int64_t total, int n_jobs,
+                               float2 *__restrict__ out) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= total * n_jobs) return;
+  const int64_t job = x / total, i = x - job * total;
+  const float2 *pj = partials + job * S * total;
+  float2 s = pj[i];
   for (int k = 1; k < S; ++k) {
-    const float2 v = partials[(int64_t)k * total + i];
+    const float2 v = pj[(int64_t)k * total + i];
     s.x += v.x;
     s.y += v.y;
   }
-  out[i] = s;
+  out[x] = s;
 }
 
 struct Plan {
@@ -242,14 +258,14 @@ Plan make_plan(const RadarDev &r, int64_t kmax) {
 }
 
 template <int HI>
-cudaError_t launch_hi(const SynthParams &p, const Plan &pl, cudaStream_t st) {
+cudaError_t launch_hi(const SynthParams &p, const Plan &pl, int n_jobs, cudaStream_t st) {
   static bool attr_set = false;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_synth_fp32<HI>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)pl.smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid(pl.n_mtiles * p.n_rx, pl.S);
+  dim3 grid(pl.n_mtiles * p.n_rx, pl.S, n_jobs);
   k_synth_fp32<HI><<<grid, kSynthThreads, pl.smem, st>>>(p);
   return cudaGetLastError();
 }
@@ -279,21 +295,22 @@ cudaError_t launch_synth_fp32_bounded(const RadarDev &r, int64_t K, const float 
   p.c1k = (float)(r.f0 * r.t_rep / kC);
   p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
   p.partials = scratch;
+  p.jobs = nullptr;
   cudaError_t e;
   switch (pl.HI) {
-    case 1: e = launch_hi<1>(p, pl, st); break;
-    case 2: e = launch_hi<2>(p, pl, st); break;
-    case 4: e = launch_hi<4>(p, pl, st); break;
-    case 8: e = launch_hi<8>(p, pl, st); break;
-    case 16: e = launch_hi<16>(p, pl, st); break;
-    case 32: e = launch_hi<32>(p, pl, st); break;
-    case 64: e = launch_hi<64>(p, pl, st); break;
+    case 1: e = launch_hi<1>(p, pl, 1, st); break;
+    case 2: e = launch_hi<2>(p, pl, 1, st); break;
+    case 4: e = launch_hi<4>(p, pl, 1, st); break;
+    case 8: e = launch_hi<8>(p, pl, 1, st); break;
+    case 16: e = launch_hi<16>(p, pl, 1, st); break;
+    case 32: e = launch_hi<32>(p, pl, 1, st); break;
+    case 64: e = launch_hi<64>(p, pl, 1, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(scratch), pl.S, total,
+  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(scratch), pl.S, total, 1,
                                                         reinterpret_cast<float2 *>(out));
   return cudaGetLastError();
 }
@@ -314,22 +331,87 @@ cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t 
   p.c1k = (float)(r.f0 * r.t_rep / kC);
   p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
   p.partials = partials;
+  p.jobs = nullptr;
   cudaError_t e;
   switch (pl.HI) {
-    case 1: e = launch_hi<1>(p, pl, st); break;
-    case 2: e = launch_hi<2>(p, pl, st); break;
-    case 4: e = launch_hi<4>(p, pl, st); break;
-    case 8: e = launch_hi<8>(p, pl, st); break;
-    case 16: e = launch_hi<16>(p, pl, st); break;
-    case 32: e = launch_hi<32>(p, pl, st); break;
-    case 64: e = launch_hi<64>(p, pl, st); break;
+    case 1: e = launch_hi<1>(p, pl, 1, st); break;
+    case 2: e = launch_hi<2>(p, pl, 1, st); break;
+    case 4: e = launch_hi<4>(p, pl, 1, st); break;
+    case 8: e = launch_hi<8>(p, pl, 1, st); break;
+    case 16: e = launch_hi<16>(p, pl, 1, st); break;
+    case 32: e = launch_hi<32>(p, pl, 1, st); break;
+    case 64: e = launch_hi<64>(p, pl, 1, st); break;
     default: return cudaErrorInvalidValue;
   }
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = (total + threads - 1) / threads;
-  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total,
+  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total, 1,
                                                         reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
+// Batch: one synthesis launch over n_jobs frames (blockIdx.z = frame) and
+// one reduction launch.  kmax: the largest hit capacity of any frame (it
+// bounds the useful split count); split: split-K factor (0 = planned from
+// the SM count).
+namespace {
+// split-K factor of a batch: the given one, else enough CTAs for about two
+// per SM over all frames, at most one split per hit chunk
+int batch_split(const Plan &pl, const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  if (split > 0) return split;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)pl.n_mtiles * r.n_rx * n_jobs;
+  const int64_t chunks = (kmax + pl.KC - 1) / pl.KC;
+  int64_t S = (2 * (int64_t)sms + tiles - 1) / tiles;
+  if (S > chunks) S = chunks;
+  return S < 1 ? 1 : (int)S;
+}
+}  // namespace
+
+int64_t synth_batch_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  const Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
+  const int S = batch_split(pl, r, kmax < 1 ? 1 : kmax, n_jobs, split);
+  return (int64_t)n_jobs * S * r.n_rx * r.M * r.N * 2;
+}
+
+cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int n_jobs, int64_t kmax, int split,
+                                    float *partials, int64_t partial_cap_floats, float *out, cudaStream_t st) {
+  if (n_jobs <= 0) return cudaSuccess;
+  Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
+  pl.S = batch_split(pl, r, kmax < 1 ? 1 : kmax, n_jobs, split);
+  const int64_t total = (int64_t)r.n_rx * r.M * r.N;
+  if ((int64_t)n_jobs * pl.S * total * 2 > partial_cap_floats) return cudaErrorInvalidValue;
+  SynthParams p;
+  p.d = p.a = p.dd = nullptr;
+  p.ld = 0;
+  p.count = nullptr;
+  p.kmax = kmax;
+  p.n_rx = r.n_rx; p.M = r.M; p.N = r.N;
+  p.G = pl.G; p.KG = pl.KG; p.KC = pl.KC; p.n_mtiles = pl.n_mtiles; p.S = pl.S;
+  p.f0_c = r.f0 / kC;
+  p.kb = r.slope * r.dt / kC;
+  p.c1k = (float)(r.f0 * r.t_rep / kC);
+  p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
+  p.partials = partials;
+  p.jobs = jobs;
+  cudaError_t e;
+  switch (pl.HI) {
+    case 1: e = launch_hi<1>(p, pl, n_jobs, st); break;
+    case 2: e = launch_hi<2>(p, pl, n_jobs, st); break;
+    case 4: e = launch_hi<4>(p, pl, n_jobs, st); break;
+    case 8: e = launch_hi<8>(p, pl, n_jobs, st); break;
+    case 16: e = launch_hi<16>(p, pl, n_jobs, st); break;
+    case 32: e = launch_hi<32>(p, pl, n_jobs, st); break;
+    case 64: e = launch_hi<64>(p, pl, n_jobs, st); break;
+    default: return cudaErrorInvalidValue;
+  }
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = (total * n_jobs + threads - 1) / threads;
+  k_synth_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total,
+                                                        n_jobs, reinterpret_cast<float2 *>(out));
   return cudaGetLastError();
 }
 

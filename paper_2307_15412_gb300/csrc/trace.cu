@@ -136,33 +136,57 @@ __device__ void ray_rect(const BvhHeader *hdr, const RadarDev &r, const GridDev 
   if (rect[3] < rect[2]) rect[3] = rect[2];
 }
 
-// Persistent traversal: warps take the 8 x 4 ray tiles of the candidate
-// rectangle in a fixed interleaved order (a shared tile counter serialised
-// on one L2 address and cost more than the traversal), so the few tiles that
-// contain the object are spread over every SM.
-__global__ void __launch_bounds__(kTraceThreads)
-k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
-        const BvhHeader *__restrict__ hdr, const RadarDev r, const GridDev g, int64_t cap,
-        uint32_t *__restrict__ counters, int32_t *__restrict__ hit_ray, int32_t *__restrict__ hit_tri,
-        int32_t *__restrict__ hit_pos, float *__restrict__ hit_t, uint32_t *__restrict__ err) {
-  __shared__ int rect[4];
-  const int n = hdr->n;
-  if (n <= 0) return;
-  if (threadIdx.x == 0) ray_rect(hdr, r, g, rect);
-  __syncthreads();
-  const int lane = threadIdx.x & 31;
-  const int tiles_az = (rect[1] - rect[0] + 7) / 8, tiles_el = (rect[3] - rect[2] + 3) / 4;
-  const int ntiles = tiles_az * tiles_el;
-  const int root = hdr->root;
-  const float blo[3] = {hdr->lo[0], hdr->lo[1], hdr->lo[2]}, bhi[3] = {hdr->hi[0], hdr->hi[1], hdr->hi[2]};
-  uint32_t *count = counters;
+// Ray tiles: a warp traces one tile of TW x (32 / TW) neighbouring rays of
+// one frame (TW = 1 << tw_log2, chosen by the autotuner).  Tiles of a frame
+// cover only its candidate rectangle; the tiles of all frames of a launch
+// are numbered consecutively (JobTiles::tile0) and taken by the warps in a
+// fixed interleaved order, so the few tiles that contain an object are
+// spread over every SM.
+__device__ __forceinline__ int tiles_of(const int *rect, int tw_log2) {
+  const int tw = 1 << tw_log2, th = 32 >> tw_log2;
+  return ((rect[1] - rect[0] + tw - 1) / tw) * ((rect[3] - rect[2] + th - 1) / th);
+}
 
+// frame of global tile t: last job whose first tile is <= t
+__device__ __forceinline__ int job_of_tile(const JobTiles *__restrict__ jt, int n_jobs, int t) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jt[mid].tile0 <= t) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kTraceThreads)
+k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *__restrict__ jt, int n_jobs,
+        const RadarDev r, int tw_log2, uint32_t *__restrict__ err) {
+  __shared__ int rect1[4];
+  int total;
+  if (!table) {  // one frame: every CTA derives the candidate rectangle itself
+    if (one.hdr->n <= 0) return;
+    if (threadIdx.x == 0) ray_rect(one.hdr, r, one.g, rect1);
+    __syncthreads();
+    total = tiles_of(rect1, tw_log2);
+  } else {
+    total = jt[n_jobs].tile0;
+  }
+  const int lane = threadIdx.x & 31;
+  const int tw = 1 << tw_log2;
   const int gw = blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5);
   const int nw = gridDim.x * (kTraceThreads / 32);
-  for (int tile = gw; tile < ntiles; tile += nw) {
-    const int i_az = rect[0] + (tile % tiles_az) * 8 + (lane & 7);
-    const int i_el = rect[2] + (tile / tiles_az) * 4 + (lane >> 3);
+  for (int tile = gw; tile < total; tile += nw) {
+    const int job = table ? job_of_tile(jt, n_jobs, tile) : 0;
+    const FrameJob &J = table ? table[job] : one;
+    const int *rect = table ? jt[job].rect : rect1;
+    const int lt = table ? tile - jt[job].tile0 : tile;
+    const int tiles_az = (rect[1] - rect[0] + tw - 1) / tw;
+    const int i_az = rect[0] + (lt % tiles_az) * tw + (lane & (tw - 1));
+    const int i_el = rect[2] + (lt / tiles_az) * (32 >> tw_log2) + (lane >> tw_log2);
     const bool valid = i_az < rect[1] && i_el < rect[3];
+    const BvhHeader *hdr = J.hdr;
+    const int n = hdr->n;
+    const int root = hdr->root;
+    const float blo[3] = {hdr->lo[0], hdr->lo[1], hdr->lo[2]}, bhi[3] = {hdr->hi[0], hdr->hi[1], hdr->hi[2]};
 
     float best_t = INFINITY;
     int best_pos = -1, best_id = 0x7fffffff;
@@ -170,8 +194,8 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
     bool active = false;  // this lane still walks the tree
     if (valid) {
       float sa, ca, se, ce;
-      sincospif(fmaf((float)i_az, g.daz_pi, g.az0_pi), &sa, &ca);
-      sincospif(fmaf((float)i_el, g.del_pi, g.el0_pi), &se, &ce);
+      sincospif(fmaf((float)i_az, J.g.daz_pi, J.g.az0_pi), &sa, &ca);
+      sincospif(fmaf((float)i_el, J.g.del_pi, J.g.el0_pi), &se, &ce);
       const float ur[3] = {ce * sa, se, ce * ca};
       float d[3];
 #pragma unroll
@@ -190,7 +214,7 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
 
       const float t_root = box_entry(rp, blo[0], bhi[0], blo[1], bhi[1], blo[2], bhi[2], INFINITY);
       if (t_root < INFINITY) {
-        if (root < 0) tri_test(rp, tris, ~root, best_t, best_pos, best_id);
+        if (root < 0) tri_test(rp, J.tris, ~root, best_t, best_pos, best_id);
         else active = true;
       }
     }
@@ -211,10 +235,10 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
         continue;
       }
       ++visits;
-      const float4 lxy = __ldg(&nodes[node].lxy);
-      const float4 rxy = __ldg(&nodes[node].rxy);
-      const float4 lrz = __ldg(&nodes[node].lrz);
-      const int4 kids = __ldg(&nodes[node].kids);
+      const float4 lxy = __ldg(&J.nodes[node].lxy);
+      const float4 rxy = __ldg(&J.nodes[node].rxy);
+      const float4 lrz = __ldg(&J.nodes[node].lrz);
+      const int4 kids = __ldg(&J.nodes[node].kids);
       const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
       const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
       bool hl = tl < INFINITY, hr = tr < INFINITY;
@@ -223,8 +247,8 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
         active = false;
         continue;
       }
-      if (hl && kids.x < 0) { tri_test(rp, tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
-      if (hr && kids.y < 0) { tri_test(rp, tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
+      if (hl && kids.x < 0) { tri_test(rp, J.tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
+      if (hr && kids.y < 0) { tri_test(rp, J.tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
       if (hl && hr) {
         const bool lnear = tl <= tr;
         if (sp == kStackDepth) {
@@ -255,15 +279,15 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
     if (mask != 0u) {
       const int leader = __ffs(mask) - 1;
       uint32_t base = 0;
-      if (lane == leader) base = atomicAdd(count, (uint32_t)__popc(mask));
+      if (lane == leader) base = atomicAdd(J.count, (uint32_t)__popc(mask));
       base = __shfl_sync(0xffffffffu, base, leader);
       if (has) {
         const int64_t slot = (int64_t)base + __popc(mask & ((1u << lane) - 1u));
-        if (slot < cap) {
-          hit_ray[slot] = i_el * g.n_az + i_az;
-          hit_tri[slot] = best_id;
-          hit_pos[slot] = best_pos;
-          hit_t[slot] = best_t;
+        if (slot < J.cap) {
+          J.hit_ray[slot] = i_el * J.g.n_az + i_az;
+          J.hit_tri[slot] = best_id;
+          J.hit_pos[slot] = best_pos;
+          J.hit_t[slot] = best_t;
         } else {
           atomicOr(err, ERR_HIT_OVERFLOW);
         }
@@ -272,19 +296,117 @@ k_trace(const BvhNode *__restrict__ nodes, const float4 *__restrict__ tris,
   }
 }
 
+// Candidate rectangles and tile numbering of a batch (one CTA of 1024
+// threads; n_jobs <= 4096).  jt[n_jobs].tile0 receives the total.
+__global__ void __launch_bounds__(1024)
+k_batch_tiles(const FrameJob *__restrict__ table, int n_jobs, const RadarDev r, int tw_log2, JobTiles *__restrict__ jt) {
+  __shared__ int s_wsum[32];
+  const int per = (n_jobs + 1023) / 1024;
+  const int j0 = threadIdx.x * per;
+  int local = 0;
+  for (int k = 0; k < per; ++k) {
+    const int j = j0 + k;
+    if (j < n_jobs) {
+      int rc[4] = {0, 0, 0, 0};
+      if (table[j].hdr->n > 0) ray_rect(table[j].hdr, r, table[j].g, rc);
+      for (int q = 0; q < 4; ++q) jt[j].rect[q] = rc[q];
+      local += tiles_of(rc, tw_log2);
+    }
+  }
+  // exclusive block scan of the per-thread tile counts
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int x = s_wsum[lane];
+    int xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    s_wsum[lane] = xi - x;
+  }
+  __syncthreads();
+  int run = s_wsum[warp] + incl - local;
+  for (int k = 0; k < per; ++k) {
+    const int j = j0 + k;
+    if (j < n_jobs) {
+      jt[j].tile0 = run;
+      run += tiles_of(jt[j].rect, tw_log2);
+    }
+  }
+  if (threadIdx.x == 1023) jt[n_jobs].tile0 = run;
+}
+
+// Hit-list prefix of a batch: pre[j] = sum of min(count, cap) over frames
+// before j, pre[n_jobs] = total (one CTA of 1024 threads).
+__global__ void __launch_bounds__(1024)
+k_batch_hit_prefix(const FrameJob *__restrict__ table, int n_jobs, int64_t *__restrict__ pre) {
+  __shared__ int64_t s_wsum[32];
+  const int per = (n_jobs + 1023) / 1024;
+  const int j0 = threadIdx.x * per;
+  int64_t local = 0;
+  for (int k = 0; k < per; ++k) {
+    const int j = j0 + k;
+    if (j < n_jobs) local += min((int64_t)*table[j].count, table[j].cap);
+  }
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  int64_t incl = local;
+  for (int o = 1; o < 32; o <<= 1) {
+    const int64_t t = __shfl_up_sync(0xffffffffu, incl, o);
+    if (lane >= o) incl += t;
+  }
+  if (lane == 31) s_wsum[warp] = incl;
+  __syncthreads();
+  if (warp == 0) {
+    const int64_t x = s_wsum[lane];
+    int64_t xi = x;
+    for (int o = 1; o < 32; o <<= 1) {
+      const int64_t t = __shfl_up_sync(0xffffffffu, xi, o);
+      if (lane >= o) xi += t;
+    }
+    s_wsum[lane] = xi - x;
+  }
+  __syncthreads();
+  int64_t run = s_wsum[warp] + incl - local;
+  for (int k = 0; k < per; ++k) {
+    const int j = j0 + k;
+    if (j < n_jobs) {
+      pre[j] = run;
+      run += min((int64_t)*table[j].count, table[j].cap);
+    }
+  }
+  if (threadIdx.x == 1023) pre[n_jobs] = run;
+}
+
+__device__ __forceinline__ int job_of_hit(const int64_t *__restrict__ pre, int n_jobs, int64_t h) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (pre[mid] <= h) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
 __global__ void __launch_bounds__(128)
-k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const float3 vel,
-       const uint32_t *__restrict__ count, int64_t cap, const int32_t *__restrict__ hit_ray,
-       const int32_t *__restrict__ hit_pos, float *__restrict__ hit_t, float *__restrict__ hit_d,
-       float *__restrict__ hit_a, float *__restrict__ hit_dd) {
-  const int64_t K = min((int64_t)*count, cap);
-  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < K; h += (int64_t)gridDim.x * blockDim.x) {
-    const int ray = hit_ray[h];
-    const int pos = hit_pos[h];
-    const int i_el = ray / g.n_az, i_az = ray - i_el * g.n_az;
+k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__restrict__ pre, int n_jobs,
+       const RadarDev r) {
+  const int64_t total = table ? pre[n_jobs] : min((int64_t)*one.count, one.cap);
+  for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < total; h += (int64_t)gridDim.x * blockDim.x) {
+    const int job = table ? job_of_hit(pre, n_jobs, h) : 0;
+    const FrameJob &J = table ? table[job] : one;
+    const int64_t hl = table ? h - pre[job] : h;
+    const int ray = J.hit_ray[hl];
+    const int pos = J.hit_pos[hl];
+    const int i_el = ray / J.g.n_az, i_az = ray - i_el * J.g.n_az;
     // exact ray direction (FP64), as the grid defines it
-    const double az = -g.half_az + g.daz * (i_az + 0.5);
-    const double el = -g.half_el + g.del * (i_el + 0.5);
+    const double az = -J.g.half_az + J.g.daz * (i_az + 0.5);
+    const double el = -J.g.half_el + J.g.del * (i_el + 0.5);
     double sa, ca, se, ce;
     sincos(az, &sa, &ca);
     sincos(el, &se, &ce);
@@ -292,7 +414,7 @@ k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const
     double u[3];
 #pragma unroll
     for (int k = 0; k < 3; ++k) u[k] = r.R[3 * k] * ur[0] + r.R[3 * k + 1] * ur[1] + r.R[3 * k + 2] * ur[2];
-    const float4 fa = __ldg(tris + 3 * pos), fb = __ldg(tris + 3 * pos + 1), fc = __ldg(tris + 3 * pos + 2);
+    const float4 fa = __ldg(J.tris + 3 * pos), fb = __ldg(J.tris + 3 * pos + 1), fc = __ldg(J.tris + 3 * pos + 2);
     const double v0[3] = {fa.x, fa.y, fa.z};
     const double e1[3] = {(double)fb.x - v0[0], (double)fb.y - v0[1], (double)fb.z - v0[2]};
     const double e2[3] = {(double)fc.x - v0[0], (double)fc.y - v0[1], (double)fc.z - v0[2]};
@@ -300,8 +422,8 @@ k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const
     const double un = u[0] * nn[0] + u[1] * nn[1] + u[2] * nn[2];
     const double num = nn[0] * (v0[0] - r.tx[0]) + nn[1] * (v0[1] - r.tx[1]) + nn[2] * (v0[2] - r.tx[2]);
     double t = num / un;
-    if (!(t > 0.0)) t = (double)hit_t[h];  // degenerate plane: keep the traversal distance
-    hit_t[h] = (float)t;
+    if (!(t > 0.0)) t = (double)J.hit_t[hl];  // degenerate plane: keep the traversal distance
+    J.hit_t[hl] = (float)t;
     const double p[3] = {r.tx[0] + t * u[0], r.tx[1] + t * u[1], r.tx[2] + t * u[2]};
     // unit face normal turned toward the incoming ray (two-sided faces)
     const double inl = rsqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
@@ -311,7 +433,7 @@ k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const
     const float ci = -(uf[0] * nf[0] + uf[1] * nf[1] + uf[2] * nf[2]);
     // Eq. 2 mirror direction u - 2 (u . n_f) n_f
     const float mr[3] = {uf[0] + 2.f * ci * nf[0], uf[1] + 2.f * ci * nf[1], uf[2] + 2.f * ci * nf[2]};
-    const float omega = (float)(ce * g.daz * g.del);
+    const float omega = (float)(ce * J.g.daz * J.g.del);
     for (int j = 0; j < r.n_rx; ++j) {
       const double w[3] = {p[0] - r.rx[j][0], p[1] - r.rx[j][1], p[2] - r.rx[j][2]};
       const double rj = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
@@ -324,31 +446,72 @@ k_echo(const float4 *__restrict__ tris, const RadarDev r, const GridDev g, const
         const float s = sdot > 0.f ? powf(sdot, r.spec_exp) : 0.f;
         gj = (1.f - r.alpha) * s + r.alpha * (ci * co);
       }
-      const int64_t o = (int64_t)j * cap + h;
-      hit_d[o] = (float)(t + rj);
-      hit_a[o] = r.amp_mode == 1 ? 1.f : (float)((double)omega * gj / (t * rj));
-      hit_dd[o] = vel.x * (uf[0] + uj[0]) + vel.y * (uf[1] + uj[1]) + vel.z * (uf[2] + uj[2]);
+      const int64_t o = (int64_t)j * J.ld + hl;
+      J.hit_d[o] = (float)(t + rj);
+      J.hit_a[o] = r.amp_mode == 1 ? 1.f : (float)((double)omega * gj / (t * rj));
+      J.hit_dd[o] = J.vel[0] * (uf[0] + uj[0]) + J.vel[1] * (uf[1] + uj[1]) + J.vel[2] * (uf[2] + uj[2]);
     }
   }
 }
 
-}  // namespace
-
-cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
-                         uint32_t *err, cudaStream_t st) {
-  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, 2 * sizeof(uint32_t), st);
-  if (e != cudaSuccess) return e;
+int sm_count() {
   int sms = 152, dev = 0;
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(s.nodes, s.tris, s.hdr, r, g, cap, s.hit_count, s.hit_ray,
-                                            s.hit_tri, s.hit_pos, s.hit_t, err);
+  return sms;
+}
+
+}  // namespace
+
+FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap) {
+  FrameJob j;
+  j.nodes = s.nodes;
+  j.tris = s.tris;
+  j.hdr = s.hdr;
+  j.g = g;
+  for (int k = 0; k < 3; ++k) j.vel[k] = s.vel[k];
+  j.cap = cap;
+  j.ld = cap;
+  j.count = s.hit_count;
+  j.hit_ray = s.hit_ray;
+  j.hit_tri = s.hit_tri;
+  j.hit_pos = s.hit_pos;
+  j.hit_t = s.hit_t;
+  j.hit_d = s.hit_d;
+  j.hit_a = s.hit_a;
+  j.hit_dd = s.hit_dd;
+  return j;
+}
+
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
+                         uint32_t *err, cudaStream_t st, int tw_log2) {
+  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, sizeof(uint32_t), st);
+  if (e != cudaSuccess) return e;
+  const int sms = sm_count();
+  const FrameJob one = frame_job_for(s, g, cap);
+  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(one, nullptr, nullptr, 1, r, tw_log2, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t want = (cap + 127) / 128;
   const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
-  const float3 vel = make_float3(s.vel[0], s.vel[1], s.vel[2]);
-  k_echo<<<blocks, 128, 0, st>>>(s.tris, r, g, vel, s.hit_count, cap, s.hit_ray, s.hit_pos, s.hit_t,
-                                 s.hit_d, s.hit_a, s.hit_dd);
+  k_echo<<<blocks, 128, 0, st>>>(one, nullptr, nullptr, 1, r);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix,
+                               const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2) {
+  if (n_jobs <= 0) return cudaSuccess;
+  const int sms = sm_count();
+  FrameJob none = {};
+  k_batch_tiles<<<1, 1024, 0, st>>>(table, n_jobs, r, tw_log2, jt);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(none, table, jt, n_jobs, r, tw_log2, err);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_batch_hit_prefix<<<1, 1024, 0, st>>>(table, n_jobs, hit_prefix);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  k_echo<<<4 * sms, 128, 0, st>>>(none, table, hit_prefix, n_jobs, r);
   return cudaGetLastError();
 }
 

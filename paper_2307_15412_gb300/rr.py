@@ -45,6 +45,13 @@ class rr_raygrid(ctypes.Structure):
                 ("half_az", ctypes.c_double), ("half_el", ctypes.c_double)]
 
 
+class rr_job(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("grid", rr_raygrid)]
+
+
+RR_BATCH_GRAPH = 1
+RR_BATCH_AUTOTUNE = 2
+
 SIGNATURES = {
     "rr_create": (_I, [ctypes.POINTER(_P), _I, _P]),
     "rr_destroy": (_I, [_P]),
@@ -63,6 +70,7 @@ SIGNATURES = {
     "rr_run_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I, _I, _P, _P]),
     "rr_get_bvh": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "rr_synth_if_from_hits_noalloc": (_I, [ctypes.POINTER(rr_radar), _I, _I64, _P, _P, _P, _P, _P]),
+    "rr_batch_run": (_I, [_P, ctypes.POINTER(rr_job), _I, ctypes.POINTER(rr_radar), _I, _I, _P, _P, _I]),
     "rr_timing_enable": (_I, [_P, _I]),
     "rr_timing_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -229,6 +237,24 @@ class Context:
         rs, gs = make_radar(radar), make_grid(grid)
         self._check(self.lib.rr_run_frame(self.h, scene, ctypes.byref(rs), ctypes.byref(gs), int(variant),
                                           int(window), _ptr(if_out), _ptr(rd_out)))
+
+    def batch_run(self, jobs, radar, if_out=None, rd_out=None, variant: int = SYNTH_FP32, window: int = 0,
+                  graph: bool = False, autotune: bool = False):
+        """Whole hot path for several frames at once.  jobs: list of
+        (scene, RayGrid or rr_raygrid), or a prepared ctypes rr_job array;
+        if_out / rd_out: torch CUDA float32 [n_jobs, n_rx, M, N, 2]."""
+        if isinstance(jobs, ctypes.Array):
+            arr = jobs
+        else:
+            arr = (rr_job * len(jobs))()
+            for i, (sc, g) in enumerate(jobs):
+                arr[i].scene = int(sc)
+                arr[i].reserved = 0
+                arr[i].grid = make_grid(g)
+        rs = make_radar(radar)
+        flags = (RR_BATCH_GRAPH if graph else 0) | (RR_BATCH_AUTOTUNE if autotune else 0)
+        self._check(self.lib.rr_batch_run(self.h, arr, len(arr), ctypes.byref(rs), int(variant), int(window),
+                                          _ptr(if_out), _ptr(rd_out), flags))
 
     def timing_enable(self, n_slots: int):
         self._check(self.lib.rr_timing_enable(self.h, int(n_slots)))

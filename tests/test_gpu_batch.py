@@ -1,0 +1,162 @@
+"""GPU: batches of frames (rr_batch_run) against the single-frame path and the
+FP64 oracle.
+
+Tolerances:
+  * batch vs single-frame run of the same scene: rel-L2 <= 1e-5 on the IF and
+    range-Doppler cubes (same kernels; only the FP32 summation order of the
+    hit list differs, because hits are appended in arrival order);
+  * batch vs FP64 oracle (tiny frames, end to end): rel-L2 <= 1e-3;
+  * an empty scene gives an exactly zero cube.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import rel_l2, to_complex
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def _cube(n_jobs, radar):
+    return torch.zeros((n_jobs, radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32,
+                       device="cuda:0")
+
+
+def _single(ctx, scene, radar, grid):
+    if_out = _cube(1, radar)[0]
+    rd_out = torch.zeros_like(if_out)
+    ctx.run_frame(scene, radar, grid, if_out=if_out, rd_out=rd_out)
+    ctx.sync()
+    return to_complex(if_out), to_complex(rd_out)
+
+
+def _mixed_batch():
+    """Uneven batch: mesh sizes from 2 to ~50k triangles (both cluster sizes
+    of the builder), different ray grids, an empty scene."""
+    radar = I.Radar(n_samples=128, n_chirps=32, rx=I.rx_l_array())
+    specs = [  # (seed, triangles, grid n, half angle deg)
+        (0, 600, 64, 30.0), (1, 2000, 128, 45.0), (2, 20000, 256, 45.0), (3, 50000, 128, 45.0),
+        (4, 5000, 96, 40.0), (5, 12000, 200, 45.0)]
+    scenes, grids = [], []
+    for seed, nt, n, half in specs:
+        scenes.append(I.hand_scene(seed, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED))
+        grids.append(I.RayGrid(n, n, math.radians(half), math.radians(half)))
+    return radar, scenes, grids
+
+
+def test_batch_matches_single_frames(ctx):
+    radar, scenes, grids = _mixed_batch()
+    base = 100
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(base + k, s.V, s.F, s.vel)
+    # an empty scene and a two-triangle plate ride along
+    ctx.scene_upload(base + 6, np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), None)
+    Vp, Fp = I.plate((0.0, 0.0, 0.35), 0.05, 0.05)
+    ctx.scene_upload(base + 7, Vp, Fp, None)
+    grids += [I.RayGrid(32, 32, 0.5, 0.5), I.RayGrid(64, 48, 0.4, 0.3)]
+    jobs = [(base + k, g) for k, g in enumerate(grids)]
+    n = len(jobs)
+    if_b, rd_b = _cube(n, radar), _cube(n, radar)
+    ctx.batch_run(jobs, radar, if_out=if_b, rd_out=rd_b)
+    ctx.sync()
+    gi, gr = to_complex(if_b), to_complex(rd_b)
+    assert not np.any(gi[6]) and not np.any(gr[6])
+    for k in range(n):
+        if k == 6:
+            continue
+        si, sr = _single(ctx, base + k, radar, grids[k])
+        assert np.linalg.norm(si) > 0
+        assert rel_l2(gi[k], si) <= 1e-5, (k, rel_l2(gi[k], si))
+        assert rel_l2(gr[k], sr) <= 1e-5, (k, rel_l2(gr[k], sr))
+
+
+def test_batch_tiny_frames_end_to_end_vs_oracle(ctx):
+    radar, grid, nt = I.workload_tiny()
+    scenes = [I.hand_scene(40 + k, nt) for k in range(4)]
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(200 + k, s.V, s.F, s.vel)
+    if_b = _cube(4, radar)
+    ctx.batch_run([(200 + k, grid) for k in range(4)], radar, if_out=if_b)
+    ctx.sync()
+    got = to_complex(if_b)
+    for k, s in enumerate(scenes):
+        ref = oracle.frame(s.V, s.F, s.vel, radar, grid)["if_cube"]
+        assert rel_l2(got[k], ref) <= 1e-3
+
+
+def test_batch_graph_replay_follows_scene_contents(ctx):
+    """A captured batch replays with the scenes' current contents: after a
+    re-upload of new poses of the same sizes the replay matches fresh
+    single-frame runs of the new poses."""
+    radar, grid, nt = I.workload_full_frame()
+    radar = I.Radar(n_samples=256, n_chirps=16, rx=I.rx_l_array())
+    grid = I.RayGrid(256, 256, grid.half_az, grid.half_el)
+    ids = [300 + k for k in range(4)]
+    for k in range(4):
+        s = I.hand_scene(60 + k, 20000, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+        ctx.scene_upload(ids[k], s.V, s.F, s.vel)
+    jobs = [(i, grid) for i in ids]
+    if_e, if_g = _cube(4, radar), _cube(4, radar)
+    ctx.batch_run(jobs, radar, if_out=if_e)
+    ctx.batch_run(jobs, radar, if_out=if_g, graph=True)  # eager run + capture
+    ctx.batch_run(jobs, radar, if_out=if_g, graph=True)  # replay
+    ctx.sync()
+    assert rel_l2(to_complex(if_g), to_complex(if_e)) <= 1e-5
+    # new poses (same triangle count, so every buffer stays where it was)
+    for k in range(4):
+        s = I.hand_scene(70 + k, 20000, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+        ctx.scene_upload(ids[k], s.V, s.F, s.vel)
+    if_g.zero_()
+    ctx.batch_run(jobs, radar, if_out=if_g, graph=True)  # replay of the captured graph
+    ctx.sync()
+    got = to_complex(if_g)
+    for k in range(4):
+        si, _ = _single(ctx, ids[k], radar, grid)
+        assert rel_l2(got[k], si) <= 1e-5
+
+
+def test_batch_autotune_keeps_results(ctx):
+    radar, scenes, grids = _mixed_batch()
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(400 + k, s.V, s.F, s.vel)
+    jobs = [(400 + k, g) for k, g in enumerate(grids)]
+    n = len(jobs)
+    ref, got = _cube(n, radar), _cube(n, radar)
+    ctx.batch_run(jobs, radar, if_out=ref)
+    ctx.batch_run(jobs, radar, if_out=got, autotune=True)
+    ctx.batch_run(jobs, radar, if_out=got, autotune=True, graph=True)
+    ctx.sync()
+    assert rel_l2(to_complex(got), to_complex(ref)) <= 1e-5
+
+
+def test_batch_rejects_bad_arguments(ctx):
+    from paper_2307_15412_gb300 import rr
+    radar, grid, nt = I.workload_tiny()
+    s = I.hand_scene(0, nt)
+    ctx.scene_upload(500, s.V, s.F, s.vel)
+    out = _cube(2, radar)
+    with pytest.raises(rr.RRError, match="RR_EINVAL"):
+        ctx.batch_run([(500, grid), (500, grid)], radar, if_out=out)  # same scene twice
+    with pytest.raises(rr.RRError, match="RR_ENOTREADY"):
+        ctx.batch_run([(501, grid)], radar, if_out=out)  # never uploaded
+    with pytest.raises(rr.RRError, match="RR_EINVAL"):
+        ctx.batch_run([(500, I.RayGrid(0, 4, 0.1, 0.1))], radar, if_out=out)
+    ctx.sync()
