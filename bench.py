@@ -1,12 +1,14 @@
 """Benchmark of the radar ray-tracing hot path on GB300.
 
-One step = one radar frame of the full-frame workload through the C ABI:
-build_bvh (LBVH of a ~22k-triangle hand), trace_frame (512 x 512 rays,
-echo for 3 receive antennas), synth_if (64 chirps x 256 samples, plain FP32
-path with the FP64 carrier reduction) and range_doppler.  Eight seeded
-scenes (pose, range U(0.2, 0.6) m, radial speed U(-1, 1) m/s) are resident
-in HBM and used in turn; L2 is flushed (256 MiB write) before every timed
-step.  Device time comes from CUDA events on the library's stream.
+One step = 16 radar frames of the full-frame workload through the C ABI
+(rr_batch_run): for every frame build_bvh (LBVH of a ~22k-triangle hand),
+trace_frame (512 x 512 rays, echo for 3 receive antennas), synth_if (64
+chirps x 256 samples, plain FP32 path with the FP64 carrier reduction) and
+range_doppler, with one launch per stage over all 16 frames, replayed from
+a CUDA graph.  The 16 seeded scenes (pose, range U(0.2, 0.6) m, radial speed
+U(-1, 1) m/s) are resident in HBM; L2 is flushed (256 MiB write) before
+every timed step.  Device time comes from CUDA events on the library's
+stream.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -34,12 +36,14 @@ METRIC = "radar frames/s on 1 GB300 (trace+IF synth) vs plain FP32 path at rel-L
 WORKLOAD = ("full frame: seeded ~22k-triangle hand, range U(0.2,0.6) m, radial speed U(-1,1) m/s; "
             "512x512 rays over +-45 deg; 1 TX 3 RX (L, lambda/2); 64 chirps x 256 samples, 60-64 GHz "
             "in 64 us; LBVH build + trace + echo + FP32 IF synthesis + range-Doppler per frame")
-N_SCENES = 8
+FRAMES_PER_STEP = 16
+N_SCENES = FRAMES_PER_STEP
 FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
-# kernels per frame: LBVH build (one cluster launch), traversal, echo,
-# IF synthesis, split-K sum, range FFT rows, Doppler FFT columns
-LAUNCHES_PER_FRAME = 7
+# kernels per step (all frames together): LBVH build (one cluster launch),
+# tile numbering, traversal, hit prefix, echo, IF synthesis, split-K sum,
+# range FFT rows, Doppler FFT columns
+LAUNCHES_PER_STEP = 9
 
 
 def _peaks():
@@ -153,7 +157,7 @@ def run_reference(args):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": {"workload": WORKLOAD, "scenes": N_SCENES},
+            "data": "synthetic", "config": {"workload": WORKLOAD, "frames_per_step": FRAMES_PER_STEP},
             "cpu_baseline": {"value": value, "unit": "frames/s", "cores": cores, "kind": "oracle",
                              "sample": "every %d-th ray of each frame traced (brute force), echoed and synthesised "
                                        "in FP64, scaled x%d; range-Doppler of the IF cube in full; %.1f s of "
@@ -177,28 +181,29 @@ def run_gpu(args):
     stream = torch.cuda.current_stream(dev)
     ctx = rr.Context(local, stream)
     radar, grid, scenes = make_scenes(rank)
+    B = len(scenes)
     for k, s in enumerate(scenes):
         ctx.scene_upload(k, s.V, s.F, s.vel)
     n_rx, M, N = radar.n_rx, radar.n_chirps, radar.n_samples
-    if_out = torch.empty((n_rx, M, N, 2), dtype=torch.float32, device=dev)
+    if_out = torch.empty((B, n_rx, M, N, 2), dtype=torch.float32, device=dev)
     rd_out = torch.empty_like(if_out)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
+    jobs = [(k, grid) for k in range(B)]
 
     # hit counts per scene (deterministic per scene) for the flop count
     counts = []
-    for k in range(N_SCENES):
+    for k in range(B):
         ctx.build_bvh(k)
         box = ctx.trace_frame(k, radar, grid)
         ctx.sync()
         counts.append(box[0])
 
-    rs, gs = rr.make_radar(radar), rr.make_grid(grid)
+    def step(graph=True):
+        ctx.batch_run(jobs, radar, if_out=if_out, rd_out=rd_out, graph=graph, autotune=True)
 
-    def step(k):
-        ctx.run_frame(k, rs, gs, if_out=if_out, rd_out=rd_out)
-
+    # warm-up: the first call autotunes, the first graph call captures
     for i in range(max(args.warmup, 3)):
-        step(i % N_SCENES)
+        step()
     ctx.sync()
     torch.cuda.synchronize()
 
@@ -214,28 +219,37 @@ def run_gpu(args):
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     for i in range(K):
-        flush.zero_()  # L2 flush, outside the frame's events
-        step(i % N_SCENES)
+        flush.zero_()  # L2 flush, outside the step's events
+        step()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     ctx.sync()
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    stages = np.array([ctx.timing_read(i) for i in range(K)])  # build, trace, synth, rd, frame (ms)
+    step_ms = np.array([ctx.timing_read(i)[4] for i in range(K)])
     ctx.timing_enable(0)
-    step_ms = stages[:, 4]
-    syn_ms = stages[:, 2]
     t_dev = float(step_ms.sum()) / 1e3
     if ws > 1:
         tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_dev = float(tt.item())
-    value = ws * K / t_dev
+    value = ws * B * K / t_dev
 
-    # dominant kernel: the IF synthesis (k_synth_fp32 + its split-K sum)
-    flops = sum(8.0 * counts[i % N_SCENES] * n_rx * M * N for i in range(K))
-    achieved = flops / (float(syn_ms.sum()) / 1e3) / 1e12
+    # stage breakdown: the same steps run eagerly (a graph replay has no
+    # events between its kernels), L2 flushed before each
+    KS = max(5, min(K, 50))
+    ctx.timing_enable(KS)
+    for i in range(KS):
+        flush.zero_()
+        step(graph=False)
+    ctx.sync()
+    stages = np.array([ctx.timing_read(i) for i in range(KS)])  # build, trace, synth, rd, whole (ms)
+    ctx.timing_enable(0)
+
+    # dominant kernel: the IF synthesis (k_synth_fp32 over all frames of the step + its split-K sum)
+    flops_step = sum(8.0 * counts[k] * n_rx * M * N for k in range(B))
+    achieved = flops_step / (float(stages[:, 2].mean()) / 1e3) / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
     peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
@@ -247,35 +261,38 @@ def run_gpu(args):
         except Exception:
             traffic = None
 
-    # end to end through the public API: pinned host mesh -> device, upload,
-    # frame, range-Doppler cube back to pinned host memory, every step
+    # end to end through the public API: every step copies the frames' meshes
+    # from pinned host memory to the device, uploads them into the scene
+    # slots, runs the batch and reads the range-Doppler cubes back into
+    # pinned host memory
     pin = [(torch.from_numpy(s.V).pin_memory(), torch.from_numpy(s.F).pin_memory()) for s in scenes]
     dV = [torch.empty(p[0].shape, dtype=torch.float32, device=dev) for p in pin]
     dF = [torch.empty(p[1].shape, dtype=torch.int32, device=dev) for p in pin]
     rd_host = torch.empty(rd_out.shape, dtype=torch.float32).pin_memory()
-    K_e2e = max(1, min(K, 400))
+    K_e2e = max(1, min(K, 200))
 
-    def e2e_step(k):
-        dV[k].copy_(pin[k][0], non_blocking=True)
-        dF[k].copy_(pin[k][1], non_blocking=True)
-        ctx.scene_upload(k, dV[k], dF[k], scenes[k].vel)
-        ctx.run_frame(k, rs, gs, rd_out=rd_out)
+    def e2e_step():
+        for k in range(B):
+            dV[k].copy_(pin[k][0], non_blocking=True)
+            dF[k].copy_(pin[k][1], non_blocking=True)
+            ctx.scene_upload(k, dV[k], dF[k], scenes[k].vel)
+        step()
         rd_host.copy_(rd_out, non_blocking=True)
         torch.cuda.current_stream(dev).synchronize()
 
     for i in range(3):
-        e2e_step(i % N_SCENES)
+        e2e_step()
     if ws > 1:
         dist.barrier()
     t0 = time.perf_counter()
     for i in range(K_e2e):
-        e2e_step(i % N_SCENES)
+        e2e_step()
     t_e2e = time.perf_counter() - t0
     if ws > 1:
         tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_e2e = float(tt.item())
-    h2d = int(np.mean([s.V.nbytes + s.F.nbytes for s in scenes]))
+    h2d = int(sum(s.V.nbytes + s.F.nbytes for s in scenes))
     d2h = rd_out.numel() * 4
     ctx.sync()
 
@@ -294,20 +311,26 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "scenes": N_SCENES, "synth": "fp32",
+                "config": {"workload": WORKLOAD, "frames_per_step": B, "synth": "fp32",
                            "mean_hits_per_frame": float(np.mean(counts)),
                            "l2": "flushed before every timed step (256 MiB write, outside the events)",
-                           "parallelism": "replicas (one frame stream per GPU)"},
-                "roofline": {"bound": "alu", "kernel": "k_synth_fp32 (+ split-K sum)", "achieved": achieved,
-                             "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak, "traffic": traffic,
+                           "execution": "rr_batch_run: one launch per stage over all frames of the step, "
+                                        "replayed from a CUDA graph; autotuned tile shape and split-K",
+                           "parallelism": "replicas (independent frames per GPU)"},
+                "roofline": {"bound": "alu", "kernel": "k_synth_fp32 (+ split-K sum), all frames of a step",
+                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
+                             "traffic": traffic,
+                             "timing": "synthesis stage of %d eager steps (CUDA events on the library stream)" % KS,
                              "peak_source": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
                                             % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max)},
                 "cpu_baseline": cpu,
-                "e2e": {"value": ws * K_e2e / t_e2e, "unit": "frames/s", "h2d_bytes_per_step": h2d,
+                "e2e": {"value": ws * B * K_e2e / t_e2e, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": K_e2e},
-                "stage_ms_mean": {"build_bvh": float(stages[:, 0].mean()), "trace_frame": float(stages[:, 1].mean()),
-                                  "synth_if": float(stages[:, 2].mean()), "range_doppler": float(stages[:, 3].mean())},
-                "gpu_launches": LAUNCHES_PER_FRAME * K,
+                "stage_ms_mean_per_step": {"build_bvh": float(stages[:, 0].mean()),
+                                           "trace_frame": float(stages[:, 1].mean()),
+                                           "synth_if": float(stages[:, 2].mean()),
+                                           "range_doppler": float(stages[:, 3].mean())},
+                "gpu_launches": LAUNCHES_PER_STEP * K,
                 "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line))
@@ -319,7 +342,7 @@ def run_gpu(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=2000)
+    ap.add_argument("--steps", type=int, default=300)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")

@@ -251,13 +251,15 @@ rr_status rr_synth_if_from_hits_noalloc(const rr_radar *radar, rr_synth_variant 
 
 /* ---- per-stage timing ------------------------------------------------------ */
 
-/* Device-side stage timing of rr_run_frame with CUDA events on the
- * context's stream.  rr_timing_enable(ctx, n_slots) with n_slots > 0 creates
- * n_slots event sets; every later rr_run_frame records its stage boundaries
- * into the next set, round robin starting at slot 0 (n_slots == 0 turns
- * timing off).  rr_timing_read(ctx, slot, ms) waits for that slot's events
- * and writes 5 floats (milliseconds): build_bvh, trace_frame (traversal and
- * echo), synth_if, range_doppler (0 if not run) and the whole frame.
+/* Device-side stage timing of rr_run_frame and rr_batch_run with CUDA
+ * events on the context's stream.  rr_timing_enable(ctx, n_slots) with
+ * n_slots > 0 creates n_slots event sets; every later rr_run_frame or
+ * rr_batch_run records its stage boundaries into the next set, round robin
+ * starting at slot 0 (n_slots == 0 turns timing off).  rr_timing_read(ctx,
+ * slot, ms) waits for that slot's events and writes 5 floats
+ * (milliseconds): build_bvh, trace_frame (traversal and echo), synth_if,
+ * range_doppler (0 if not run) and the whole call.  A batch replayed from
+ * its CUDA graph records only the whole call (the four stage times read 0).
  * Returns RR_ENOTREADY if the slot was never recorded. */
 rr_status rr_timing_enable(rr_ctx *ctx, int n_slots);
 rr_status rr_timing_read(rr_ctx *ctx, int slot, float *ms_out);

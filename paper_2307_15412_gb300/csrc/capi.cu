@@ -605,10 +605,11 @@ struct BatchPlan {
 
 // Enqueues one batch on the context stream: no allocation, no host wait, so
 // the same sequence runs eagerly and under stream capture.
-cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P) {
+cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaEvent_t *ev = nullptr) {
   auto &b = c->batch;
   cudaStream_t st = c->stream;
   cudaError_t e;
+  if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b.ftab, b.h_ftab, sizeof(rr::FrameJob) * P.n_jobs, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
   if (P.n8 + P.n16 > 0 &&
       (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16), cudaMemcpyHostToDevice, st)) != cudaSuccess)
@@ -618,13 +619,17 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P) {
   if (P.n16 && (e = rr::launch_build_bvh_cluster_table(b.btab + P.n8, P.n16, 16, P.max_cap16, st)) != cudaSuccess) return e;
   for (SceneDev *s : P.others)
     if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
+  if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   if ((e = rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, P.split, b.partials, b.partials_cap, P.ifb, st)) !=
       cudaSuccess)
     return e;
+  if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   if (P.rd_out &&
       (e = rr::launch_range_doppler(P.ifb, P.n_jobs * P.rd.n_rx, P.rd.M, P.rd.N, P.window, P.rd_out, st)) != cudaSuccess)
     return e;
+  if (ev && (e = cudaEventRecord(ev[4], st)) != cudaSuccess) return e;
   return cudaSuccess;
 }
 
@@ -847,10 +852,24 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     key = fnv(key, &s->nt, sizeof(s->nt));
   }
 
+  // stage timing (rr_timing_enable) of eager runs; a graph replay records
+  // only the whole batch (slot fields 0-3 then stay 0)
+  cudaEvent_t *ev = nullptr;
+  if (c->tslots > 0) {
+    const int slot = c->tnext;
+    c->tnext = (c->tnext + 1) % c->tslots;
+    c->tev_used[slot] = 1;
+    ev = &c->tev[5 * slot];
+  }
   if ((flags & RR_BATCH_GRAPH) && b.exec && b.key == key) {
+    if (ev) {
+      RR_CUDA(c, cudaEventRecord(ev[0], c->stream), "timing");
+      for (int k = 1; k < 4; ++k) RR_CUDA(c, cudaEventRecord(ev[k], c->stream), "timing");
+    }
     RR_CUDA(c, cudaGraphLaunch(b.exec, c->stream), "batch graph launch");
+    if (ev) RR_CUDA(c, cudaEventRecord(ev[4], c->stream), "timing");
   } else {
-    RR_CUDA(c, batch_enqueue(c, P), "batch launch");
+    RR_CUDA(c, batch_enqueue(c, P, ev), "batch launch");
     if (flags & RR_BATCH_GRAPH) {
       if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
       cudaGraph_t graph = nullptr;
