@@ -188,17 +188,26 @@ rr_status synth_checks(rr_ctx *c, const rr_radar *r, rr_synth_variant v) {
   if (!pow2(r->n_samples) || r->n_samples < 16 || r->n_samples > 1024)
     return fail(c, RR_EINVAL, "n_samples=%d must be a power of two in [16,1024]", r->n_samples);
   if (r->n_chirps > 1024) return fail(c, RR_EINVAL, "n_chirps=%d > 1024", r->n_chirps);
-  if (v != RR_SYNTH_FP32) return fail(c, RR_EINVAL, "synthesis variant %d is not available in this build", (int)v);
+  if (v != RR_SYNTH_FP32 && v != RR_SYNTH_TC_BF16X3 && v != RR_SYNTH_TC_TF32)
+    return fail(c, RR_EINVAL, "unknown synthesis variant %d", (int)v);
   return RR_OK;
 }
 
-rr_status run_synth(rr_ctx *c, const rr_radar *r, const uint32_t *count, int64_t kmax, int64_t ld,
-                    const float *d, const float *a, const float *dd, float *out) {
+rr_status run_synth(rr_ctx *c, const rr_radar *r, rr_synth_variant v, const uint32_t *count, int64_t kmax,
+                    int64_t ld, const float *d, const float *a, const float *dd, float *out) {
   const rr::RadarDev rd = to_dev(r);
-  const int64_t need = rr::synth_partial_floats(rd, kmax);
+  if (v == RR_SYNTH_FP32) {
+    const int64_t need = rr::synth_partial_floats(rd, kmax);
+    RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
+    RR_CUDA(c, rr::launch_synth_fp32(rd, count, kmax, ld, d, a, dd, c->partials, c->partials_cap, out, c->stream),
+            "synth_if launch");
+    return RR_OK;
+  }
+  const int64_t need = rr::synth_tc_partial_floats(rd, kmax, 1, 0);
   RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
-  RR_CUDA(c, rr::launch_synth_fp32(rd, count, kmax, ld, d, a, dd, c->partials, c->partials_cap, out, c->stream),
-          "synth_if launch");
+  RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, 0, c->partials,
+                                 c->partials_cap, out, c->d_err, c->stream),
+          "synth_if launch (tensor cores)");
   return RR_OK;
 }
 
@@ -306,6 +315,9 @@ rr_status rr_sync(rr_ctx *c) {
   else if (err & rr::ERR_STACK_OVERFLOW) st = fail(c, RR_EOVERFLOW, "traversal stack overflow");
   else if ((err & rr::ERR_HIT_OVERFLOW) || overflow) st = fail(c, RR_EOVERFLOW, "hit list capacity exceeded");
   else if (err & rr::ERR_BAD_INPUT) st = fail(c, RR_EINVAL, "kernel rejected its input");
+  else if (err & rr::ERR_TC_BOUND)
+    st = fail(c, RR_EINVAL, "tensor-core synthesis: a path rate moves the range within a chirp tile beyond the "
+                            "first-order bound; use RR_SYNTH_FP32 for this hit list");
   return st;
 }
 
@@ -454,7 +466,8 @@ rr_status rr_synth_if(rr_ctx *c, int scene, const rr_radar *radar, rr_synth_vari
   if (radar->n_rx != s->hit_nrx) return fail(c, RR_EINVAL, "radar n_rx differs from the traced hit list");
   if (!if_out) return fail(c, RR_EINVAL, "if_out is NULL");
   DeviceGuard g(c->device);
-  return run_synth(c, radar, s->hit_count, s->hit_used_cap, s->hit_used_cap, s->hit_d, s->hit_a, s->hit_dd, if_out);
+  return run_synth(c, radar, variant, s->hit_count, s->hit_used_cap, s->hit_used_cap, s->hit_d, s->hit_a, s->hit_dd,
+                   if_out);
 }
 
 rr_status rr_synth_if_from_hits(rr_ctx *c, const rr_radar *radar, rr_synth_variant variant, int64_t K,
@@ -465,7 +478,7 @@ rr_status rr_synth_if_from_hits(rr_ctx *c, const rr_radar *radar, rr_synth_varia
   if (K < 0 || K > ((int64_t)1 << 31)) return fail(c, RR_EINVAL, "K=%lld out of range", (long long)K);
   if (!if_out || (K > 0 && (!d || !amp || !ddot))) return fail(c, RR_EINVAL, "null pointer");
   DeviceGuard g(c->device);
-  return run_synth(c, radar, nullptr, K, K, d, amp, ddot, if_out);
+  return run_synth(c, radar, variant, nullptr, K, K, d, amp, ddot, if_out);
 }
 
 rr_status rr_range_doppler(rr_ctx *c, const float *if_in, int n_rx, int n_chirps, int n_samples, int window,
@@ -599,9 +612,24 @@ struct BatchPlan {
   int64_t kmax = 0;                 // largest hit segment
   rr::RadarDev rd;
   int tw = 3, split = 0;
+  rr_synth_variant variant = RR_SYNTH_FP32;
   float *ifb = nullptr, *rd_out = nullptr;
   int window = 0;
 };
+
+int64_t batch_partials_need(const BatchPlan &P, int split) {
+  if (P.variant == RR_SYNTH_FP32) return rr::synth_batch_partial_floats(P.rd, P.kmax, P.n_jobs, split);
+  return rr::synth_tc_partial_floats(P.rd, P.kmax, P.n_jobs, split);
+}
+
+cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split) {
+  auto &b = c->batch;
+  if (P.variant == RR_SYNTH_FP32)
+    return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb,
+                                       c->stream);
+  return rr::launch_synth_tc(P.rd, P.variant == RR_SYNTH_TC_TF32, nullptr, P.kmax, 0, nullptr, nullptr, nullptr, b.ftab,
+                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, c->stream);
+}
 
 // Enqueues one batch on the context stream: no allocation, no host wait, so
 // the same sequence runs eagerly and under stream capture.
@@ -622,9 +650,7 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaEvent_t *ev = nullp
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  if ((e = rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, P.split, b.partials, b.partials_cap, P.ifb, st)) !=
-      cudaSuccess)
-    return e;
+  if ((e = batch_synth(c, P, P.split)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   if (P.rd_out &&
       (e = rr::launch_range_doppler(P.ifb, P.n_jobs * P.rd.n_rx, P.rd.M, P.rd.N, P.window, P.rd_out, st)) != cudaSuccess)
@@ -669,12 +695,10 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
   best = INFINITY;
   const int splits[4] = {0, 1, 2, 4};
   for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
-    if (rr::synth_batch_partial_floats(P.rd, P.kmax, P.n_jobs, splits[k]) > b.partials_cap) continue;
+    if (batch_partials_need(P, splits[k]) > b.partials_cap) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-      if ((e = rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, splits[k], b.partials, b.partials_cap, P.ifb,
-                                           st)) != cudaSuccess)
-        break;
+      if ((e = batch_synth(c, P, splits[k])) != cudaSuccess) break;
       if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
       float ms = 0.f;
@@ -732,6 +756,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   const int64_t total = seg[n_jobs];
   const int n_rx = radar->n_rx;
   P.rd = to_dev(radar);
+  P.variant = variant;
   P.window = window;
   P.rd_out = rd_out;
 
@@ -789,12 +814,13 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   shape = fnv(shape, &total, sizeof(total));
   const int dims[3] = {n_rx, radar->n_chirps, radar->n_samples};
   shape = fnv(shape, dims, sizeof(dims));
+  shape = fnv(shape, &variant, sizeof(variant));
   auto it = b.tuned.find(shape);
   const bool tune = (flags & RR_BATCH_AUTOTUNE) && it == b.tuned.end();
   if (it != b.tuned.end()) { P.tw = it->second.first; P.split = it->second.second; }
-  int64_t need = rr::synth_batch_partial_floats(P.rd, P.kmax, n_jobs, P.split);
+  int64_t need = batch_partials_need(P, P.split);
   if (tune)
-    for (int sp : {1, 2, 4}) need = std::max(need, rr::synth_batch_partial_floats(P.rd, P.kmax, n_jobs, sp));
+    for (int sp : {0, 1, 2, 4}) need = std::max(need, batch_partials_need(P, sp));
   if (need > b.partials_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
   RR_CUDA(c, grow(b.partials, b.partials_cap, need), "batch partials");
 

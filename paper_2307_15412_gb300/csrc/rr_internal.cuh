@@ -15,6 +15,7 @@ enum : uint32_t {
   ERR_STACK_OVERFLOW = 1u << 1,
   ERR_TIMEOUT = 1u << 2,
   ERR_BAD_INPUT = 1u << 3,
+  ERR_TC_BOUND = 1u << 4,  // tensor-core synthesis: range migration inside a tile beyond the first-order bound
 };
 
 constexpr double kC = 299792458.0;  // speed of light, m/s
@@ -168,6 +169,15 @@ cudaError_t launch_synth_fp32_bounded(const RadarDev &r, int64_t K, const float 
 int64_t synth_batch_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split);
 cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int n_jobs, int64_t kmax, int split,
                                     float *partials, int64_t partial_cap_floats, float *out, cudaStream_t st);
+// Split-time complex GEMM synthesis on tcgen05 (see synth_tc.cu): one frame
+// (jobs == nullptr: d/a/dd/ld/count/kmax) or a FrameJob table of n_jobs
+// frames; tf32 selects kind::tf32, else split-BF16x3.
+bool synth_tc_supported(const RadarDev &r);
+int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
+                            const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
+                            int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
+                            cudaStream_t st);
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st);
 

@@ -1,0 +1,517 @@
+// synth_tc.cu -- FMCW IF synthesis as a split-time complex GEMM on the
+// 5th-generation tensor cores (tcgen05, accumulators in tensor memory).
+//
+// Eq. 4 (Sec. III-B), FMCW form: sample n of chirp m of receive channel j is
+//   s[m][n] = sum_k a_k exp(-j 2 pi phi_k(m, n)),
+//   phi = c0 + c1 m + (b0 + b1 m) n      (cycles),
+//   c0 = f0 d / c (reduced modulo 1 in FP64), c1 = f0 ddot T_rep / c,
+//   b0 = S dt d / c, b1 = S dt ddot T_rep / c.
+// Time is split as t_n = t_hi + t_lo with n = LO h + l (LO = 16): the rows
+// of the GEMM are (chirp m, h) pairs, its columns the fast-time offsets l,
+// its reduction index the hits.  A tile of 128 rows holds mc chirps of
+// HE = max(HI, 8) rows each (HI = N / 16; rows h >= HI are zero padding, so
+// mc = 128 / HE <= 16).  Around the tile's centre chirp m_c, m = m_c + mu:
+//   phi = [c0 + c1 m + beta_m LO h] + beta_c l + b1 mu l,
+//   beta_m = b0 + b1 m, beta_c = b0 + b1 m_c.
+// The coupling exp(-j 2 pi b1 mu l) is expanded to third order,
+//   exp(-j x) = sum_{t<4} (-j sigma)^t l^t / t!,  sigma = 2 pi b1 mu, x = sigma l,
+// which gives four exact-rank terms per hit:
+//   s[(m,h)][l] = sum_k sum_{t<4} A_t[(m,h)][k] B_t[k][l],
+//   A_t = a e^{-j 2 pi [c0 + c1 m + beta_m LO h]} (-j sigma)^t / t!,
+//   B_t = l^t e^{-j 2 pi beta_c l}.
+// The remainder is below x^4 / 24, x <= 2 pi |b1| max|mu| (LO - 1); every
+// hit checks x <= 0.157 (remainder <= 1e-6 relative) and latches
+// ERR_TC_BOUND otherwise.  For the full-frame radar (N = 256, 8 chirps per
+// tile) at |d-dot| = 2 m/s, x = 2.2e-3; for N = 128 (16 chirps), 9.4e-3.
+//
+// Complex values are made real by doubling the columns: D = [Re | Im] is
+// 128 x 32 (M = 128, N = 32); the reduction runs over (hit, term, re/im),
+// 8 entries per hit, with B = [[Re B_t, Im B_t], [-Im B_t, Re B_t]].
+// Variants: BF16x3 (x = x_hi + x_lo in bfloat16, products lo*hi + hi*lo +
+// hi*hi, kind::f16) and TF32 (inputs rounded to TF32 in the producer,
+// kind::tf32); FP32 accumulation in tensor memory in both.
+//
+// Per CTA: one (frame, channel, 128-row tile) and an interleaved share of
+// its hits (split-K).  Blocks of 16 hits are generated by all 256 threads
+// into one of two 80 KB shared-memory stages (canonical K-major layout
+// without swizzle: 8 x 16-byte core matrices, LBO = 128 B between
+// K-neighbours, SBO = 256 B between 8-row groups) while the tensor core
+// consumes the other; thread 0 issues the MMAs and commits them to the
+// stage's mbarrier.  Every (row, hit) pair is one 16-byte core row (BF16)
+// or two (TF32); eight lanes write eight different rows of a core matrix,
+// so the stores are free of bank conflicts.  All waits are bounded; a wait
+// that runs out latches ERR_TIMEOUT, drains what it can and frees the
+// tensor memory.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rr_internal.cuh"
+
+namespace rr {
+namespace {
+
+constexpr int kTcThreads = 256;
+constexpr int kLO = 16;
+constexpr int kHitsPerBlock = 16;
+constexpr int kTerms = 4;                         // terms of the coupling expansion
+constexpr int kStageBytes = 80 * 1024;           // A region 64 KB + B region 16 KB
+constexpr int kABytes = 64 * 1024;
+constexpr int kTmemCols = 32;
+constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
+
+struct SynthTcParams {
+  const float *d, *a, *dd;
+  int64_t ld;
+  const uint32_t *count;
+  int64_t kmax;
+  int n_rx, M, N, HI, mc, n_tiles, S;
+  double f0_c, kb;
+  float c1k, b1k;
+  float *partials;        // [jobs][S][n_rx][M][N] complex
+  const FrameJob *jobs;
+  uint32_t *err;
+};
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// bounded wait for the given phase parity; false if it ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer() - t0 > kWaitNs) return false;
+  return true;
+}
+
+// Shared-memory matrix descriptor: canonical K-major layout, no swizzle.
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// Instruction descriptor: D f32, A/B of type `ab` (1 = BF16 under kind::f16,
+// 2 = TF32 under kind::tf32), both K-major, N = 32, M = 128.
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab) {
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+}
+
+template <bool TF32>
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+  if (TF32) {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc(2)), "r"(accumulate));
+  } else {
+    asm volatile(
+        "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+        "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+        "l"(da), "l"(db), "r"(idesc(1)), "r"(accumulate));
+  }
+}
+
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+
+__device__ __forceinline__ float2 cmul(float2 x, float2 y) {
+  return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
+}
+
+// e^{-j 2 pi x} for any FP32 x (x is first reduced to [-1/2, 1/2])
+__device__ __forceinline__ float2 expm2pi(float x) {
+  const float r = x - rintf(x);
+  float s, c;
+  sincospif(2.f * r, &s, &c);
+  return make_float2(c, -s);
+}
+
+__device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
+  return *reinterpret_cast<uint32_t *>(&v);
+}
+
+// 8 reduction entries of one (row or column, hit): terms t = 0..3, each
+// (re, im).  BF16x3 writes one 16-byte core row of hi parts and one of lo
+// parts; TF32 writes two 16-byte core rows (terms 0-1 at off, 2-3 at off + 128).
+template <bool TF32>
+__device__ __forceinline__ void put8(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, const float *v) {
+  if (TF32) {
+    uint32_t t[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[q]) : "f"(v[q]));
+    *reinterpret_cast<uint4 *>(hi_base + off) = make_uint4(t[0], t[1], t[2], t[3]);
+    *reinterpret_cast<uint4 *>(hi_base + off + 128) = make_uint4(t[4], t[5], t[6], t[7]);
+  } else {
+    uint32_t h[4], l[4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
+      const float2 f = __bfloat1622float2(hv);
+      const __nv_bfloat162 lv = __floats2bfloat162_rn(v[2 * q] - f.x, v[2 * q + 1] - f.y);
+      h[q] = bf16x2_bits(hv);
+      l[q] = bf16x2_bits(lv);
+    }
+    *reinterpret_cast<uint4 *>(hi_base + off) = make_uint4(h[0], h[1], h[2], h[3]);
+    *reinterpret_cast<uint4 *>(lo_base + off) = make_uint4(l[0], l[1], l[2], l[3]);
+  }
+}
+
+// byte offset of (row or column x, block-local hit k) in an operand region
+// whose MMA k-steps are `step_bytes` apart: BF16 steps hold 2 hits (core
+// K-index = hit parity), TF32 steps one hit (core K-index = term pair)
+template <bool TF32>
+__device__ __forceinline__ uint32_t op_off(int x, int k, uint32_t step_bytes) {
+  if (TF32) return (uint32_t)k * step_bytes + (uint32_t)(x >> 3) * 256u + (uint32_t)(x & 7) * 16u;
+  return (uint32_t)(k >> 1) * step_bytes + (uint32_t)(x >> 3) * 256u + (uint32_t)(k & 1) * 128u +
+         (uint32_t)(x & 7) * 16u;
+}
+
+template <bool TF32>
+__global__ void __launch_bounds__(kTcThreads, 1)
+k_synth_tc(const SynthTcParams p) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ uint32_t s_tmem;
+  __shared__ float s_c0[kHitsPerBlock], s_c1[kHitsPerBlock], s_b0[kHitsPerBlock], s_b1[kHitsPerBlock],
+      s_a[kHitsPerBlock];
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int j = blockIdx.x % p.n_rx;
+  const int tile = blockIdx.x / p.n_rx;
+  const int s_idx = blockIdx.y;
+  const int job = blockIdx.z;
+  const int m0 = tile * p.mc;
+  const int mvalid = min(p.mc, p.M - m0);
+  const float mcen = m0 + 0.5f * (float)(mvalid - 1);  // centre chirp of the tile
+  const float mu_max = 0.5f * (float)(mvalid - 1);
+
+  const float *dbase = p.d, *abase = p.a, *ddbase = p.dd;
+  int64_t ld = p.ld;
+  int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+  if (p.jobs) {
+    const FrameJob &J = p.jobs[job];
+    dbase = J.hit_d;
+    abase = J.hit_a;
+    ddbase = J.hit_dd;
+    ld = J.ld;
+    K = min((int64_t)*J.count, J.cap);
+  }
+  const float *dj = dbase + (int64_t)j * ld;
+  const float *aj = abase + (int64_t)j * ld;
+  const float *ddj = ddbase + (int64_t)j * ld;
+  const int64_t nblk_all = (K + kHitsPerBlock - 1) / kHitsPerBlock;
+  const int nb = nblk_all > s_idx ? (int)((nblk_all - 1 - s_idx) / p.S + 1) : 0;  // this CTA's blocks
+
+  // tensor memory and barriers
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kTmemCols)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (tid == 0) {
+    mbar_init(smem_u32(&s_bar[0]), 1);
+    mbar_init(smem_u32(&s_bar[1]), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  // operand-generation roles: warp w owns hits 2w and 2w + 1 of a block;
+  // lane group g = lane / 8 picks the hit (g & 1) and a half of its units
+  // (g >> 1); c8 = lane % 8 staggers the rows so that the eight lanes of a
+  // group write eight different rows of a core matrix.
+  const int g = lane >> 3, c8 = lane & 7;
+  const int kh = 2 * warp + (g & 1);               // block-local hit of this thread
+  const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
+  const int nseg = HE / 8;                         // 8-row units per chirp
+  const int unit = c8 + 8 * (g >> 1);              // 16 units per hit, 256 per block
+  const uint32_t a_step = 4096u, b_step = 1024u;
+  const uint32_t lo_a = TF32 ? 0u : 32768u, lo_b = TF32 ? 0u : 8192u;
+
+  bool ok = true;
+  int issued = 0;  // blocks whose MMAs were committed
+  for (int b = 0; b < nb && ok; ++b) {
+    const int stg = b & 1;
+    unsigned char *A = smem + stg * kStageBytes;
+    unsigned char *B = A + kABytes;
+    if (b >= 2) {  // the tensor core has finished reading this stage (block b - 2)
+      if (!mbar_wait(smem_u32(&s_bar[stg]), ((b - 2) >> 1) & 1)) {
+        atomicOr(p.err, ERR_TIMEOUT);
+        ok = false;
+      }
+    }
+    if (!__syncthreads_and(ok)) { ok = false; break; }
+    const int64_t k0 = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock;
+    if (tid < kHitsPerBlock) {
+      const int64_t k = k0 + tid;
+      float c0 = 0.f, c1 = 0.f, b0 = 0.f, b1 = 0.f, a = 0.f;
+      if (k < K) {
+        const float d = dj[k], dd = ddj[k];
+        const double x = p.f0_c * (double)d;  // FP64 carrier reduction
+        c0 = (float)(x - floor(x));
+        c1 = p.c1k * dd;
+        b0 = (float)(p.kb * (double)d);
+        b1 = p.b1k * dd;
+        a = aj[k];
+        const float xm = 6.2831853f * fabsf(b1) * mu_max * (float)(kLO - 1);
+        if (xm > 0.157f) atomicOr(p.err, ERR_TC_BOUND);
+      }
+      s_c0[tid] = c0; s_c1[tid] = c1; s_b0[tid] = b0; s_b1[tid] = b1; s_a[tid] = a;
+    }
+    __syncthreads();
+    {
+      const float c0 = s_c0[kh], c1 = s_c1[kh], b0 = s_b0[kh], b1 = s_b1[kh], a = s_a[kh];
+      // A: 16 units of 8 rows per hit (unit = chirp * nseg + segment), one per thread
+      {
+        const int mi = unit / nseg, seg = unit - mi * nseg;
+        const int m = m0 + mi;
+        const int hbase = 8 * seg;
+        float2 P = make_float2(0.f, 0.f), P0 = P, W = make_float2(1.f, 0.f);
+        float sg = 0.f;
+        if (mi < mvalid) {
+          const float fm = (float)m;
+          const float beta = fmaf(fm, b1, b0);
+          const float cyc = fmaf(fm, c1, c0);
+          W = expm2pi(beta * (float)kLO);
+          P = expm2pi(fmaf(beta * (float)kLO, (float)(hbase + c8), cyc));
+          P0 = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
+          P.x *= a; P.y *= a; P0.x *= a; P0.y *= a;
+          sg = 6.2831853f * b1 * (fm - mcen);
+        }
+        const float s2 = -0.5f * sg * sg, s3 = sg * sg * sg * (1.f / 6.f);
+        for (int q = 0; q < 8; ++q) {
+          int hh = c8 + q;
+          if (hh == 8) P = P0;
+          if (hh >= 8) hh -= 8;
+          const int h = hbase + hh;
+          const int row = mi * HE + h;
+          const bool live = h < p.HI;  // rows h >= HI pad a short chirp to 8 rows
+          float v[8];
+          // A_t = P (-j sg)^t / t!: (P), (sg Im, -sg Re), (s2 P), (-s3 Im, s3 Re)
+          v[0] = live ? P.x : 0.f;            v[1] = live ? P.y : 0.f;
+          v[2] = live ? sg * P.y : 0.f;       v[3] = live ? -sg * P.x : 0.f;
+          v[4] = live ? s2 * P.x : 0.f;       v[5] = live ? s2 * P.y : 0.f;
+          v[6] = live ? -s3 * P.y : 0.f;      v[7] = live ? s3 * P.x : 0.f;
+          put8<TF32>(A, A + lo_a, op_off<TF32>(row, kh, a_step), v);
+          P = cmul(P, W);
+        }
+      }
+      // B: columns l and 16 + l for l = c8 + 8 (g >> 1)
+      {
+        const float beta_c = fmaf(mcen, b1, b0);
+        const int l = c8 + 8 * (g >> 1);
+        const float2 B0 = expm2pi(beta_c * (float)l);
+        const float fl = (float)l;
+        float w[4] = {1.f, fl, fl * fl, fl * fl * fl};  // l^t
+        float v[8], u[8];
+#pragma unroll
+        for (int t = 0; t < kTerms; ++t) {
+          // column l (Re half): (Re B_t, -Im B_t); column 16 + l (Im half): (Im B_t, Re B_t)
+          v[2 * t] = w[t] * B0.x;  v[2 * t + 1] = -w[t] * B0.y;
+          u[2 * t] = w[t] * B0.y;  u[2 * t + 1] = w[t] * B0.x;
+        }
+        put8<TF32>(B, B + lo_b, op_off<TF32>(l, kh, b_step), v);
+        put8<TF32>(B, B + lo_b, op_off<TF32>(l + kLO, kh, b_step), u);
+      }
+    }
+    // generic-proxy smem writes -> visible to the tensor core (async proxy)
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const uint32_t a0 = smem_u32(A), bb0 = smem_u32(B);
+      if (TF32) {
+#pragma unroll 1
+        for (int ks = 0; ks < kHitsPerBlock; ++ks)
+          mma<true>(tmem, smem_desc(a0 + ks * a_step, 128, 256), smem_desc(bb0 + ks * b_step, 128, 256),
+                    (b > 0 || ks > 0) ? 1u : 0u);
+      } else {
+#pragma unroll 1
+        for (int ks = 0; ks < kHitsPerBlock / 2; ++ks) {
+          const uint64_t ahi = smem_desc(a0 + ks * a_step, 128, 256), alo = smem_desc(a0 + lo_a + ks * a_step, 128, 256);
+          const uint64_t bhi = smem_desc(bb0 + ks * b_step, 128, 256), blo = smem_desc(bb0 + lo_b + ks * b_step, 128, 256);
+          mma<false>(tmem, alo, bhi, (b > 0 || ks > 0) ? 1u : 0u);
+          mma<false>(tmem, ahi, blo, 1u);
+          mma<false>(tmem, ahi, bhi, 1u);
+        }
+      }
+      mma_commit(smem_u32(&s_bar[stg]));
+    }
+    issued = b + 1;
+  }
+
+  // wait for the last committed block's MMAs (they complete in issue order)
+  bool have = issued > 0;
+  if (have) {
+    if (!mbar_wait(smem_u32(&s_bar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1)) {
+      atomicOr(p.err, ERR_TIMEOUT);
+      have = false;
+    }
+  }
+  have = have && ok;
+  have = __syncthreads_and(have) != 0;
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+
+  // epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes), 32 columns each
+  if (warp < 4) {
+    const int row = 32 * warp + lane;
+    const int HEo = p.HI < 8 ? 8 : p.HI;
+    const int mi = row / HEo, h = row - mi * HEo;
+    const int m = m0 + mi;
+    float v[32];
+    if (have) {
+      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
+      uint32_t r[32];
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+          : "r"(taddr));
+      asm volatile(
+          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+          : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+            "=r"(r[30]), "=r"(r[31])
+          : "r"(taddr + 16u));
+      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
+    } else {
+#pragma unroll
+      for (int q = 0; q < 32; ++q) v[q] = 0.f;
+    }
+    if (mi < mvalid && h < p.HI) {
+      float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
+                                                                    (int64_t)p.N + (int64_t)h * kLO));
+#pragma unroll
+      for (int q = 0; q < 8; ++q) o[q] = make_float4(v[2 * q], v[kLO + 2 * q], v[2 * q + 1], v[kLO + 2 * q + 1]);
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 0) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
+  }
+}
+
+__global__ void k_tc_reduce(const float2 *__restrict__ partials, int S, int64_t total, int n_jobs,
+                            float2 *__restrict__ out) {
+  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (x >= total * n_jobs) return;
+  const int64_t job = x / total, i = x - job * total;
+  const float2 *pj = partials + job * S * total;
+  float2 s = pj[i];
+  for (int k = 1; k < S; ++k) {
+    const float2 v = pj[(int64_t)k * total + i];
+    s.x += v.x;
+    s.y += v.y;
+  }
+  out[x] = s;
+}
+
+struct TcPlan {
+  int HI, mc, n_tiles, S;
+};
+
+TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  TcPlan pl;
+  pl.HI = r.N / kLO;
+  pl.mc = 128 / (pl.HI < 8 ? 8 : pl.HI);
+  pl.n_tiles = (r.M + pl.mc - 1) / pl.mc;
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t ctas = (int64_t)pl.n_tiles * r.n_rx * n_jobs;
+  const int64_t blocks = (kmax + kHitsPerBlock - 1) / kHitsPerBlock;
+  int64_t S = split > 0 ? split : (sms + ctas - 1) / ctas;
+  if (S > blocks) S = blocks;
+  if (S < 1) S = 1;
+  pl.S = (int)S;
+  return pl;
+}
+
+template <bool TF32>
+cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
+  static bool attr_set = false;
+  const int smem = 2 * kStageBytes;
+  if (!attr_set) {
+    cudaError_t e = cudaFuncSetAttribute(k_synth_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    attr_set = true;
+  }
+  dim3 grid(p.n_tiles * p.n_rx, p.S, n_jobs);
+  k_synth_tc<TF32><<<grid, kTcThreads, smem, st>>>(p);
+  return cudaGetLastError();
+}
+
+}  // namespace
+
+bool synth_tc_supported(const RadarDev &r) {
+  return r.N >= 16 && r.N <= 2048 && (r.N & (r.N - 1)) == 0 && r.M >= 1;
+}
+
+int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  const TcPlan pl = tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split);
+  return (int64_t)n_jobs * pl.S * r.n_rx * r.M * r.N * 2;
+}
+
+cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
+                            const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
+                            int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
+                            cudaStream_t st) {
+  if (!synth_tc_supported(r) || n_jobs < 1) return cudaErrorInvalidValue;
+  const TcPlan pl = tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split);
+  const int64_t total = (int64_t)r.n_rx * r.M * r.N;
+  if ((int64_t)n_jobs * pl.S * total * 2 > partial_cap_floats) return cudaErrorInvalidValue;
+  SynthTcParams p;
+  p.d = d; p.a = a; p.dd = dd; p.ld = ld;
+  p.count = count; p.kmax = kmax;
+  p.n_rx = r.n_rx; p.M = r.M; p.N = r.N;
+  p.HI = pl.HI; p.mc = pl.mc; p.n_tiles = pl.n_tiles; p.S = pl.S;
+  p.f0_c = r.f0 / kC;
+  p.kb = r.slope * r.dt / kC;
+  p.c1k = (float)(r.f0 * r.t_rep / kC);
+  p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
+  p.partials = partials;
+  p.jobs = jobs;
+  p.err = err;
+  cudaError_t e = tf32 ? launch_tc<true>(p, n_jobs, st) : launch_tc<false>(p, n_jobs, st);
+  if (e != cudaSuccess) return e;
+  const int threads = 256;
+  const int64_t blocks = (total * n_jobs + threads - 1) / threads;
+  k_tc_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total, n_jobs,
+                                                    reinterpret_cast<float2 *>(out));
+  return cudaGetLastError();
+}
+
+}  // namespace rr

@@ -1,0 +1,171 @@
+"""GPU: IF synthesis as a split-time complex GEMM on the tensor cores
+(RR_SYNTH_TC_BF16X3, RR_SYNTH_TC_TF32) against the FP64 oracle.
+
+Tolerances (relative L2 over the cube, oracle fed the same float32 hits):
+  * split-BF16x3: <= 1e-4.  Each operand is carried as bf16 hi + lo (about
+    2^-17 relative representation error) and the dropped lo*lo product is
+    below 2^-16 relative, so one term is off by ~1e-5 at most; the sum of K
+    terms of random phase keeps that order.  The first-order chirp-coupling
+    expansion adds < 5e-7 (its bound is checked on the device).
+  * TF32: <= 1e-3 (the bound stated for the tensor-core variants).  Inputs
+    are rounded to 10 explicit mantissa bits (2^-11 relative), so a product
+    is off by up to ~1e-3 and the sum by ~2-5e-4 in rel-L2.
+"""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import rel_l2, to_complex
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {1: 1e-4, 2: 1e-3}   # variant -> rel-L2 bound
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def _synth(ctx, radar, d, a, dd, variant):
+    out = torch.full((radar.n_rx, radar.n_chirps, radar.n_samples, 2), 3.0, dtype=torch.float32, device="cuda:0")
+    dt = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    ctx.synth_if_from_hits(radar, dt(d), dt(a), dt(dd), out, variant=variant)
+    ctx.sync()
+    return to_complex(out)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_single_tile_small(ctx, variant):
+    """One 128-row tile (8 chirps x 16 rows), one block of 32 hits."""
+    radar = I.Radar(n_samples=256, n_chirps=8)
+    d, a, dd = I.random_hits(1, 32, 1)
+    got = _synth(ctx, radar, d, a, dd, variant)
+    ref = oracle.synth(d, a, dd, radar)
+    assert rel_l2(got, ref) <= TOL[variant], rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+@pytest.mark.parametrize("N,M,n_rx,K", [
+    (16, 1, 1, 1), (16, 200, 2, 77), (32, 3, 2, 257), (64, 1, 1, 300), (64, 5, 3, 1000), (128, 32, 3, 2049),
+    (256, 64, 3, 4000), (256, 1, 1, 6000), (256, 13, 1, 33), (512, 2, 1, 513), (1024, 1, 1, 700),
+    (1024, 3, 2, 100), (256, 7, 2, 1)])
+def test_tc_synth_from_hits_parity(ctx, variant, N, M, n_rx, K):
+    """Tiles with a ragged chirp tail, hit counts that are not multiples of
+    the 32-hit block, 1 to 128 chirps per tile (N = 1024 down to 16)."""
+    radar = I.Radar(n_samples=N, n_chirps=M, rx=I.rx_l_array()[:n_rx])
+    d, a, dd = I.random_hits(100 + K, K, n_rx)
+    got = _synth(ctx, radar, d, a, dd, variant)
+    ref = oracle.synth(d, a, dd, radar)
+    assert rel_l2(got, ref) <= TOL[variant], rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_empty_hit_list_gives_zeros(ctx, variant):
+    radar = I.Radar(n_samples=64, n_chirps=4, rx=I.rx_l_array())
+    out = torch.full((3, 4, 64, 2), 7.0, dtype=torch.float32, device="cuda:0")
+    e = torch.empty((3, 0), dtype=torch.float32, device="cuda:0")
+    ctx.synth_if_from_hits(radar, e, e, e, out, variant=variant)
+    ctx.sync()
+    assert torch.count_nonzero(out).item() == 0
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_max_hits(ctx, variant):
+    """2^18 hits into one 256-sample chirp (the precision workload's largest
+    hit list), split into t = 16 hi x 16 lo."""
+    radar = I.Radar(n_samples=256, n_chirps=1)
+    K = 1 << 18
+    d, a, dd = I.random_hits(9, K, 1)
+    got = _synth(ctx, radar, d, a, dd, variant)
+    ref = oracle.synth(d, a, dd, radar)
+    assert rel_l2(got, ref) <= TOL[variant], rel_l2(got, ref)
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_point_target_bins(ctx, variant):
+    """Point target at integer range and Doppler bins through the TC path
+    and the range-Doppler map: peak at (q0 + M/2, k0)."""
+    M, N = 64, 256
+    radar = I.Radar(n_samples=N, n_chirps=M)
+    k0, q0 = 37, 5
+    d = np.array([[k0 * I.C_LIGHT / radar.bandwidth]], np.float32)
+    dd = np.array([[q0 * I.C_LIGHT / (radar.f0 * radar.t_rep * M)]], np.float32)
+    x = _synth(ctx, radar, d, np.ones((1, 1), np.float32), dd, variant)
+    xin = torch.from_numpy(np.stack([x.real, x.imag], -1).astype(np.float32)).cuda()
+    rd = torch.empty((1, M, N, 2), dtype=torch.float32, device="cuda:0")
+    ctx.range_doppler(xin, rd)
+    ctx.sync()
+    X = np.abs(to_complex(rd))[0]
+    q, k = np.unravel_index(np.argmax(X), X.shape)
+    assert (q, k) == (q0 + M // 2, k0)
+
+
+def test_tc_rejects_path_rates_beyond_the_expansion_bound(ctx):
+    """A path rate of 1000 m/s moves the range inside a 32-chirp tile far
+    beyond the first-order bound: the device flags it, rr_sync reports."""
+    from paper_2307_15412_gb300 import rr
+    radar = I.Radar(n_samples=64, n_chirps=32)
+    d, a, dd = I.random_hits(3, 64, 1)
+    dd[:] = 1000.0
+    out = torch.empty((1, 32, 64, 2), dtype=torch.float32, device="cuda:0")
+    dt = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
+    ctx.synth_if_from_hits(radar, dt(d), dt(a), dt(dd), out, variant=1)
+    with pytest.raises(rr.RRError, match="first-order bound"):
+        ctx.sync()
+    ctx.sync()  # the error word was cleared
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_full_frame_end_to_end(ctx, variant):
+    """Full-frame hand (trace on the GPU), TC synthesis vs the FP32 path on
+    the same frame and vs the oracle's synthesis of the GPU's hit list."""
+    from gpu_helpers import gpu_hits
+    radar, grid, nt = I.workload_full_frame()
+    s = I.hand_scene(21, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+    ctx.scene_upload(9, s.V, s.F, s.vel)
+    ctx.build_bvh(9)
+    box = ctx.trace_frame(9, radar, grid)
+    ctx.sync()
+    K = box[0]
+    cube = (radar.n_rx, radar.n_chirps, radar.n_samples, 2)
+    f32 = torch.empty(cube, dtype=torch.float32, device="cuda:0")
+    tc = torch.empty_like(f32)
+    ctx.synth_if(9, radar, f32)
+    ctx.synth_if(9, radar, tc, variant=variant)
+    ctx.sync()
+    h = gpu_hits(ctx, 9, radar.n_rx, K)
+    ref = oracle.synth(h["d"], h["a"], h["dd"], radar)
+    assert rel_l2(to_complex(tc), ref) <= TOL[variant]
+    assert rel_l2(to_complex(f32), ref) <= 1e-5
+
+
+@pytest.mark.parametrize("variant", [1, 2])
+def test_tc_batch_matches_single_frames(ctx, variant):
+    import math
+    radar = I.Radar(n_samples=128, n_chirps=32, rx=I.rx_l_array())
+    grids = [I.RayGrid(n, n, math.radians(45), math.radians(45)) for n in (128, 256, 96, 200)]
+    for k in range(4):
+        s = I.hand_scene(80 + k, (5000, 20000, 12000, 40000)[k], range_m=I.FULL_FRAME_RANGE,
+                         speed=I.FULL_FRAME_SPEED)
+        ctx.scene_upload(600 + k, s.V, s.F, s.vel)
+    out = torch.empty((4, 3, 32, 128, 2), dtype=torch.float32, device="cuda:0")
+    ctx.batch_run([(600 + k, g) for k, g in enumerate(grids)], radar, if_out=out, variant=variant)
+    ctx.sync()
+    got = to_complex(out)
+    for k in range(4):
+        one = torch.empty((3, 32, 128, 2), dtype=torch.float32, device="cuda:0")
+        ctx.run_frame(600 + k, radar, grids[k], if_out=one, variant=0)
+        ctx.sync()
+        assert rel_l2(got[k], to_complex(one)) <= TOL[variant]
