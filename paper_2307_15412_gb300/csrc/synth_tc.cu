@@ -24,24 +24,29 @@
 // ERR_TC_BOUND otherwise.  For the full-frame radar (N = 256, 8 chirps per
 // tile) at |d-dot| = 2 m/s, x = 2.2e-3; for N = 128 (16 chirps), 9.4e-3.
 //
-// Complex values are made real by doubling the columns: D = [Re | Im] is
-// 128 x 32 (M = 128, N = 32); the reduction runs over (hit, term, re/im),
-// 8 entries per hit, with B = [[Re B_t, Im B_t], [-Im B_t, Re B_t]].
-// Variants: BF16x3 (x = x_hi + x_lo in bfloat16, products lo*hi + hi*lo +
-// hi*hi, kind::f16) and TF32 (inputs rounded to TF32 in the producer,
-// kind::tf32); FP32 accumulation in tensor memory in both.
+// The b1 factor of each term belongs to the hit and mu to the row, so the
+// terms are carried in the GEMM's N dimension:
+//   D_t[(m,h)][l] = sum_k A[(m,h)][k] B_t[k][l],   A = a e^{-j 2 pi [c0 + c1 m + beta_m LO h]},
+//                                                  B_t = (b1 l)^t e^{-j 2 pi beta_c l},
+//   s[(m,h)][l] = sum_t kappa_t(mu) D_t,           kappa_t = (-j 2 pi mu)^t / t!,
+// with kappa applied per row in the epilogue.  Complex values are made real
+// by doubling the columns: D = [t][Re | Im][l] is 128 x 128 (M = N = 128);
+// the reduction runs over (hit, re/im), 2 entries per hit, with
+// B = [[Re B_t, Im B_t], [-Im B_t, Re B_t]].  Variants: BF16x3
+// (x = x_hi + x_lo in bfloat16, products lo*hi + hi*lo + hi*hi, kind::f16)
+// and TF32 (inputs rounded to TF32 in the producer, kind::tf32); FP32
+// accumulation in tensor memory (128 columns) in both.
 //
 // Per CTA: one (frame, channel, 128-row tile) and an interleaved share of
-// its hits (split-K).  Blocks of 16 hits are generated by all 256 threads
-// into one of two 80 KB shared-memory stages (canonical K-major layout
+// its hits (split-K).  Blocks of 32 hits are generated by all 256 threads
+// into one of three 64 KB shared-memory stages (canonical K-major layout
 // without swizzle: 8 x 16-byte core matrices, LBO = 128 B between
 // K-neighbours, SBO = 256 B between 8-row groups) while the tensor core
-// consumes the other; thread 0 issues the MMAs and commits them to the
-// stage's mbarrier.  Every (row, hit) pair is one 16-byte core row (BF16)
-// or two (TF32); eight lanes write eight different rows of a core matrix,
-// so the stores are free of bank conflicts.  All waits are bounded; a wait
-// that runs out latches ERR_TIMEOUT, drains what it can and frees the
-// tensor memory.
+// consumes the others; thread 0 issues the MMAs and commits them to the
+// stage's mbarrier.  A warp writes 4 hits x 8 rows (or columns) per store,
+// the rows staggered so that they fill one 128-byte bank window.  All waits
+// are bounded; a wait that runs out latches ERR_TIMEOUT, drains what it can
+// and frees the tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -54,11 +59,12 @@ namespace {
 
 constexpr int kTcThreads = 256;
 constexpr int kLO = 16;
-constexpr int kHitsPerBlock = 16;
+constexpr int kHitsPerBlock = 32;
 constexpr int kTerms = 4;                         // terms of the coupling expansion
-constexpr int kStageBytes = 80 * 1024;           // A region 64 KB + B region 16 KB
-constexpr int kABytes = 64 * 1024;
-constexpr int kTmemCols = 32;
+constexpr int kStages = 3;
+constexpr int kStageBytes = 64 * 1024;           // A region 32 KB + B region 32 KB
+constexpr int kABytes = 32 * 1024;
+constexpr int kTmemCols = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 struct SynthTcParams {
@@ -116,9 +122,9 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor: D f32, A/B of type `ab` (1 = BF16 under kind::f16,
-// 2 = TF32 under kind::tf32), both K-major, N = 32, M = 128.
+// 2 = TF32 under kind::tf32), both K-major, N = 128, M = 128.
 __host__ __device__ constexpr uint32_t idesc(uint32_t ab) {
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((32u >> 3) << 17) | ((128u >> 4) << 24);
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 template <bool TF32>
@@ -157,47 +163,42 @@ __device__ __forceinline__ uint32_t bf16x2_bits(__nv_bfloat162 v) {
   return *reinterpret_cast<uint32_t *>(&v);
 }
 
-// 8 reduction entries of one (row or column, hit): terms t = 0..3, each
-// (re, im).  BF16x3 writes one 16-byte core row of hi parts and one of lo
-// parts; TF32 writes two 16-byte core rows (terms 0-1 at off, 2-3 at off + 128).
+// The 2 reduction entries (re, im) of one (row or column, hit): BF16x3
+// writes a 4-byte hi pair and a 4-byte lo pair, TF32 one 8-byte pair.
 template <bool TF32>
-__device__ __forceinline__ void put8(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, const float *v) {
+__device__ __forceinline__ void put2(unsigned char *hi_base, unsigned char *lo_base, uint32_t off, float x, float y) {
   if (TF32) {
-    uint32_t t[8];
-#pragma unroll
-    for (int q = 0; q < 8; ++q) asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(t[q]) : "f"(v[q]));
-    *reinterpret_cast<uint4 *>(hi_base + off) = make_uint4(t[0], t[1], t[2], t[3]);
-    *reinterpret_cast<uint4 *>(hi_base + off + 128) = make_uint4(t[4], t[5], t[6], t[7]);
+    uint32_t tx, ty;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tx) : "f"(x));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ty) : "f"(y));
+    *reinterpret_cast<uint2 *>(hi_base + off) = make_uint2(tx, ty);
   } else {
-    uint32_t h[4], l[4];
-#pragma unroll
-    for (int q = 0; q < 4; ++q) {
-      const __nv_bfloat162 hv = __floats2bfloat162_rn(v[2 * q], v[2 * q + 1]);
-      const float2 f = __bfloat1622float2(hv);
-      const __nv_bfloat162 lv = __floats2bfloat162_rn(v[2 * q] - f.x, v[2 * q + 1] - f.y);
-      h[q] = bf16x2_bits(hv);
-      l[q] = bf16x2_bits(lv);
-    }
-    *reinterpret_cast<uint4 *>(hi_base + off) = make_uint4(h[0], h[1], h[2], h[3]);
-    *reinterpret_cast<uint4 *>(lo_base + off) = make_uint4(l[0], l[1], l[2], l[3]);
+    const __nv_bfloat162 hv = __floats2bfloat162_rn(x, y);
+    const float2 f = __bfloat1622float2(hv);
+    const __nv_bfloat162 lv = __floats2bfloat162_rn(x - f.x, y - f.y);
+    *reinterpret_cast<uint32_t *>(hi_base + off) = bf16x2_bits(hv);
+    *reinterpret_cast<uint32_t *>(lo_base + off) = bf16x2_bits(lv);
   }
 }
 
-// byte offset of (row or column x, block-local hit k) in an operand region
-// whose MMA k-steps are `step_bytes` apart: BF16 steps hold 2 hits (core
-// K-index = hit parity), TF32 steps one hit (core K-index = term pair)
+// Byte offset of (row or column x, block-local hit k) in an operand region
+// of 4 KB per MMA k-step (128 rows x 32 bytes).  BF16: 8 hits per k-step,
+// core K-index (k % 8) / 4, 4 bytes per hit in a core row; TF32: 4 hits
+// per k-step, core K-index (k % 4) / 2, 8 bytes per hit.
 template <bool TF32>
-__device__ __forceinline__ uint32_t op_off(int x, int k, uint32_t step_bytes) {
-  if (TF32) return (uint32_t)k * step_bytes + (uint32_t)(x >> 3) * 256u + (uint32_t)(x & 7) * 16u;
-  return (uint32_t)(k >> 1) * step_bytes + (uint32_t)(x >> 3) * 256u + (uint32_t)(k & 1) * 128u +
-         (uint32_t)(x & 7) * 16u;
+__device__ __forceinline__ uint32_t op_off(int x, int k) {
+  if (TF32)
+    return (uint32_t)(k >> 2) * 4096u + (uint32_t)(x >> 3) * 256u + (uint32_t)((k >> 1) & 1) * 128u +
+           (uint32_t)(x & 7) * 16u + (uint32_t)(k & 1) * 8u;
+  return (uint32_t)(k >> 3) * 4096u + (uint32_t)(x >> 3) * 256u + (uint32_t)((k >> 2) & 1) * 128u +
+         (uint32_t)(x & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
 
 template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_synth_tc(const SynthTcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[2];
+  __shared__ __align__(8) uint64_t s_bar[kStages];
   __shared__ uint32_t s_tmem;
   __shared__ float s_c0[kHitsPerBlock], s_c1[kHitsPerBlock], s_b0[kHitsPerBlock], s_b1[kHitsPerBlock],
       s_a[kHitsPerBlock];
@@ -237,8 +238,7 @@ k_synth_tc(const SynthTcParams p) {
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    mbar_init(smem_u32(&s_bar[0]), 1);
-    mbar_init(smem_u32(&s_bar[1]), 1);
+    for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&s_bar[q]), 1);
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -246,26 +246,23 @@ k_synth_tc(const SynthTcParams p) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
 
-  // operand-generation roles: warp w owns hits 2w and 2w + 1 of a block;
-  // lane group g = lane / 8 picks the hit (g & 1) and a half of its units
-  // (g >> 1); c8 = lane % 8 staggers the rows so that the eight lanes of a
-  // group write eight different rows of a core matrix.
+  // operand-generation roles: a warp writes 4 hits (lane group g = lane / 8
+  // gives k % 4) x 8 rows or columns (c8 = lane % 8) per store; the 8 lanes
+  // of a group handle 8 different 8-row units and walk their rows from a
+  // staggered start, so each store fills one 128-byte bank window.
   const int g = lane >> 3, c8 = lane & 7;
-  const int kh = 2 * warp + (g & 1);               // block-local hit of this thread
   const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
-  const int nseg = HE / 8;                         // 8-row units per chirp
-  const int unit = c8 + 8 * (g >> 1);              // 16 units per hit, 256 per block
-  const uint32_t a_step = 4096u, b_step = 1024u;
-  const uint32_t lo_a = TF32 ? 0u : 32768u, lo_b = TF32 ? 0u : 8192u;
+  const int nseg = HE / 8;                         // 8-row units per chirp (16 units per tile)
+  const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 16384u;
 
   bool ok = true;
   int issued = 0;  // blocks whose MMAs were committed
   for (int b = 0; b < nb && ok; ++b) {
-    const int stg = b & 1;
+    const int stg = b % kStages;
     unsigned char *A = smem + stg * kStageBytes;
     unsigned char *B = A + kABytes;
-    if (b >= 2) {  // the tensor core has finished reading this stage (block b - 2)
-      if (!mbar_wait(smem_u32(&s_bar[stg]), ((b - 2) >> 1) & 1)) {
+    if (b >= kStages) {  // the tensor core has finished reading this stage (block b - kStages)
+      if (!mbar_wait(smem_u32(&s_bar[stg]), ((b - kStages) / kStages) & 1)) {
         atomicOr(p.err, ERR_TIMEOUT);
         ok = false;
       }
@@ -289,59 +286,53 @@ k_synth_tc(const SynthTcParams p) {
       s_c0[tid] = c0; s_c1[tid] = c1; s_b0[tid] = b0; s_b1[tid] = b1; s_a[tid] = a;
     }
     __syncthreads();
-    {
+#pragma unroll 1
+    for (int it = 0; it < 2; ++it) {
+      const int slice = warp + 8 * it;           // 16 slices: 8 hit quads x 2 unit octets
+      const int kq = slice & 7, uo = slice >> 3;
+      const int kh = 4 * kq + g;                 // block-local hit
       const float c0 = s_c0[kh], c1 = s_c1[kh], b0 = s_b0[kh], b1 = s_b1[kh], a = s_a[kh];
-      // A: 16 units of 8 rows per hit (unit = chirp * nseg + segment), one per thread
+      // A: unit u = 8 rows (chirp mi, segment seg) of this hit
       {
-        const int mi = unit / nseg, seg = unit - mi * nseg;
-        const int m = m0 + mi;
+        const int u = 8 * uo + c8;
+        const int mi = u / nseg, seg = u - mi * nseg;
         const int hbase = 8 * seg;
         float2 P = make_float2(0.f, 0.f), P0 = P, W = make_float2(1.f, 0.f);
-        float sg = 0.f;
         if (mi < mvalid) {
-          const float fm = (float)m;
+          const float fm = (float)(m0 + mi);
           const float beta = fmaf(fm, b1, b0);
           const float cyc = fmaf(fm, c1, c0);
           W = expm2pi(beta * (float)kLO);
           P = expm2pi(fmaf(beta * (float)kLO, (float)(hbase + c8), cyc));
           P0 = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
           P.x *= a; P.y *= a; P0.x *= a; P0.y *= a;
-          sg = 6.2831853f * b1 * (fm - mcen);
         }
-        const float s2 = -0.5f * sg * sg, s3 = sg * sg * sg * (1.f / 6.f);
+#pragma unroll
         for (int q = 0; q < 8; ++q) {
           int hh = c8 + q;
           if (hh == 8) P = P0;
           if (hh >= 8) hh -= 8;
           const int h = hbase + hh;
-          const int row = mi * HE + h;
           const bool live = h < p.HI;  // rows h >= HI pad a short chirp to 8 rows
-          float v[8];
-          // A_t = P (-j sg)^t / t!: (P), (sg Im, -sg Re), (s2 P), (-s3 Im, s3 Re)
-          v[0] = live ? P.x : 0.f;            v[1] = live ? P.y : 0.f;
-          v[2] = live ? sg * P.y : 0.f;       v[3] = live ? -sg * P.x : 0.f;
-          v[4] = live ? s2 * P.x : 0.f;       v[5] = live ? s2 * P.y : 0.f;
-          v[6] = live ? -s3 * P.y : 0.f;      v[7] = live ? s3 * P.x : 0.f;
-          put8<TF32>(A, A + lo_a, op_off<TF32>(row, kh, a_step), v);
+          put2<TF32>(A, A + lo_a, op_off<TF32>(mi * HE + h, kh), live ? P.x : 0.f, live ? P.y : 0.f);
           P = cmul(P, W);
         }
       }
-      // B: columns l and 16 + l for l = c8 + 8 (g >> 1)
+      // B: l = c8 + 8 uo, terms t = 0..3, halves Re / Im: column 32 t + 16 half + l
       {
         const float beta_c = fmaf(mcen, b1, b0);
-        const int l = c8 + 8 * (g >> 1);
+        const int l = c8 + 8 * uo;
         const float2 B0 = expm2pi(beta_c * (float)l);
-        const float fl = (float)l;
-        float w[4] = {1.f, fl, fl * fl, fl * fl * fl};  // l^t
-        float v[8], u[8];
+        const float bl = b1 * (float)l;
+        float w = 1.f;  // (b1 l)^t
 #pragma unroll
         for (int t = 0; t < kTerms; ++t) {
-          // column l (Re half): (Re B_t, -Im B_t); column 16 + l (Im half): (Im B_t, Re B_t)
-          v[2 * t] = w[t] * B0.x;  v[2 * t + 1] = -w[t] * B0.y;
-          u[2 * t] = w[t] * B0.y;  u[2 * t + 1] = w[t] * B0.x;
+          const float re = w * B0.x, im = w * B0.y;
+          // entries (c = 0: multiplies Re A, c = 1: multiplies Im A)
+          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, kh), re, -im);        // Re half
+          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, kh), im, re);   // Im half
+          w *= bl;
         }
-        put8<TF32>(B, B + lo_b, op_off<TF32>(l, kh, b_step), v);
-        put8<TF32>(B, B + lo_b, op_off<TF32>(l + kLO, kh, b_step), u);
       }
     }
     // generic-proxy smem writes -> visible to the tensor core (async proxy)
@@ -352,14 +343,14 @@ k_synth_tc(const SynthTcParams p) {
       const uint32_t a0 = smem_u32(A), bb0 = smem_u32(B);
       if (TF32) {
 #pragma unroll 1
-        for (int ks = 0; ks < kHitsPerBlock; ++ks)
-          mma<true>(tmem, smem_desc(a0 + ks * a_step, 128, 256), smem_desc(bb0 + ks * b_step, 128, 256),
+        for (int ks = 0; ks < kHitsPerBlock / 4; ++ks)
+          mma<true>(tmem, smem_desc(a0 + ks * 4096u, 128, 256), smem_desc(bb0 + ks * 4096u, 128, 256),
                     (b > 0 || ks > 0) ? 1u : 0u);
       } else {
 #pragma unroll 1
-        for (int ks = 0; ks < kHitsPerBlock / 2; ++ks) {
-          const uint64_t ahi = smem_desc(a0 + ks * a_step, 128, 256), alo = smem_desc(a0 + lo_a + ks * a_step, 128, 256);
-          const uint64_t bhi = smem_desc(bb0 + ks * b_step, 128, 256), blo = smem_desc(bb0 + lo_b + ks * b_step, 128, 256);
+        for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
+          const uint64_t ahi = smem_desc(a0 + ks * 4096u, 128, 256), alo = smem_desc(a0 + lo_a + ks * 4096u, 128, 256);
+          const uint64_t bhi = smem_desc(bb0 + ks * 4096u, 128, 256), blo = smem_desc(bb0 + lo_b + ks * 4096u, 128, 256);
           mma<false>(tmem, alo, bhi, (b > 0 || ks > 0) ? 1u : 0u);
           mma<false>(tmem, ahi, blo, 1u);
           mma<false>(tmem, ahi, bhi, 1u);
@@ -373,7 +364,7 @@ k_synth_tc(const SynthTcParams p) {
   // wait for the last committed block's MMAs (they complete in issue order)
   bool have = issued > 0;
   if (have) {
-    if (!mbar_wait(smem_u32(&s_bar[(issued - 1) & 1]), ((issued - 1) >> 1) & 1)) {
+    if (!mbar_wait(smem_u32(&s_bar[(issued - 1) % kStages]), ((issued - 1) / kStages) & 1)) {
       atomicOr(p.err, ERR_TIMEOUT);
       have = false;
     }
@@ -382,39 +373,52 @@ k_synth_tc(const SynthTcParams p) {
   have = __syncthreads_and(have) != 0;
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
 
-  // epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes), 32 columns each
+  // epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes); per fast-time
+  // offset l the four terms combine as s = sum_t kappa_t D_t with
+  // kappa = (1, -j sg, -sg^2 / 2, j sg^3 / 6), sg = 2 pi mu
   if (warp < 4) {
     const int row = 32 * warp + lane;
     const int HEo = p.HI < 8 ? 8 : p.HI;
     const int mi = row / HEo, h = row - mi * HEo;
     const int m = m0 + mi;
-    float v[32];
+    const float sg = 6.2831853f * ((float)m - mcen);
+    const float k2 = -0.5f * sg * sg, k3 = sg * sg * sg * (1.f / 6.f);
+    float re[kLO], im[kLO];
+#pragma unroll
+    for (int l = 0; l < kLO; ++l) re[l] = im[l] = 0.f;
     if (have) {
-      const uint32_t taddr = tmem + ((uint32_t)(32 * warp) << 16);
-      uint32_t r[32];
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-            "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-          : "r"(taddr));
-      asm volatile(
-          "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-          : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-            "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-            "=r"(r[30]), "=r"(r[31])
-          : "r"(taddr + 16u));
-      asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = __uint_as_float(r[q]);
-    } else {
+      for (int t = 0; t < kTerms; ++t) {
+        uint32_t r[32];
+        const uint32_t taddr = tbase + 32u * t;
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + 16u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int q = 0; q < 32; ++q) v[q] = 0.f;
+        for (int l = 0; l < kLO; ++l) {
+          const float dr = __uint_as_float(r[l]), di = __uint_as_float(r[kLO + l]);
+          if (t == 0) { re[l] += dr; im[l] += di; }
+          else if (t == 1) { re[l] += sg * di; im[l] -= sg * dr; }   // (-j sg)(dr + j di)
+          else if (t == 2) { re[l] += k2 * dr; im[l] += k2 * di; }
+          else { re[l] -= k3 * di; im[l] += k3 * dr; }               // (j k3)(dr + j di)
+        }
+      }
     }
     if (mi < mvalid && h < p.HI) {
       float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
                                                                     (int64_t)p.N + (int64_t)h * kLO));
 #pragma unroll
-      for (int q = 0; q < 8; ++q) o[q] = make_float4(v[2 * q], v[kLO + 2 * q], v[2 * q + 1], v[kLO + 2 * q + 1]);
+      for (int q = 0; q < 8; ++q) o[q] = make_float4(re[2 * q], im[2 * q], re[2 * q + 1], im[2 * q + 1]);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -463,7 +467,7 @@ TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
 template <bool TF32>
 cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
   static bool attr_set = false;
-  const int smem = 2 * kStageBytes;
+  const int smem = kStages * kStageBytes;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_synth_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
