@@ -57,7 +57,7 @@
 namespace rr {
 namespace {
 
-constexpr int kTcThreads = 256;
+constexpr int kTcThreads = 544;  // 16 producer warps + 1 MMA warp
 constexpr int kLO = 16;
 constexpr int kHitsPerBlock = 32;
 constexpr int kTerms = 4;                         // terms of the coupling expansion
@@ -194,14 +194,20 @@ __device__ __forceinline__ uint32_t op_off(int x, int k) {
          (uint32_t)(x & 7) * 16u + (uint32_t)(k & 3) * 4u;
 }
 
+// Warp roles: warps 0..15 produce operands (and warps 0..3 run the
+// epilogue), warp 16 allocates tensor memory and issues the MMAs.
+// Barriers per stage: full (512 producer arrivals: the stage holds block b)
+// and empty (one tcgen05.commit: the tensor core has read it); `done`
+// receives a commit after the last block.
+constexpr int kProducers = 512;
+
 template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_synth_tc(const SynthTcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_bar[kStages];
+  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done;
   __shared__ uint32_t s_tmem;
-  __shared__ float s_c0[kHitsPerBlock], s_c1[kHitsPerBlock], s_b0[kHitsPerBlock], s_b1[kHitsPerBlock],
-      s_a[kHitsPerBlock];
+  __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j = blockIdx.x % p.n_rx;
@@ -230,49 +236,56 @@ k_synth_tc(const SynthTcParams p) {
   const int64_t nblk_all = (K + kHitsPerBlock - 1) / kHitsPerBlock;
   const int nb = nblk_all > s_idx ? (int)((nblk_all - 1 - s_idx) / p.S + 1) : 0;  // this CTA's blocks
 
-  // tensor memory and barriers
-  if (warp == 0) {
+  if (warp == 16) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
                  "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
   if (tid == 0) {
-    for (int q = 0; q < kStages; ++q) mbar_init(smem_u32(&s_bar[q]), 1);
+    for (int q = 0; q < kStages; ++q) {
+      mbar_init(smem_u32(&s_full[q]), kProducers);
+      mbar_init(smem_u32(&s_empty[q]), 1);
+    }
+    mbar_init(smem_u32(&s_done), 1);
+    s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-
-  // operand-generation roles: a warp writes 4 hits (lane group g = lane / 8
-  // gives k % 4) x 8 rows or columns (c8 = lane % 8) per store; the 8 lanes
-  // of a group handle 8 different 8-row units and walk their rows from a
-  // staggered start, so each store fills one 128-byte bank window.
-  const int g = lane >> 3, c8 = lane & 7;
-  const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
-  const int nseg = HE / 8;                         // 8-row units per chirp (16 units per tile)
   const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 16384u;
 
-  bool ok = true;
-  int issued = 0;  // blocks whose MMAs were committed
-  for (int b = 0; b < nb && ok; ++b) {
-    const int stg = b % kStages;
-    unsigned char *A = smem + stg * kStageBytes;
-    unsigned char *B = A + kABytes;
-    if (b >= kStages) {  // the tensor core has finished reading this stage (block b - kStages)
-      if (!mbar_wait(smem_u32(&s_bar[stg]), ((b - kStages) / kStages) & 1)) {
+  if (warp < 16) {
+    // ---- producers: warp w owns hits 4 (w % 8) + g of every block (g =
+    // lane / 8), the A units 8 (w / 8) + c8 and the B offsets l = 8 (w / 8) + c8
+    // (c8 = lane % 8); a store of the warp covers 4 hits x 8 rows or columns,
+    // the rows staggered so that it fills one 128-byte bank window
+    const int g = lane >> 3, c8 = lane & 7;
+    const int kh = 4 * (warp & 7) + g;
+    const int uo = warp >> 3;
+    const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
+    const int nseg = HE / 8;                         // 8-row units per chirp (16 per tile)
+    const int u = 8 * uo + c8;
+    const int mi = u / nseg, seg = u - mi * nseg;
+    const int hbase = 8 * seg;
+    const int l = 8 * uo + c8;
+    for (int b = 0; b < nb; ++b) {
+      if (s_abort) break;
+      const int stg = b % kStages;
+      unsigned char *A = smem + stg * kStageBytes;
+      unsigned char *B = A + kABytes;
+      if (b >= kStages && !mbar_wait(smem_u32(&s_empty[stg]), ((b - kStages) / kStages) & 1)) {
         atomicOr(p.err, ERR_TIMEOUT);
-        ok = false;
+        s_abort = 1;
+        break;
       }
-    }
-    if (!__syncthreads_and(ok)) { ok = false; break; }
-    const int64_t k0 = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock;
-    if (tid < kHitsPerBlock) {
-      const int64_t k = k0 + tid;
+      // hit constants: lanes 0..3 load and reduce the warp's 4 hits, then broadcast
+      const int64_t kb0 = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + 4 * (warp & 7);
       float c0 = 0.f, c1 = 0.f, b0 = 0.f, b1 = 0.f, a = 0.f;
-      if (k < K) {
+      if (lane < 4 && kb0 + lane < K) {
+        const int64_t k = kb0 + lane;
         const float d = dj[k], dd = ddj[k];
         const double x = p.f0_c * (double)d;  // FP64 carrier reduction
         c0 = (float)(x - floor(x));
@@ -281,22 +294,15 @@ k_synth_tc(const SynthTcParams p) {
         b1 = p.b1k * dd;
         a = aj[k];
         const float xm = 6.2831853f * fabsf(b1) * mu_max * (float)(kLO - 1);
-        if (xm > 0.157f) atomicOr(p.err, ERR_TC_BOUND);
+        if (xm > 0.157f && uo == 0) atomicOr(p.err, ERR_TC_BOUND);
       }
-      s_c0[tid] = c0; s_c1[tid] = c1; s_b0[tid] = b0; s_b1[tid] = b1; s_a[tid] = a;
-    }
-    __syncthreads();
-#pragma unroll 1
-    for (int it = 0; it < 2; ++it) {
-      const int slice = warp + 8 * it;           // 16 slices: 8 hit quads x 2 unit octets
-      const int kq = slice & 7, uo = slice >> 3;
-      const int kh = 4 * kq + g;                 // block-local hit
-      const float c0 = s_c0[kh], c1 = s_c1[kh], b0 = s_b0[kh], b1 = s_b1[kh], a = s_a[kh];
-      // A: unit u = 8 rows (chirp mi, segment seg) of this hit
+      c0 = __shfl_sync(0xffffffffu, c0, g);
+      c1 = __shfl_sync(0xffffffffu, c1, g);
+      b0 = __shfl_sync(0xffffffffu, b0, g);
+      b1 = __shfl_sync(0xffffffffu, b1, g);
+      a = __shfl_sync(0xffffffffu, a, g);
+      // A: unit (chirp mi, segment seg) = 8 rows of this hit
       {
-        const int u = 8 * uo + c8;
-        const int mi = u / nseg, seg = u - mi * nseg;
-        const int hbase = 8 * seg;
         float2 P = make_float2(0.f, 0.f), P0 = P, W = make_float2(1.f, 0.f);
         if (mi < mvalid) {
           const float fm = (float)(m0 + mi);
@@ -318,65 +324,73 @@ k_synth_tc(const SynthTcParams p) {
           P = cmul(P, W);
         }
       }
-      // B: l = c8 + 8 uo, terms t = 0..3, halves Re / Im: column 32 t + 16 half + l
+      // B: terms t = 0..3, halves Re / Im of offset l: column 32 t + 16 half + l
       {
         const float beta_c = fmaf(mcen, b1, b0);
-        const int l = c8 + 8 * uo;
         const float2 B0 = expm2pi(beta_c * (float)l);
         const float bl = b1 * (float)l;
         float w = 1.f;  // (b1 l)^t
 #pragma unroll
         for (int t = 0; t < kTerms; ++t) {
           const float re = w * B0.x, im = w * B0.y;
-          // entries (c = 0: multiplies Re A, c = 1: multiplies Im A)
           put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, kh), re, -im);        // Re half
           put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, kh), im, re);   // Im half
           w *= bl;
         }
       }
+      // generic-proxy smem writes -> visible to the tensor core, then arrive
+      asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_full[stg])) : "memory");
     }
-    // generic-proxy smem writes -> visible to the tensor core (async proxy)
-    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-    __syncthreads();
-    if (tid == 0) {
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      const uint32_t a0 = smem_u32(A), bb0 = smem_u32(B);
-      if (TF32) {
-#pragma unroll 1
-        for (int ks = 0; ks < kHitsPerBlock / 4; ++ks)
-          mma<true>(tmem, smem_desc(a0 + ks * 4096u, 128, 256), smem_desc(bb0 + ks * 4096u, 128, 256),
-                    (b > 0 || ks > 0) ? 1u : 0u);
-      } else {
-#pragma unroll 1
-        for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
-          const uint64_t ahi = smem_desc(a0 + ks * 4096u, 128, 256), alo = smem_desc(a0 + lo_a + ks * 4096u, 128, 256);
-          const uint64_t bhi = smem_desc(bb0 + ks * 4096u, 128, 256), blo = smem_desc(bb0 + lo_b + ks * 4096u, 128, 256);
-          mma<false>(tmem, alo, bhi, (b > 0 || ks > 0) ? 1u : 0u);
-          mma<false>(tmem, ahi, blo, 1u);
-          mma<false>(tmem, ahi, bhi, 1u);
+  } else {
+    // ---- MMA issuer (warp 16, one lane)
+    if (lane == 0) {
+      for (int b = 0; b < nb; ++b) {
+        if (s_abort) break;
+        const int stg = b % kStages;
+        if (!mbar_wait(smem_u32(&s_full[stg]), (b / kStages) & 1)) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
         }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a0 = smem_u32(smem + stg * kStageBytes), bb0 = a0 + kABytes;
+        if (TF32) {
+#pragma unroll 1
+          for (int ks = 0; ks < kHitsPerBlock / 4; ++ks)
+            mma<true>(tmem, smem_desc(a0 + ks * 4096u, 128, 256), smem_desc(bb0 + ks * 4096u, 128, 256),
+                      (b > 0 || ks > 0) ? 1u : 0u);
+        } else {
+#pragma unroll 1
+          for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
+            const uint64_t ahi = smem_desc(a0 + ks * 4096u, 128, 256), alo = smem_desc(a0 + lo_a + ks * 4096u, 128, 256);
+            const uint64_t bhi = smem_desc(bb0 + ks * 4096u, 128, 256), blo = smem_desc(bb0 + lo_b + ks * 4096u, 128, 256);
+            mma<false>(tmem, alo, bhi, (b > 0 || ks > 0) ? 1u : 0u);
+            mma<false>(tmem, ahi, blo, 1u);
+            mma<false>(tmem, ahi, bhi, 1u);
+          }
+        }
+        mma_commit(smem_u32(&s_empty[stg]));
       }
-      mma_commit(smem_u32(&s_bar[stg]));
+      // after the last block's MMAs (they complete in issue order); with no
+      // block at all the commit arrives at once
+      mma_commit(smem_u32(&s_done));
     }
-    issued = b + 1;
+    __syncwarp();
   }
 
-  // wait for the last committed block's MMAs (they complete in issue order)
-  bool have = issued > 0;
-  if (have) {
-    if (!mbar_wait(smem_u32(&s_bar[(issued - 1) % kStages]), ((issued - 1) / kStages) & 1)) {
+  // ---- epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes); per
+  // fast-time offset l the four terms combine as s = sum_t kappa_t D_t with
+  // kappa = (1, -j sg, -sg^2 / 2, j sg^3 / 6), sg = 2 pi mu
+  if (warp < 4) {
+    bool have = nb > 0;
+    if (!mbar_wait(smem_u32(&s_done), 0)) {
       atomicOr(p.err, ERR_TIMEOUT);
       have = false;
     }
-  }
-  have = have && ok;
-  have = __syncthreads_and(have) != 0;
-  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-
-  // epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes); per fast-time
-  // offset l the four terms combine as s = sum_t kappa_t D_t with
-  // kappa = (1, -j sg, -sg^2 / 2, j sg^3 / 6), sg = 2 pi mu
-  if (warp < 4) {
+    if (s_abort) have = false;
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    have = __all_sync(0xffffffffu, have);
     const int row = 32 * warp + lane;
     const int HEo = p.HI < 8 ? 8 : p.HI;
     const int mi = row / HEo, h = row - mi * HEo;
@@ -385,7 +399,7 @@ k_synth_tc(const SynthTcParams p) {
     const float k2 = -0.5f * sg * sg, k3 = sg * sg * sg * (1.f / 6.f);
     float re[kLO], im[kLO];
 #pragma unroll
-    for (int l = 0; l < kLO; ++l) re[l] = im[l] = 0.f;
+    for (int q = 0; q < kLO; ++q) re[q] = im[q] = 0.f;
     if (have) {
       const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
 #pragma unroll
@@ -405,12 +419,12 @@ k_synth_tc(const SynthTcParams p) {
             : "r"(taddr + 16u));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-        for (int l = 0; l < kLO; ++l) {
-          const float dr = __uint_as_float(r[l]), di = __uint_as_float(r[kLO + l]);
-          if (t == 0) { re[l] += dr; im[l] += di; }
-          else if (t == 1) { re[l] += sg * di; im[l] -= sg * dr; }   // (-j sg)(dr + j di)
-          else if (t == 2) { re[l] += k2 * dr; im[l] += k2 * di; }
-          else { re[l] -= k3 * di; im[l] += k3 * dr; }               // (j k3)(dr + j di)
+        for (int q = 0; q < kLO; ++q) {
+          const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[kLO + q]);
+          if (t == 0) { re[q] += dr; im[q] += di; }
+          else if (t == 1) { re[q] += sg * di; im[q] -= sg * dr; }   // (-j sg)(dr + j di)
+          else if (t == 2) { re[q] += k2 * dr; im[q] += k2 * di; }
+          else { re[q] -= k3 * di; im[q] += k3 * dr; }               // (j k3)(dr + j di)
         }
       }
     }
@@ -423,7 +437,7 @@ k_synth_tc(const SynthTcParams p) {
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
-  if (warp == 0) {
+  if (warp == 16) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
