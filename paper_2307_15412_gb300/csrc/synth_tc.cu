@@ -62,6 +62,11 @@ constexpr int kLO = 16;
 constexpr int kHitsPerBlock = 32;
 constexpr int kTerms = 4;                         // terms of the coupling expansion
 constexpr int kStages = 3;
+// Long accumulation chains in tensor memory lose precision (2.4e-4 rel-L2
+// for 37k hits in one accumulator against 1.3e-5 for 1.7k, split-BF16x3), so
+// every kMaxChain blocks the accumulator is folded into an FP32 row buffer
+// in shared memory and the chain restarts.
+constexpr int kMaxChain = 64;                      // blocks (of 32 hits) per accumulation chain
 constexpr int kStageBytes = 64 * 1024;           // A region 32 KB + B region 32 KB
 constexpr int kABytes = 32 * 1024;
 constexpr int kTmemCols = 128;
@@ -200,12 +205,46 @@ __device__ __forceinline__ uint32_t op_off(int x, int k) {
 // and empty (one tcgen05.commit: the tensor core has read it); `done`
 // receives a commit after the last block.
 constexpr int kProducers = 512;
+constexpr int kFoldStride = 33;  // floats per row of the fold buffer (padded against bank conflicts)
+constexpr int kFoldBytes = 128 * kFoldStride * 4;
+
+// Adds sum_t kappa_t D_t of this thread's accumulator row (TMEM lane
+// 32 w + lane, w = warp % 4) into acc[0..15] (Re) and acc[16..31] (Im);
+// kappa = (1, -j sg, k2, j k3), k2 = -sg^2 / 2, k3 = sg^3 / 6.
+__device__ __forceinline__ void fold_row(uint32_t tmem, int warp, float sg, float k2, float k3, float *acc) {
+  const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+#pragma unroll
+  for (int t = 0; t < kTerms; ++t) {
+    uint32_t r[32];
+    const uint32_t taddr = tbase + 32u * t;
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+        : "r"(taddr));
+    asm volatile(
+        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+          "=r"(r[30]), "=r"(r[31])
+        : "r"(taddr + 16u));
+    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+    for (int q = 0; q < kLO; ++q) {
+      const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[kLO + q]);
+      if (t == 0) { acc[q] += dr; acc[kLO + q] += di; }
+      else if (t == 1) { acc[q] += sg * di; acc[kLO + q] -= sg * dr; }   // (-j sg)(dr + j di)
+      else if (t == 2) { acc[q] += k2 * dr; acc[kLO + q] += k2 * di; }
+      else { acc[q] -= k3 * di; acc[kLO + q] += k3 * dr; }               // (j k3)(dr + j di)
+    }
+  }
+}
 
 template <bool TF32>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_synth_tc(const SynthTcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done;
+  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done, s_fold, s_folded;
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
 
@@ -248,6 +287,8 @@ k_synth_tc(const SynthTcParams p) {
       mbar_init(smem_u32(&s_empty[q]), 1);
     }
     mbar_init(smem_u32(&s_done), 1);
+    mbar_init(smem_u32(&s_fold), 1);
+    mbar_init(smem_u32(&s_folded), 128);
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -256,6 +297,15 @@ k_synth_tc(const SynthTcParams p) {
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
   const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 16384u;
+  // accumulator rows of warps 0-3: row 32 w + lane = (chirp, h); fold buffer
+  float *fold = reinterpret_cast<float *>(smem + kStages * kStageBytes);
+  const int my_row = 32 * (warp & 3) + lane;
+  const int HEr = p.HI < 8 ? 8 : p.HI;
+  const int my_mi = my_row / HEr, my_h = my_row - my_mi * HEr;
+  const float my_sg = 6.2831853f * ((float)(m0 + my_mi) - mcen);
+  const float my_k2 = -0.5f * my_sg * my_sg, my_k3 = my_sg * my_sg * my_sg * (1.f / 6.f);
+  if (warp < 4)
+    for (int q = 0; q < 2 * kLO; ++q) fold[my_row * kFoldStride + q] = 0.f;
 
   if (warp < 16) {
     // ---- producers: warp w owns hits 4 (w % 8) + g of every block (g =
@@ -273,6 +323,18 @@ k_synth_tc(const SynthTcParams p) {
     const int l = 8 * uo + c8;
     for (int b = 0; b < nb; ++b) {
       if (s_abort) break;
+      if (warp < 4 && b > 0 && b % kMaxChain == 0) {
+        // fold the accumulator of the last kMaxChain blocks into the row buffer
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_fold), (b / kMaxChain - 1) & 1))) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        fold_row(tmem, warp, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * kFoldStride);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
+      }
       const int stg = b % kStages;
       unsigned char *A = smem + stg * kStageBytes;
       unsigned char *B = A + kABytes;
@@ -313,15 +375,24 @@ k_synth_tc(const SynthTcParams p) {
           P0 = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
           P.x *= a; P.y *= a; P0.x *= a; P0.y *= a;
         }
+        const uint32_t rbase = op_off<TF32>(mi * HE + hbase, kh);  // row hbase; rows are 16 B apart
+        if (p.HI >= 8) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          int hh = c8 + q;
-          if (hh == 8) P = P0;
-          if (hh >= 8) hh -= 8;
-          const int h = hbase + hh;
-          const bool live = h < p.HI;  // rows h >= HI pad a short chirp to 8 rows
-          put2<TF32>(A, A + lo_a, op_off<TF32>(mi * HE + h, kh), live ? P.x : 0.f, live ? P.y : 0.f);
-          P = cmul(P, W);
+          for (int q = 0; q < 8; ++q) {
+            const int hh = (c8 + q) & 7;
+            if (hh == 0) P = P0;
+            put2<TF32>(A, A + lo_a, rbase + 16u * hh, P.x, P.y);
+            P = cmul(P, W);
+          }
+        } else {  // rows h >= HI pad a short chirp to 8 rows
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const int hh = (c8 + q) & 7;
+            if (hh == 0) P = P0;
+            const bool live = hh < p.HI;
+            put2<TF32>(A, A + lo_a, rbase + 16u * hh, live ? P.x : 0.f, live ? P.y : 0.f);
+            P = cmul(P, W);
+          }
         }
       }
       // B: terms t = 0..3, halves Re / Im of offset l: column 32 t + 16 half + l
@@ -353,24 +424,31 @@ k_synth_tc(const SynthTcParams p) {
           s_abort = 1;
           break;
         }
+        const bool fresh = b % kMaxChain == 0;  // first block of an accumulation chain
+        if (b > 0 && fresh && !mbar_wait(smem_u32(&s_folded), (b / kMaxChain - 1) & 1)) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
         const uint32_t a0 = smem_u32(smem + stg * kStageBytes), bb0 = a0 + kABytes;
         if (TF32) {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 4; ++ks)
             mma<true>(tmem, smem_desc(a0 + ks * 4096u, 128, 256), smem_desc(bb0 + ks * 4096u, 128, 256),
-                      (b > 0 || ks > 0) ? 1u : 0u);
+                      (!fresh || ks > 0) ? 1u : 0u);
         } else {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
             const uint64_t ahi = smem_desc(a0 + ks * 4096u, 128, 256), alo = smem_desc(a0 + lo_a + ks * 4096u, 128, 256);
             const uint64_t bhi = smem_desc(bb0 + ks * 4096u, 128, 256), blo = smem_desc(bb0 + lo_b + ks * 4096u, 128, 256);
-            mma<false>(tmem, alo, bhi, (b > 0 || ks > 0) ? 1u : 0u);
+            mma<false>(tmem, alo, bhi, (!fresh || ks > 0) ? 1u : 0u);
             mma<false>(tmem, ahi, blo, 1u);
             mma<false>(tmem, ahi, bhi, 1u);
           }
         }
         mma_commit(smem_u32(&s_empty[stg]));
+        if ((b + 1) % kMaxChain == 0 && b + 1 < nb) mma_commit(smem_u32(&s_fold));
       }
       // after the last block's MMAs (they complete in issue order); with no
       // block at all the commit arrives at once
@@ -379,9 +457,8 @@ k_synth_tc(const SynthTcParams p) {
     __syncwarp();
   }
 
-  // ---- epilogue: warps 0-3 read rows 32w..32w+31 (TMEM lanes); per
-  // fast-time offset l the four terms combine as s = sum_t kappa_t D_t with
-  // kappa = (1, -j sg, -sg^2 / 2, j sg^3 / 6), sg = 2 pi mu
+  // ---- epilogue: warps 0-3 fold the last chain into their rows and write
+  // them (row 32 w + lane = (chirp, h): 16 complex samples n = 16 h + l)
   if (warp < 4) {
     bool have = nb > 0;
     if (!mbar_wait(smem_u32(&s_done), 0)) {
@@ -391,48 +468,16 @@ k_synth_tc(const SynthTcParams p) {
     if (s_abort) have = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     have = __all_sync(0xffffffffu, have);
-    const int row = 32 * warp + lane;
-    const int HEo = p.HI < 8 ? 8 : p.HI;
-    const int mi = row / HEo, h = row - mi * HEo;
-    const int m = m0 + mi;
-    const float sg = 6.2831853f * ((float)m - mcen);
-    const float k2 = -0.5f * sg * sg, k3 = sg * sg * sg * (1.f / 6.f);
-    float re[kLO], im[kLO];
-#pragma unroll
-    for (int q = 0; q < kLO; ++q) re[q] = im[q] = 0.f;
-    if (have) {
-      const uint32_t tbase = tmem + ((uint32_t)(32 * warp) << 16);
-#pragma unroll
-      for (int t = 0; t < kTerms; ++t) {
-        uint32_t r[32];
-        const uint32_t taddr = tbase + 32u * t;
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-              "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr + 16u));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-#pragma unroll
-        for (int q = 0; q < kLO; ++q) {
-          const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[kLO + q]);
-          if (t == 0) { re[q] += dr; im[q] += di; }
-          else if (t == 1) { re[q] += sg * di; im[q] -= sg * dr; }   // (-j sg)(dr + j di)
-          else if (t == 2) { re[q] += k2 * dr; im[q] += k2 * di; }
-          else { re[q] -= k3 * di; im[q] += k3 * dr; }               // (j k3)(dr + j di)
-        }
-      }
-    }
-    if (mi < mvalid && h < p.HI) {
+    float *acc = fold + my_row * kFoldStride;
+    if (have) fold_row(tmem, warp, my_sg, my_k2, my_k3, acc);
+    const int m = m0 + my_mi;
+    if (my_mi < mvalid && my_h < p.HI) {
       float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
-                                                                    (int64_t)p.N + (int64_t)h * kLO));
+                                                                    (int64_t)p.N + (int64_t)my_h * kLO));
 #pragma unroll
-      for (int q = 0; q < 8; ++q) o[q] = make_float4(re[2 * q], im[2 * q], re[2 * q + 1], im[2 * q + 1]);
+      for (int q = 0; q < 8; ++q)
+        o[q] = have ? make_float4(acc[2 * q], acc[kLO + 2 * q], acc[2 * q + 1], acc[kLO + 2 * q + 1])
+                    : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -471,7 +516,15 @@ TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
   if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
   const int64_t ctas = (int64_t)pl.n_tiles * r.n_rx * n_jobs;
   const int64_t blocks = (kmax + kHitsPerBlock - 1) / kHitsPerBlock;
-  int64_t S = split > 0 ? split : (sms + ctas - 1) / ctas;
+  int64_t S = split;
+  if (S <= 0) {  // one CTA per SM at a time: pick the split with the least idle tail
+    double best = 1e30;
+    for (int64_t c = 1; c <= 8; ++c) {
+      const double waves = (double)((ctas * c + sms - 1) / sms);
+      const double cost = waves / c + 0.02 * c;  // per-CTA fixed cost (set-up, epilogue, partials)
+      if (cost < best) { best = cost; S = c; }
+    }
+  }
   if (S > blocks) S = blocks;
   if (S < 1) S = 1;
   pl.S = (int)S;
@@ -481,7 +534,7 @@ TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
 template <bool TF32>
 cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
   static bool attr_set = false;
-  const int smem = kStages * kStageBytes;
+  const int smem = kStages * kStageBytes + kFoldBytes;
   if (!attr_set) {
     cudaError_t e = cudaFuncSetAttribute(k_synth_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;

@@ -1,11 +1,13 @@
-"""Runs N frames of a workload through the C ABI, untimed (for profilers).
+"""Runs N steps of a workload through the C ABI, untimed (for profilers).
 
-  python -m paper_2307_15412_gb300.run_case [--workload full|tiny] [--frames N]
-         [--scenes S] [--no-flush]
+  python -m paper_2307_15412_gb300.run_case [--workload full|tiny] [--steps N]
+         [--scenes S] [--batch] [--variant 0|1|2] [--no-flush]
 
-Each frame: build_bvh, trace_frame, synth_if (plain FP32), range_doppler on
-one of S resident seeded scenes; L2 is flushed (256 MiB write) before each
-frame unless --no-flush, as in the benchmark.
+Each step runs every one of the S resident seeded scenes: one rr_run_frame
+per scene, or with --batch one rr_batch_run over all of them.  --variant
+selects the synthesis (0 FP32, 1 tensor-core BF16x3, 2 tensor-core TF32).
+L2 is flushed (256 MiB write) before each step unless --no-flush, as in the
+benchmark.
 """
 from __future__ import annotations
 
@@ -17,8 +19,10 @@ import sys
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--workload", default="full", choices=["full", "tiny"])
-    ap.add_argument("--frames", type=int, default=4)
+    ap.add_argument("--steps", type=int, default=4)
     ap.add_argument("--scenes", type=int, default=2)
+    ap.add_argument("--batch", action="store_true")
+    ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-flush", action="store_true")
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
@@ -38,17 +42,22 @@ def main():
     ctx = rr.Context(0)
     for k, s in enumerate(scenes):
         ctx.scene_upload(k, s.V, s.F, s.vel)
-    if_out = torch.empty((radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda:0")
+    S = len(scenes)
+    if_out = torch.empty((S, radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda:0")
     rd_out = torch.empty_like(if_out)
     flush = None if args.no_flush else torch.empty(256 << 20, dtype=torch.uint8, device="cuda:0")
-    for i in range(args.frames):
+    for i in range(args.steps):
         if flush is not None:
             flush.zero_()
-        ctx.run_frame(i % len(scenes), radar, grid, if_out=if_out, rd_out=rd_out)
+        if args.batch:
+            ctx.batch_run([(k, grid) for k in range(S)], radar, if_out=if_out, rd_out=rd_out, variant=args.variant)
+        else:
+            for k in range(S):
+                ctx.run_frame(k, radar, grid, if_out=if_out[k], rd_out=rd_out[k], variant=args.variant)
     ctx.sync()
     torch.cuda.synchronize()
     ctx.close()
-    print("ran %d frames" % args.frames)
+    print("ran %d steps of %d scenes" % (args.steps, S))
 
 
 if __name__ == "__main__":
