@@ -378,3 +378,48 @@ def workload_full_frame() -> Tuple[Radar, RayGrid, int]:
 
 FULL_FRAME_RANGE = (0.2, 0.6)
 FULL_FRAME_SPEED = (-1.0, 1.0)
+
+
+# --------------------------------------------------------------------------
+# Learned-surrogate workload: seeded hand parameters and their scenes
+# --------------------------------------------------------------------------
+
+# Training box of the surrogate's 32 inputs: 27 joint/pose angles (deg),
+# hand centre x, y, z (m) and velocity (radial, lateral x) (m/s).
+SURROGATE_LO = np.array([0.0] * N_ANGLES + [-0.05, -0.05, 0.20, -1.0, -1.0])
+SURROGATE_HI = np.array([60.0] * N_ANGLES + [0.05, 0.05, 0.60, 1.0, 1.0])
+SURROGATE_TRIANGLES = 2000
+
+
+def surrogate_radar_grid() -> Tuple[Radar, RayGrid]:
+    """Frames the surrogate learns: the tiny hand's 64 x 64 rays over
+    +-30 deg, 1 TX 3 RX (L, lambda/2), 32 chirps x 32 samples, 60-64 GHz."""
+    return (Radar(n_samples=32, n_chirps=32, rx=rx_l_array()),
+            RayGrid(64, 64, math.radians(30.0), math.radians(30.0)))
+
+
+def surrogate_inputs(seed: int, n: int, lo=None, hi=None) -> np.ndarray:
+    """n seeded parameter vectors [n][32] (float64), uniform in the box."""
+    rng = np.random.default_rng(seed)
+    lo = SURROGATE_LO if lo is None else np.asarray(lo, np.float64)
+    hi = SURROGATE_HI if hi is None else np.asarray(hi, np.float64)
+    return lo + (hi - lo) * rng.random((n, lo.size))
+
+
+def surrogate_features(raw: np.ndarray) -> np.ndarray:
+    """Network inputs: each parameter mapped linearly from the training box
+    to [-1, 1] (float32)."""
+    return (2.0 * (np.asarray(raw) - SURROGATE_LO) / (SURROGATE_HI - SURROGATE_LO) - 1.0).astype(np.float32)
+
+
+def surrogate_scene(raw_row: np.ndarray, n_tri_target: int = SURROGATE_TRIANGLES) -> Scene:
+    """Hand scene of one parameter vector: posed by the 27 angles, centred
+    at (x, y, z), moving with v_r along the unit vector from the radar to the
+    centre plus v_x along x."""
+    raw_row = np.asarray(raw_row, np.float64)
+    center = raw_row[N_ANGLES:N_ANGLES + 3]
+    vr, vx = raw_row[N_ANGLES + 3], raw_row[N_ANGLES + 4]
+    chat = center / np.linalg.norm(center)
+    vel = vr * chat + np.array([vx, 0.0, 0.0])
+    V, F = hand_mesh(n_tri_target, raw_row[:N_ANGLES], center)
+    return Scene(V=V, F=F, vel=vel.astype(np.float32), center=center, angles_deg=raw_row[:N_ANGLES])
