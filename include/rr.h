@@ -218,6 +218,60 @@ typedef struct {
 rr_status rr_batch_run(rr_ctx *ctx, const rr_job *jobs, int n_jobs, const rr_radar *radar,
                        rr_synth_variant variant, int window, float *if_out, float *rd_out, int flags);
 
+/* ---- learned surrogate --------------------------------------------------- */
+
+/* A multilayer perceptron that maps hand parameters to a range-Doppler cube,
+ * trained on frames the tracer itself produces, with the tracer as its
+ * fallback and judge.  The paper has no learned part: this is an
+ * acceleration of the method's per-pose output.  The network is
+ *   h_l = relu(h_{l-1} W_l^T + b_l) (l < L),  y = h_{L-1} W_L^T + b_L,
+ * W_l stored [out][in]; BF16 weights and activations on the tensor cores
+ * (tcgen05) with FP32 accumulation and FP32 master weights; loss
+ * mean((y - t)^2); AdamW with decoupled weight decay on the weights only.
+ * Parameters are packed as FP32 [W_1, b_1, W_2, b_2, ...].  Inputs are
+ * features in [-1, 1] (the training box); x, t, y are device row-major
+ * FP32 arrays; batch sizes are multiples of 8 (TMA alignment). */
+typedef struct {
+  float lr, beta1, beta2, eps, weight_decay;
+} rr_adamw;
+
+typedef struct {
+  rr_adamw opt;
+  int32_t epochs;
+  int32_t batch;        /* minibatch size, multiple of 8 */
+  uint64_t seed;        /* sample order of every epoch */
+  float *loss_out;      /* host float[epochs]: mean training loss per epoch, or NULL */
+} rr_train_cfg;
+
+/* Creates (or replaces) the context's surrogate: dims[0..n_dims-1] are the
+ * layer widths (n_dims >= 2, every width a multiple of 8, at most 8
+ * layers); parameters start at zero until rr_surrogate_set_params. */
+rr_status rr_surrogate_create(rr_ctx *ctx, const int32_t *dims, int n_dims);
+/* Number of packed FP32 parameters. */
+int64_t rr_surrogate_num_params(rr_ctx *ctx);
+/* Loads packed FP32 parameters (host if ptr_is_device == 0, else device);
+ * resets the AdamW moments and step count. */
+rr_status rr_surrogate_set_params(rr_ctx *ctx, const float *params, int ptr_is_device);
+/* Copies the packed FP32 master parameters to device memory `out`. */
+rr_status rr_surrogate_get_params(rr_ctx *ctx, float *out);
+/* y [B][dims_last] = network(x [B][dims_0]). */
+rr_status rr_surrogate_forward(rr_ctx *ctx, const float *x, int64_t B, float *y);
+/* Loss and packed FP32 gradients (device) of mean((net(x) - t)^2). */
+rr_status rr_surrogate_gradients(rr_ctx *ctx, const float *x, const float *t, int64_t B, float *grads, float *loss);
+/* One AdamW step on the minibatch (x, t); loss (device float, optional)
+ * receives the minibatch loss before the step. */
+rr_status rr_surrogate_train_step(rr_ctx *ctx, const float *x, const float *t, int64_t B, const rr_adamw *opt,
+                                  float *loss);
+/* cfg->epochs passes over the device dataset x [n][dims_0], t [n][dims_last]
+ * in minibatches (the last partial one is dropped), shuffled per epoch from
+ * cfg->seed.  Waits for the stream when cfg->loss_out is given. */
+rr_status rr_surrogate_train(rr_ctx *ctx, const rr_train_cfg *cfg, const float *x, const float *t, int64_t n);
+/* y_out [n][dims_last] for every row of x [n][dims_0] (batches of up to
+ * 4096); fell_back (device uint8 [n], optional) is set to 1 for rows with a
+ * feature outside [-1, 1]: the training box does not cover them and the
+ * caller traces them instead (the surrogate keeps the tracer as fallback). */
+rr_status rr_surrogate_infer(rr_ctx *ctx, const float *x, int64_t n, float *y_out, uint8_t *fell_back);
+
 /* ---- allocation-free synthesis ------------------------------------------- */
 
 /* Size of the fixed device scratch used by rr_synth_if_from_hits_noalloc. */

@@ -43,14 +43,25 @@ def init_params(dims, seed: int) -> Params:
     return out
 
 
-def forward(params: Params, x: np.ndarray):
-    """Returns y and the per-layer cache [(h_in, z)] (z = pre-activation)."""
-    h = np.asarray(x, np.float64)
+def _keep(a):
+    return a
+
+
+def forward(params: Params, x: np.ndarray, store=None):
+    """Returns y and the per-layer cache [(h_in, z)] (z = pre-activation).
+
+    store: optional rounding applied where an implementation stores a value
+    in a narrower format -- the weights, the network input and every hidden
+    activation (the output y stays unrounded); identity by default, so the
+    oracle is the exact FP64 definition unless a test asks for the storage
+    points of a given precision."""
+    r = store or _keep
+    h = r(np.asarray(x, np.float64))
     cache = []
     for i, (W, b) in enumerate(params):
-        z = h @ W.T + b
+        z = h @ r(W).T + b
         cache.append((h, z))
-        h = z if i == len(params) - 1 else np.maximum(z, 0.0)
+        h = z if i == len(params) - 1 else r(np.maximum(z, 0.0))
     return h, cache
 
 
@@ -58,19 +69,24 @@ def mse(y: np.ndarray, t: np.ndarray) -> float:
     return float(np.mean((y - t) ** 2))
 
 
-def backward(params: Params, x: np.ndarray, t: np.ndarray):
-    """Loss and gradients [(dW, db)] of L = mean((y - t)^2)."""
-    y, cache = forward(params, x)
+def backward(params: Params, x: np.ndarray, t: np.ndarray, store=None):
+    """Loss and gradients [(dW, db)] of L = mean((y - t)^2).
+
+    store: as for forward, also applied to every stored gradient dz; the
+    ReLU derivative is taken on the stored activation (h > 0, which is
+    z > 0 for exact values)."""
+    r = store or _keep
+    y, cache = forward(params, x, store)
     B, O = y.shape
-    dz = 2.0 * (y - t) / (B * O)
+    dz = r(2.0 * (y - t) / (B * O))
     grads = [None] * len(params)
     for i in range(len(params) - 1, -1, -1):
         h_in, z = cache[i]
         W, _ = params[i]
         grads[i] = (dz.T @ h_in, dz.sum(axis=0))
         if i > 0:
-            dh = dz @ W
-            dz = dh * (cache[i - 1][1] > 0.0)
+            dh = dz @ r(W)
+            dz = r(dh * (cache[i][0] > 0.0))
     return mse(y, t), grads
 
 

@@ -61,6 +61,7 @@ struct rr_ctx {
     // autotuner choices per batch shape: (ray-tile width log2, split-K)
     std::map<uint64_t, std::pair<int, int>> tuned;
   } batch;
+  rr::Surrogate *sur = nullptr;    // learned surrogate (rr_surrogate_*)
   // stage timing ring: 5 events per slot
   std::vector<cudaEvent_t> tev;
   std::vector<char> tev_used;
@@ -270,6 +271,7 @@ rr_status rr_destroy(rr_ctx *c) {
     if (b.staged) cudaEventDestroy(b.staged);
     if (b.exec) cudaGraphExecDestroy(b.exec);
   }
+  if (c->sur) rr::surrogate_free(c->sur);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return RR_OK;
@@ -917,3 +919,22 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   }
   return RR_OK;
 }
+
+// ---------------------------------------------------------------------------
+// context access for the other translation units
+// ---------------------------------------------------------------------------
+
+cudaStream_t rr_ctx_stream(rr_ctx *c) { return c->stream; }
+uint32_t *rr_ctx_err(rr_ctx *c) { return c->d_err; }
+int rr_ctx_device(rr_ctx *c) { return c->device; }
+rr::Surrogate *&rr_ctx_surrogate(rr_ctx *c) { return c->sur; }
+rr_status rr_ctx_fail(rr_ctx *c, rr_status st, const char *fmt, ...) {
+  if (c) {
+    va_list ap;
+    va_start(ap, fmt);
+    vsnprintf(c->msg, sizeof(c->msg), fmt, ap);
+    va_end(ap);
+  }
+  return st;
+}
+rr_status rr_ctx_cuda_fail(rr_ctx *c, cudaError_t e, const char *where) { return cuda_fail(c, e, where); }

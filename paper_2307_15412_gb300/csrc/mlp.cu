@@ -1,0 +1,479 @@
+// mlp.cu -- kernels of the learned surrogate (BF16 MLP, FP32 accumulation).
+//
+// gemm_tn: C[M][N] = A[M][K] B[N][K]^T (both operands K-major, BF16) on the
+// 5th-generation tensor cores.  One CTA computes a 128 x 128 tile:
+//   warp 0  loads operand tiles with TMA (cp.async.bulk.tensor, no swizzle,
+//           boxes of 8 K-elements x 128 rows, so that each box is one column
+//           of 8 x 16-byte core matrices of the canonical K-major layout:
+//           SBO = 128 B between 8-row groups, LBO = 2048 B between
+//           K-neighbouring core matrices) into a 4-stage ring, completing
+//           each stage's `full` mbarrier by transaction bytes;
+//   warp 1  allocates 128 tensor-memory columns and issues
+//           tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = N = 128, K = 16)
+//           per stage, committing to the stage's `empty` mbarrier;
+//   warps 2-5 wait for the last commit and run the epilogue from tensor
+//           memory (tcgen05.ld): + bias, optional ReLU or ReLU-derivative
+//           mask, stored as FP32 and/or BF16, row-major and/or transposed.
+// Operands outside [M, N, K] are read as zeros by TMA, so any M, N and any K
+// that is a multiple of 8 (the 16-byte TMA alignment) is accepted.  All
+// waits are bounded (2 s); a wait that runs out latches ERR_TIMEOUT.
+//
+// Around it: MSE loss and its gradient, bias-gradient row sums, a tiled
+// transpose, AdamW (Loshchilov & Hutter, ICLR 2019) on FP32 master weights
+// that also refreshes the BF16 copies, a minibatch gather and a training-box
+// check.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "rr_internal.cuh"
+
+namespace rr {
+namespace {
+
+constexpr int kBM = 128, kBN = 128, kBK = 64, kGStages = 4;
+constexpr int kGThreads = 192;
+constexpr int kTileBytes = kBM * kBK * 2;           // 16 KB per operand per stage
+constexpr int kGemmSmem = kGStages * 2 * kTileBytes;  // 128 KB
+constexpr unsigned long long kGWaitNs = 2000000000ull;
+
+__device__ __forceinline__ uint32_t smem_u32(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try(bar, parity))
+    if (gtimer() - t0 > kGWaitNs) return false;
+  return true;
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
+         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+}
+
+// kind::f16 instruction descriptor: D F32, A and B BF16, K-major, N = 128, M = 128
+constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
+
+__device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+
+struct GemmArgs {
+  int M, N, K;
+  const float *bias;          // [N] or nullptr
+  int act;                    // 0 none, 1 relu
+  const __nv_bfloat16 *mask;  // [M][N] row-major (ld N): keep entries where mask > 0; nullptr: none
+  float *c32;                 // [M][N] FP32 row-major or nullptr
+  __nv_bfloat16 *c16;         // [M][N] BF16 row-major or nullptr
+  __nv_bfloat16 *c16t;        // [N][M] BF16 (transposed) or nullptr
+  uint32_t *err;
+};
+
+__global__ void __launch_bounds__(kGThreads, 1)
+k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
+  extern __shared__ __align__(1024) unsigned char smem[];
+  __shared__ __align__(8) uint64_t s_full[kGStages], s_empty[kGStages], s_done;
+  __shared__ uint32_t s_tmem;
+  __shared__ volatile int s_abort;
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
+  const int nk = (g.K + kBK - 1) / kBK;
+
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
+                 "r"(kBN)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  if (threadIdx.x == 0) {
+    for (int q = 0; q < kGStages; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[q])) : "memory");
+    }
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done)) : "memory");
+    s_abort = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
+    asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapB)) : "memory");
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+  const uint32_t tmem = s_tmem;
+
+  if (warp == 0) {
+    if (lane == 0) {
+      for (int kt = 0; kt < nk; ++kt) {
+        if (s_abort) break;
+        const int s = kt % kGStages;
+        if (kt >= kGStages && !mbar_wait(smem_u32(&s_empty[s]), ((kt / kGStages) - 1) & 1)) {
+          atomicOr(g.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        const uint32_t bar = smem_u32(&s_full[s]);
+        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kTileBytes)
+                     : "memory");
+        const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
+        const int k0 = kt * kBK;
+#pragma unroll
+        for (int c = 0; c < kBK / 8; ++c) {
+          tma_box(a + c * 2048, &mapA, k0 + 8 * c, m0, bar);
+          tma_box(b + c * 2048, &mapB, k0 + 8 * c, n0, bar);
+        }
+      }
+    }
+    __syncwarp();
+  } else if (warp == 1) {
+    if (lane == 0) {
+      for (int kt = 0; kt < nk; ++kt) {
+        if (s_abort) break;
+        const int s = kt % kGStages;
+        if (!mbar_wait(smem_u32(&s_full[s]), (kt / kGStages) & 1)) {
+          atomicOr(g.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
+#pragma unroll
+        for (int ks = 0; ks < kBK / 16; ++ks) {
+          const uint64_t da = smem_desc(a + ks * 4096, 2048, 128), db = smem_desc(b + ks * 4096, 2048, 128);
+          const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+          asm volatile(
+              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
+              "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                         smem_u32(&s_empty[s]))
+                     : "memory");
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+                       smem_u32(&s_done))
+                   : "memory");
+    }
+    __syncwarp();
+  } else {
+    // epilogue warps 2..5: TMEM lane quarter (warp % 4) = rows 32 (warp % 4) + lane
+    bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_done), 0));
+    if (!ok) atomicOr(g.err, ERR_TIMEOUT);
+    if (s_abort) ok = false;
+    ok = __all_sync(0xffffffffu, ok);
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    const int q = warp & 3;
+    const int row = m0 + 32 * q + lane;
+    const bool row_ok = row < g.M;
+#pragma unroll 1
+    for (int cb = 0; cb < kBN / 32; ++cb) {
+      uint32_t r[32];
+      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 32u * cb;
+      if (nk > 0) {
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+            : "r"(taddr));
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+              "=r"(r[30]), "=r"(r[31])
+            : "r"(taddr + 16u));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+      }
+      float v[32];
+      const int nb = n0 + 32 * cb;
+#pragma unroll
+      for (int c = 0; c < 32; ++c) {
+        float x = (ok && nk > 0) ? __uint_as_float(r[c]) : 0.f;
+        const int n = nb + c;
+        if (g.bias && n < g.N) x += g.bias[n];
+        if (g.act == 1) x = fmaxf(x, 0.f);
+        if (g.mask && row_ok && n < g.N && !(__bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.f)) x = 0.f;
+        v[c] = x;
+      }
+      if (row_ok) {
+        if (g.c32) {
+          float *dst = g.c32 + (int64_t)row * g.N + nb;
+          if (nb + 32 <= g.N && (g.N & 3) == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
+          } else {
+            for (int c = 0; c < 32; ++c)
+              if (nb + c < g.N) dst[c] = v[c];
+          }
+        }
+        if (g.c16) {
+          __nv_bfloat16 *dst = g.c16 + (int64_t)row * g.N + nb;
+          if (nb + 32 <= g.N && (g.N & 7) == 0) {
+#pragma unroll
+            for (int c = 0; c < 32; c += 8) {
+              __nv_bfloat162 p0 = __floats2bfloat162_rn(v[c], v[c + 1]), p1 = __floats2bfloat162_rn(v[c + 2], v[c + 3]);
+              __nv_bfloat162 p2 = __floats2bfloat162_rn(v[c + 4], v[c + 5]), p3 = __floats2bfloat162_rn(v[c + 6], v[c + 7]);
+              uint4 u;
+              u.x = *reinterpret_cast<uint32_t *>(&p0);
+              u.y = *reinterpret_cast<uint32_t *>(&p1);
+              u.z = *reinterpret_cast<uint32_t *>(&p2);
+              u.w = *reinterpret_cast<uint32_t *>(&p3);
+              *reinterpret_cast<uint4 *>(dst + c) = u;
+            }
+          } else {
+            for (int c = 0; c < 32; ++c)
+              if (nb + c < g.N) dst[c] = __float2bfloat16_rn(v[c]);
+          }
+        }
+      }
+      if (g.c16t) {  // transposed: for each column the 32 lanes write 32 consecutive rows
+#pragma unroll
+        for (int c = 0; c < 32; ++c)
+          if (row_ok && nb + c < g.N) g.c16t[(int64_t)(nb + c) * g.M + row] = __float2bfloat16_rn(v[c]);
+      }
+    }
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+  __syncthreads();
+  if (warp == 1) {
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+  }
+}
+
+// MSE of y against t over B x O entries: loss_acc += sum (y - t)^2 (FP32
+// block partials, one atomic per block); dy = 2 (y - t) / (B O) as BF16,
+// row-major and transposed.
+__global__ void k_mse_grad(const float *__restrict__ y, const float *__restrict__ t, int64_t B, int O,
+                           __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dyt, float *loss_acc) {
+  __shared__ float s_part[32];
+  const int64_t total = B * O;
+  const float scale = 2.f / (float)total;
+  float part = 0.f;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const float e = y[i] - t[i];
+    part += e * e;
+    const __nv_bfloat16 gv = __float2bfloat16_rn(scale * e);
+    dy[i] = gv;
+    const int64_t b = i / O, o = i - b * O;
+    dyt[o * B + b] = gv;
+  }
+  for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
+  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+  __syncthreads();
+  if (threadIdx.x < 32) {
+    float v = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0.f;
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if (threadIdx.x == 0 && loss_acc) atomicAdd(loss_acc, v);
+  }
+}
+
+// db[o] = sum_b dzt[o][b] (one warp per row, FP32 accumulation in a fixed order)
+__global__ void k_row_sums(const __nv_bfloat16 *__restrict__ dzt, int rows, int64_t cols, float *__restrict__ out) {
+  const int w = (blockIdx.x * blockDim.x + threadIdx.x) >> 5, lane = threadIdx.x & 31;
+  if (w >= rows) return;
+  const __nv_bfloat16 *r = dzt + (int64_t)w * cols;
+  float s = 0.f;
+  for (int64_t c = lane; c < cols; c += 32) s += __bfloat162float(r[c]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if (lane == 0) out[w] = s;
+}
+
+// FP32 [rows][cols] -> BF16 row-major copy and BF16 transposed copy [cols][rows]
+// (32 x 32 tiles through shared memory, coalesced on both sides)
+__global__ void k_to_bf16_both(const float *__restrict__ src, int rows, int cols, __nv_bfloat16 *__restrict__ dst,
+                               __nv_bfloat16 *__restrict__ dstt) {
+  __shared__ float tile[32][33];
+  const int c0 = blockIdx.x * 32, r0 = blockIdx.y * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  for (int k = ty; k < 32; k += 8) {
+    const int r = r0 + k, c = c0 + tx;
+    float v = 0.f;
+    if (r < rows && c < cols) {
+      v = src[(int64_t)r * cols + c];
+      if (dst) dst[(int64_t)r * cols + c] = __float2bfloat16_rn(v);
+    }
+    tile[k][tx] = v;
+  }
+  __syncthreads();
+  if (!dstt) return;
+  for (int k = ty; k < 32; k += 8) {
+    const int c = c0 + k, r = r0 + tx;
+    if (r < rows && c < cols) dstt[(int64_t)c * rows + r] = __float2bfloat16_rn(tile[tx][k]);
+  }
+}
+
+// AdamW on FP32 master parameters (decoupled weight decay):
+//   m = b1 m + (1 - b1) g, v = b2 v + (1 - b2) g^2,
+//   p -= lr (m / (1 - b1^t) / (sqrt(v / (1 - b2^t)) + eps) + wd p)
+// with wd applied only where decay_mask is set (weights, not biases).
+__global__ void k_adamw(float *__restrict__ p, const float *__restrict__ g, float *__restrict__ m, float *__restrict__ v,
+                        int64_t n, float lr, float b1, float b2, float eps, float wd, float c1, float c2,
+                        const uint8_t *__restrict__ decay_mask) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    const float mh = mi / c1, vh = vi / c2;
+    const float w = decay_mask && decay_mask[i] ? wd : 0.f;
+    p[i] = p[i] - lr * (mh / (sqrtf(vh) + eps) + w * p[i]);
+  }
+}
+
+// rows idx[i] of src [n][cols] (FP32) -> dst [count][cols]
+__global__ void k_gather_rows(const float *__restrict__ src, int cols, const int64_t *__restrict__ idx, int64_t count,
+                              float *__restrict__ dst) {
+  const int64_t total = count * cols;
+  for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < total; e += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t i = e / cols, c = e - i * cols;
+    dst[e] = src[idx[i] * cols + c];
+  }
+}
+
+// out[i] = 1 if any feature of row i lies outside [-1, 1] (the training box)
+__global__ void k_outside_box(const float *__restrict__ x, int64_t n, int cols, uint8_t *__restrict__ out) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+    uint8_t o = 0;
+    for (int c = 0; c < cols; ++c) {
+      const float v = x[i * cols + c];
+      if (!(v >= -1.f && v <= 1.f)) o = 1;
+    }
+    out[i] = o;
+  }
+}
+
+__global__ void k_accumulate_scalar(float *dst, const float *src, float scale) { *dst += scale * *src; }
+
+typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
+                                  const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
+                                  CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+EncodeTiledFn encode_fn() {
+  static EncodeTiledFn fn = nullptr;
+  if (!fn) {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<EncodeTiledFn>(p);
+  }
+  return fn;
+}
+
+// Tensor map of a row-major BF16 matrix [rows][cols] (cols = K, contiguous):
+// boxes of 8 columns x 128 rows, no swizzle, zero fill outside.
+cudaError_t make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols) {
+  EncodeTiledFn fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  if ((cols & 7) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorInvalidValue;
+  const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
+  const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
+  const cuuint32_t box[2] = {8, (cuuint32_t)kBM};
+  const cuuint32_t estr[2] = {1, 1};
+  const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
+}
+
+int grid_for(int64_t n, int threads) {
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n + threads - 1) / threads;
+  const int64_t cap = (int64_t)sms * 8;
+  return (int)(want < 1 ? 1 : (want > cap ? cap : want));
+}
+
+}  // namespace
+
+cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const float *bias, int act,
+                    const __nv_bfloat16 *mask, float *c32, __nv_bfloat16 *c16, __nv_bfloat16 *c16t, uint32_t *err,
+                    cudaStream_t st) {
+  if (M <= 0 || N <= 0 || K <= 0 || (K & 7) != 0) return cudaErrorInvalidValue;
+  static bool attr = false;
+  if (!attr) {
+    cudaError_t e = cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
+    if (e != cudaSuccess) return e;
+    attr = true;
+  }
+  CUtensorMap ma, mb;
+  cudaError_t e = make_map(&ma, A, M, K);
+  if (e != cudaSuccess) return e;
+  if ((e = make_map(&mb, B, N, K)) != cudaSuccess) return e;
+  GemmArgs g;
+  g.M = M; g.N = N; g.K = K;
+  g.bias = bias; g.act = act; g.mask = mask;
+  g.c32 = c32; g.c16 = c16; g.c16t = c16t; g.err = err;
+  dim3 grid((M + kBM - 1) / kBM, (N + kBN - 1) / kBN);
+  k_gemm_tn<<<grid, kGThreads, kGemmSmem, st>>>(ma, mb, g);
+  return cudaGetLastError();
+}
+
+cudaError_t mse_grad(const float *y, const float *t, int64_t B, int O, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
+                     float *loss_acc, cudaStream_t st) {
+  k_mse_grad<<<grid_for(B * O, 256), 256, 0, st>>>(y, t, B, O, dy, dyt, loss_acc);
+  return cudaGetLastError();
+}
+
+cudaError_t row_sums(const __nv_bfloat16 *dzt, int rows, int64_t cols, float *out, cudaStream_t st) {
+  const int threads = 256;
+  k_row_sums<<<(rows * 32 + threads - 1) / threads, threads, 0, st>>>(dzt, rows, cols, out);
+  return cudaGetLastError();
+}
+
+cudaError_t to_bf16_both(const float *src, int rows, int cols, __nv_bfloat16 *dst, __nv_bfloat16 *dstt,
+                         cudaStream_t st) {
+  dim3 grid((cols + 31) / 32, (rows + 31) / 32);
+  k_to_bf16_both<<<grid, 256, 0, st>>>(src, rows, cols, dst, dstt);
+  return cudaGetLastError();
+}
+
+cudaError_t adamw(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+                  float wd, int step, const uint8_t *decay_mask, cudaStream_t st) {
+  const float c1 = 1.f - powf(b1, (float)step), c2 = 1.f - powf(b2, (float)step);
+  k_adamw<<<grid_for(n, 256), 256, 0, st>>>(p, g, m, v, n, lr, b1, b2, eps, wd, c1, c2, decay_mask);
+  return cudaGetLastError();
+}
+
+cudaError_t gather_rows(const float *src, int cols, const int64_t *idx, int64_t count, float *dst, cudaStream_t st) {
+  k_gather_rows<<<grid_for(count * cols, 256), 256, 0, st>>>(src, cols, idx, count, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t accumulate_scalar(float *dst, const float *src, float scale, cudaStream_t st) {
+  k_accumulate_scalar<<<1, 1, 0, st>>>(dst, src, scale);
+  return cudaGetLastError();
+}
+
+cudaError_t outside_box(const float *x, int64_t n, int cols, uint8_t *out, cudaStream_t st) {
+  k_outside_box<<<grid_for(n, 256), 256, 0, st>>>(x, n, cols, out);
+  return cudaGetLastError();
+}
+
+}  // namespace rr

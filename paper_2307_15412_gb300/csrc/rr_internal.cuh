@@ -2,6 +2,7 @@
 // CUDA translation units of the radar ray-tracing library.  Not installed.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -178,7 +179,36 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
                             int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
                             cudaStream_t st);
+// Learned-surrogate kernels (see mlp.cu).  gemm_tn: C = A B^T with A
+// [M][K], B [N][K] BF16 row-major (K a multiple of 8, 16-byte aligned),
+// + bias[N], act 1 = ReLU, mask [M][N] BF16 (zero where mask <= 0); outputs
+// any of FP32 [M][N], BF16 [M][N], BF16 transposed [N][M].
+cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const float *bias, int act,
+                    const __nv_bfloat16 *mask, float *c32, __nv_bfloat16 *c16, __nv_bfloat16 *c16t, uint32_t *err,
+                    cudaStream_t st);
+cudaError_t mse_grad(const float *y, const float *t, int64_t B, int O, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
+                     float *loss_acc, cudaStream_t st);
+cudaError_t row_sums(const __nv_bfloat16 *dzt, int rows, int64_t cols, float *out, cudaStream_t st);
+cudaError_t to_bf16_both(const float *src, int rows, int cols, __nv_bfloat16 *dst, __nv_bfloat16 *dstt,
+                         cudaStream_t st);
+cudaError_t adamw(float *p, const float *g, float *m, float *v, int64_t n, float lr, float b1, float b2, float eps,
+                  float wd, int step, const uint8_t *decay_mask, cudaStream_t st);
+cudaError_t gather_rows(const float *src, int cols, const int64_t *idx, int64_t count, float *dst, cudaStream_t st);
+cudaError_t outside_box(const float *x, int64_t n, int cols, uint8_t *out, cudaStream_t st);
+// *dst += scale * *src (one thread)
+cudaError_t accumulate_scalar(float *dst, const float *src, float scale, cudaStream_t st);
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st);
 
+struct Surrogate;
+void surrogate_free(Surrogate *s);
+
 }  // namespace rr
+
+// Access to the context for the translation units outside capi.cu.
+cudaStream_t rr_ctx_stream(rr_ctx *c);
+uint32_t *rr_ctx_err(rr_ctx *c);
+int rr_ctx_device(rr_ctx *c);
+rr::Surrogate *&rr_ctx_surrogate(rr_ctx *c);
+rr_status rr_ctx_fail(rr_ctx *c, rr_status st, const char *fmt, ...);
+rr_status rr_ctx_cuda_fail(rr_ctx *c, cudaError_t e, const char *where);

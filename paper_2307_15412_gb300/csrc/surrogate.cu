@@ -1,0 +1,428 @@
+// surrogate.cu -- the rr_surrogate_* C ABI: parameters, activations and the
+// training / inference sequences of the learned surrogate around the
+// kernels of mlp.cu.
+//
+// Per layer l (W_l [out][in], BF16 copies W_l and W_l^T kept next to the FP32
+// master): forward
+//   h_l = relu(h_{l-1} W_l^T + b_l)   gemm_tn(A = h_{l-1} [B][in], B = W_l)
+// (written row-major for the next layer and transposed for the weight
+// gradient), backward with dz_L = 2 (y - t) / (B O):
+//   dW_l = dz_l^T h_{l-1}             gemm_tn(A = dz_l^T [out][B], B = h_{l-1}^T [in][B])
+//   db_l = sum_b dz_l                 row sums of dz_l^T
+//   dz_{l-1} = (dz_l W_l) * [h_{l-1} > 0]
+//                                     gemm_tn(A = dz_l [B][out], B = W_l^T [in][out], mask h_{l-1})
+// then AdamW on the FP32 master and a refresh of the BF16 copies.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <new>
+#include <vector>
+
+#include "rr.h"
+#include "rr_internal.cuh"
+
+namespace rr {
+
+constexpr int kMaxLayers = 8;
+constexpr int64_t kInferChunk = 4096;
+
+struct Surrogate {
+  int L = 0;                       // layers
+  int dims[kMaxLayers + 1] = {};
+  int64_t n_params = 0;
+  int64_t woff[kMaxLayers] = {}, boff[kMaxLayers] = {};
+  float *p = nullptr, *g = nullptr, *m = nullptr, *v = nullptr;
+  uint8_t *decay = nullptr;
+  __nv_bfloat16 *w16[kMaxLayers] = {}, *w16t[kMaxLayers] = {};
+  int step = 0;
+  // activations for up to bcap samples
+  int64_t bcap = 0;
+  __nv_bfloat16 *x16 = nullptr, *x16t = nullptr;
+  __nv_bfloat16 *h16[kMaxLayers] = {}, *h16t[kMaxLayers] = {};
+  __nv_bfloat16 *dz16[kMaxLayers] = {}, *dz16t[kMaxLayers] = {};
+  float *y = nullptr;
+  float *loss = nullptr;           // device scalar: sum of squared errors
+  // minibatch scratch of rr_surrogate_train
+  float *xb = nullptr, *tb = nullptr;
+  int64_t *idx = nullptr;
+  int64_t idx_cap = 0;
+};
+
+namespace {
+
+void free_acts(Surrogate *s) {
+  std::vector<void *> ptrs = {s->x16, s->x16t, s->y, s->xb, s->tb};
+  for (int l = 0; l < kMaxLayers; ++l) {
+    ptrs.push_back(s->h16[l]);
+    ptrs.push_back(s->h16t[l]);
+    ptrs.push_back(s->dz16[l]);
+    ptrs.push_back(s->dz16t[l]);
+    s->h16[l] = s->h16t[l] = s->dz16[l] = s->dz16t[l] = nullptr;
+  }
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  s->x16 = s->x16t = nullptr;
+  s->y = s->xb = s->tb = nullptr;
+  s->bcap = 0;
+}
+
+cudaError_t ensure_acts(Surrogate *s, int64_t B) {
+  if (B <= s->bcap) return cudaSuccess;
+  free_acts(s);
+  cudaError_t e = cudaSuccess;
+  auto bf = [&](__nv_bfloat16 *&q, int64_t n) {
+    if (e == cudaSuccess) e = cudaMalloc((void **)&q, sizeof(__nv_bfloat16) * n);
+  };
+  bf(s->x16, B * s->dims[0]);
+  bf(s->x16t, B * s->dims[0]);
+  for (int l = 0; l < s->L; ++l) {
+    const int64_t w = s->dims[l + 1];
+    if (l < s->L - 1) {
+      bf(s->h16[l], B * w);
+      bf(s->h16t[l], B * w);
+    }
+    bf(s->dz16[l], B * w);
+    bf(s->dz16t[l], B * w);
+  }
+  if (e == cudaSuccess) e = cudaMalloc((void **)&s->y, sizeof(float) * B * s->dims[s->L]);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&s->xb, sizeof(float) * B * s->dims[0]);
+  if (e == cudaSuccess) e = cudaMalloc((void **)&s->tb, sizeof(float) * B * s->dims[s->L]);
+  if (e == cudaSuccess) s->bcap = B;
+  else free_acts(s);
+  return e;
+}
+
+// BF16 copies of every weight matrix from the FP32 master
+cudaError_t refresh_bf16(Surrogate *s, cudaStream_t st) {
+  for (int l = 0; l < s->L; ++l) {
+    const cudaError_t e = to_bf16_both(s->p + s->woff[l], s->dims[l + 1], s->dims[l], s->w16[l], s->w16t[l], st);
+    if (e != cudaSuccess) return e;
+  }
+  return cudaSuccess;
+}
+
+// Forward pass on x [B][d0] (FP32, device).  keep_t: also write the
+// transposed activations the backward pass needs.
+cudaError_t forward(Surrogate *s, const float *x, int64_t B, bool keep_t, uint32_t *err, cudaStream_t st) {
+  cudaError_t e = to_bf16_both(x, (int)B, s->dims[0], s->x16, keep_t ? s->x16t : nullptr, st);
+  if (e != cudaSuccess) return e;
+  const __nv_bfloat16 *h = s->x16;
+  for (int l = 0; l < s->L; ++l) {
+    const bool last = l == s->L - 1;
+    e = gemm_tn(h, s->w16[l], (int)B, s->dims[l + 1], s->dims[l], s->p + s->boff[l], last ? 0 : 1, nullptr,
+                last ? s->y : nullptr, last ? nullptr : s->h16[l], (!last && keep_t) ? s->h16t[l] : nullptr, err, st);
+    if (e != cudaSuccess) return e;
+    if (!last) h = s->h16[l];
+  }
+  return cudaSuccess;
+}
+
+// Backward pass after forward(keep_t = true): gradients into s->g, the sum
+// of squared errors added to s->loss.
+cudaError_t backward(Surrogate *s, const float *t, int64_t B, uint32_t *err, cudaStream_t st) {
+  const int L = s->L;
+  cudaError_t e = mse_grad(s->y, t, B, s->dims[L], s->dz16[L - 1], s->dz16t[L - 1], s->loss, st);
+  if (e != cudaSuccess) return e;
+  for (int l = L - 1; l >= 0; --l) {
+    const int out = s->dims[l + 1], in = s->dims[l];
+    const __nv_bfloat16 *hin_t = l > 0 ? s->h16t[l - 1] : s->x16t;
+    e = gemm_tn(s->dz16t[l], hin_t, out, in, (int)B, nullptr, 0, nullptr, s->g + s->woff[l], nullptr, nullptr, err, st);
+    if (e != cudaSuccess) return e;
+    e = row_sums(s->dz16t[l], out, B, s->g + s->boff[l], st);
+    if (e != cudaSuccess) return e;
+    if (l > 0) {
+      e = gemm_tn(s->dz16[l], s->w16t[l], (int)B, in, out, nullptr, 0, s->h16[l - 1], nullptr, s->dz16[l - 1],
+                  s->dz16t[l - 1], err, st);
+      if (e != cudaSuccess) return e;
+    }
+  }
+  return cudaSuccess;
+}
+
+cudaError_t opt_step(Surrogate *s, const rr_adamw &o, cudaStream_t st) {
+  ++s->step;
+  cudaError_t e = adamw(s->p, s->g, s->m, s->v, s->n_params, o.lr, o.beta1, o.beta2, o.eps, o.weight_decay, s->step,
+                        s->decay, st);
+  if (e != cudaSuccess) return e;
+  return refresh_bf16(s, st);
+}
+
+rr_status get_sur(rr_ctx *c, Surrogate **out) {
+  Surrogate *s = rr_ctx_surrogate(c);
+  if (!s) return rr_ctx_fail(c, RR_ENOTREADY, "no surrogate: call rr_surrogate_create first");
+  *out = s;
+  return RR_OK;
+}
+
+bool opt_ok(const rr_adamw *o) {
+  return o && o->lr >= 0.f && o->beta1 >= 0.f && o->beta1 < 1.f && o->beta2 >= 0.f && o->beta2 < 1.f && o->eps > 0.f &&
+         o->weight_decay >= 0.f;
+}
+
+struct Guard {
+  int prev = -1;
+  explicit Guard(int dev) {
+    if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+    if (prev != dev) cudaSetDevice(dev);
+  }
+  ~Guard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+#define SUR_CUDA(c, call, where)                                          \
+  do {                                                                    \
+    cudaError_t e__ = (call);                                             \
+    if (e__ != cudaSuccess) return rr_ctx_cuda_fail((c), e__, where);     \
+  } while (0)
+
+}  // namespace
+
+void surrogate_free(Surrogate *s) {
+  if (!s) return;
+  free_acts(s);
+  void *ptrs[] = {s->p, s->g, s->m, s->v, s->decay, s->loss, s->idx};
+  for (void *q : ptrs)
+    if (q) cudaFree(q);
+  for (int l = 0; l < kMaxLayers; ++l) {
+    if (s->w16[l]) cudaFree(s->w16[l]);
+    if (s->w16t[l]) cudaFree(s->w16t[l]);
+  }
+  delete s;
+}
+
+}  // namespace rr
+
+using rr::Surrogate;
+
+extern "C" {
+
+rr_status rr_surrogate_create(rr_ctx *c, const int32_t *dims, int n_dims) {
+  if (!c) return RR_EINVAL;
+  if (!dims || n_dims < 2 || n_dims > rr::kMaxLayers + 1) return rr_ctx_fail(c, RR_EINVAL, "n_dims out of [2, 9]");
+  for (int i = 0; i < n_dims; ++i)
+    if (dims[i] < 8 || dims[i] % 8 != 0 || dims[i] > (1 << 16))
+      return rr_ctx_fail(c, RR_EINVAL, "layer width %d must be a positive multiple of 8 (<= 65536)", dims[i]);
+  rr::Guard g(rr_ctx_device(c));
+  if (rr_ctx_surrogate(c)) {
+    cudaStreamSynchronize(rr_ctx_stream(c));
+    rr::surrogate_free(rr_ctx_surrogate(c));
+    rr_ctx_surrogate(c) = nullptr;
+  }
+  Surrogate *s = new (std::nothrow) Surrogate();
+  if (!s) return rr_ctx_fail(c, RR_ENOMEM, "host allocation");
+  s->L = n_dims - 1;
+  int64_t off = 0;
+  for (int i = 0; i < n_dims; ++i) s->dims[i] = dims[i];
+  for (int l = 0; l < s->L; ++l) {
+    s->woff[l] = off;
+    off += (int64_t)dims[l + 1] * dims[l];
+    s->boff[l] = off;
+    off += dims[l + 1];
+  }
+  s->n_params = off;
+  rr_ctx_surrogate(c) = s;
+  const size_t nb = sizeof(float) * (size_t)off;
+  SUR_CUDA(c, cudaMalloc((void **)&s->p, nb), "surrogate parameters");
+  SUR_CUDA(c, cudaMalloc((void **)&s->g, nb), "surrogate gradients");
+  SUR_CUDA(c, cudaMalloc((void **)&s->m, nb), "surrogate moments");
+  SUR_CUDA(c, cudaMalloc((void **)&s->v, nb), "surrogate moments");
+  SUR_CUDA(c, cudaMalloc((void **)&s->decay, (size_t)off), "surrogate decay mask");
+  SUR_CUDA(c, cudaMalloc((void **)&s->loss, sizeof(float)), "surrogate loss");
+  cudaStream_t st = rr_ctx_stream(c);
+  SUR_CUDA(c, cudaMemsetAsync(s->p, 0, nb, st), "surrogate init");
+  SUR_CUDA(c, cudaMemsetAsync(s->m, 0, nb, st), "surrogate init");
+  SUR_CUDA(c, cudaMemsetAsync(s->v, 0, nb, st), "surrogate init");
+  SUR_CUDA(c, cudaMemsetAsync(s->decay, 0, (size_t)off, st), "surrogate init");
+  for (int l = 0; l < s->L; ++l) {
+    const int64_t nw = (int64_t)dims[l + 1] * dims[l];
+    SUR_CUDA(c, cudaMemsetAsync(s->decay + s->woff[l], 1, (size_t)nw, st), "surrogate init");
+    SUR_CUDA(c, cudaMalloc((void **)&s->w16[l], sizeof(__nv_bfloat16) * nw), "surrogate BF16 weights");
+    SUR_CUDA(c, cudaMalloc((void **)&s->w16t[l], sizeof(__nv_bfloat16) * nw), "surrogate BF16 weights");
+  }
+  SUR_CUDA(c, rr::refresh_bf16(s, st), "surrogate init");
+  return RR_OK;
+}
+
+int64_t rr_surrogate_num_params(rr_ctx *c) {
+  if (!c || !rr_ctx_surrogate(c)) return 0;
+  return rr_ctx_surrogate(c)->n_params;
+}
+
+rr_status rr_surrogate_set_params(rr_ctx *c, const float *params, int ptr_is_device) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!params) return rr_ctx_fail(c, RR_EINVAL, "params is NULL");
+  rr::Guard g(rr_ctx_device(c));
+  cudaStream_t cs = rr_ctx_stream(c);
+  const size_t nb = sizeof(float) * (size_t)s->n_params;
+  SUR_CUDA(c, cudaMemcpyAsync(s->p, params, nb, ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, cs),
+           "set_params");
+  if (!ptr_is_device) SUR_CUDA(c, cudaStreamSynchronize(cs), "set_params");
+  SUR_CUDA(c, cudaMemsetAsync(s->m, 0, nb, cs), "set_params");
+  SUR_CUDA(c, cudaMemsetAsync(s->v, 0, nb, cs), "set_params");
+  s->step = 0;
+  SUR_CUDA(c, rr::refresh_bf16(s, cs), "set_params");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_get_params(rr_ctx *c, float *out) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!out) return rr_ctx_fail(c, RR_EINVAL, "out is NULL");
+  rr::Guard g(rr_ctx_device(c));
+  SUR_CUDA(c, cudaMemcpyAsync(out, s->p, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, rr_ctx_stream(c)),
+           "get_params");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_forward(rr_ctx *c, const float *x, int64_t B, float *y) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!x || !y || B < 8 || B % 8 != 0 || B > (1 << 24))
+    return rr_ctx_fail(c, RR_EINVAL, "forward: batch %lld must be a positive multiple of 8", (long long)B);
+  rr::Guard g(rr_ctx_device(c));
+  cudaStream_t cs = rr_ctx_stream(c);
+  SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
+  SUR_CUDA(c, rr::forward(s, x, B, false, rr_ctx_err(c), cs), "surrogate forward");
+  SUR_CUDA(c, cudaMemcpyAsync(y, s->y, sizeof(float) * B * s->dims[s->L], cudaMemcpyDeviceToDevice, cs), "forward");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_gradients(rr_ctx *c, const float *x, const float *t, int64_t B, float *grads, float *loss) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!x || !t || B < 8 || B % 8 != 0 || B > (1 << 24))
+    return rr_ctx_fail(c, RR_EINVAL, "gradients: batch %lld must be a positive multiple of 8", (long long)B);
+  rr::Guard g(rr_ctx_device(c));
+  cudaStream_t cs = rr_ctx_stream(c);
+  SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
+  SUR_CUDA(c, cudaMemsetAsync(s->loss, 0, sizeof(float), cs), "gradients");
+  SUR_CUDA(c, rr::forward(s, x, B, true, rr_ctx_err(c), cs), "surrogate forward");
+  SUR_CUDA(c, rr::backward(s, t, B, rr_ctx_err(c), cs), "surrogate backward");
+  if (grads)
+    SUR_CUDA(c, cudaMemcpyAsync(grads, s->g, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, cs), "gradients");
+  if (loss) SUR_CUDA(c, cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, cs), "gradients");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_train_step(rr_ctx *c, const float *x, const float *t, int64_t B, const rr_adamw *opt,
+                                  float *loss) {
+  if (!c) return RR_EINVAL;
+  if (!rr::opt_ok(opt)) return rr_ctx_fail(c, RR_EINVAL, "AdamW settings out of range");
+  rr_status st = rr_surrogate_gradients(c, x, t, B, nullptr, loss);
+  if (st != RR_OK) return st;
+  Surrogate *s = rr_ctx_surrogate(c);
+  rr::Guard g(rr_ctx_device(c));
+  SUR_CUDA(c, rr::opt_step(s, *opt, rr_ctx_stream(c)), "AdamW");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_train(rr_ctx *c, const rr_train_cfg *cfg, const float *x, const float *t, int64_t n) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!cfg || !rr::opt_ok(&cfg->opt) || cfg->epochs < 0 || cfg->batch < 8 || cfg->batch % 8 != 0)
+    return rr_ctx_fail(c, RR_EINVAL, "train: bad configuration (batch must be a positive multiple of 8)");
+  if (!x || !t || n < cfg->batch) return rr_ctx_fail(c, RR_EINVAL, "train: need at least one full batch");
+  rr::Guard g(rr_ctx_device(c));
+  cudaStream_t cs = rr_ctx_stream(c);
+  const int64_t B = cfg->batch, steps = n / B;
+  SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
+  if (n > s->idx_cap) {
+    if (s->idx) cudaFree(s->idx);
+    s->idx = nullptr;
+    s->idx_cap = 0;
+    SUR_CUDA(c, cudaMalloc((void **)&s->idx, sizeof(int64_t) * n), "train order");
+    s->idx_cap = n;
+  }
+  std::vector<int64_t> order(n);
+  int64_t *pin = nullptr;
+  SUR_CUDA(c, cudaMallocHost((void **)&pin, sizeof(int64_t) * n), "train order");
+  std::vector<float> epoch_loss(cfg->epochs > 0 ? cfg->epochs : 1, 0.f);
+  float *dloss = nullptr;
+  cudaError_t e = cudaMalloc((void **)&dloss, sizeof(float) * (cfg->epochs > 0 ? cfg->epochs : 1));
+  if (e == cudaSuccess) e = cudaMemsetAsync(dloss, 0, sizeof(float) * (cfg->epochs > 0 ? cfg->epochs : 1), cs);
+  uint64_t state = cfg->seed * 0x9E3779B97F4A7C15ull + 0x2545F4914F6CDD1Dull;
+  auto next = [&]() {  // xorshift64*: the sample order only
+    state ^= state >> 12;
+    state ^= state << 25;
+    state ^= state >> 27;
+    return state * 0x2545F4914F6CDD1Dull;
+  };
+  for (int ep = 0; ep < cfg->epochs && e == cudaSuccess; ++ep) {
+    for (int64_t i = 0; i < n; ++i) order[i] = i;
+    for (int64_t i = n - 1; i > 0; --i) {  // Fisher-Yates
+      const int64_t j = (int64_t)(next() % (uint64_t)(i + 1));
+      const int64_t tmp = order[i];
+      order[i] = order[j];
+      order[j] = tmp;
+    }
+    e = cudaStreamSynchronize(cs);  // the previous epoch's copy out of `pin` is done
+    if (e != cudaSuccess) break;
+    for (int64_t i = 0; i < n; ++i) pin[i] = order[i];
+    e = cudaMemcpyAsync(s->idx, pin, sizeof(int64_t) * n, cudaMemcpyHostToDevice, cs);
+    for (int64_t k = 0; k < steps && e == cudaSuccess; ++k) {
+      e = rr::gather_rows(x, s->dims[0], s->idx + k * B, B, s->xb, cs);
+      if (e == cudaSuccess) e = rr::gather_rows(t, s->dims[s->L], s->idx + k * B, B, s->tb, cs);
+      if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, sizeof(float), cs);
+      if (e == cudaSuccess) e = rr::forward(s, s->xb, B, true, rr_ctx_err(c), cs);
+      if (e == cudaSuccess) e = rr::backward(s, s->tb, B, rr_ctx_err(c), cs);
+      if (e == cudaSuccess) e = rr::opt_step(s, cfg->opt, cs);
+      // epoch loss: mean over the epoch's minibatches of their mean squared error
+      if (e == cudaSuccess && cfg->loss_out)
+        e = rr::accumulate_scalar(dloss + ep, s->loss, 1.f / ((float)steps * (float)B * (float)s->dims[s->L]), cs);
+    }
+  }
+  if (e == cudaSuccess && cfg->loss_out && cfg->epochs > 0)
+    e = cudaMemcpyAsync(epoch_loss.data(), dloss, sizeof(float) * cfg->epochs, cudaMemcpyDeviceToHost, cs);
+  if (e == cudaSuccess && cfg->loss_out) e = cudaStreamSynchronize(cs);
+  if (e == cudaSuccess && cfg->loss_out)
+    for (int ep = 0; ep < cfg->epochs; ++ep) cfg->loss_out[ep] = epoch_loss[ep];
+  if (pin) cudaFreeHost(pin);
+  if (dloss) cudaFree(dloss);
+  if (e != cudaSuccess) return rr_ctx_cuda_fail(c, e, "surrogate train");
+  return RR_OK;
+}
+
+rr_status rr_surrogate_infer(rr_ctx *c, const float *x, int64_t n, float *y_out, uint8_t *fell_back) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!x || !y_out || n < 0) return rr_ctx_fail(c, RR_EINVAL, "infer: null pointer or negative n");
+  if (n == 0) return RR_OK;
+  rr::Guard g(rr_ctx_device(c));
+  cudaStream_t cs = rr_ctx_stream(c);
+  const int64_t chunk = n < rr::kInferChunk ? ((n + 7) / 8) * 8 : rr::kInferChunk;
+  SUR_CUDA(c, rr::ensure_acts(s, chunk), "surrogate activations");
+  const int din = s->dims[0], dout = s->dims[s->L];
+  for (int64_t r0 = 0; r0 < n; r0 += chunk) {
+    const int64_t rows = n - r0 < chunk ? n - r0 : chunk;
+    const int64_t padded = ((rows + 7) / 8) * 8;
+    const float *xin = x + r0 * din;
+    if (padded != rows) {  // copy the ragged tail into the zero-padded scratch batch
+      SUR_CUDA(c, cudaMemsetAsync(s->xb, 0, sizeof(float) * padded * din, cs), "infer");
+      SUR_CUDA(c, cudaMemcpyAsync(s->xb, xin, sizeof(float) * rows * din, cudaMemcpyDeviceToDevice, cs), "infer");
+      xin = s->xb;
+    }
+    SUR_CUDA(c, rr::forward(s, xin, padded, false, rr_ctx_err(c), cs), "surrogate forward");
+    SUR_CUDA(c, cudaMemcpyAsync(y_out + r0 * dout, s->y, sizeof(float) * rows * dout, cudaMemcpyDeviceToDevice, cs),
+             "infer");
+  }
+  if (fell_back) SUR_CUDA(c, rr::outside_box(x, n, din, fell_back, cs), "infer");
+  return RR_OK;
+}
+
+}  // extern "C"

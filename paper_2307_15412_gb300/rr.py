@@ -49,6 +49,16 @@ class rr_job(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("grid", rr_raygrid)]
 
 
+class rr_adamw(ctypes.Structure):
+    _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
+                ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float)]
+
+
+class rr_train_cfg(ctypes.Structure):
+    _fields_ = [("opt", rr_adamw), ("epochs", ctypes.c_int32), ("batch", ctypes.c_int32),
+                ("seed", ctypes.c_uint64), ("loss_out", ctypes.POINTER(ctypes.c_float))]
+
+
 RR_BATCH_GRAPH = 1
 RR_BATCH_AUTOTUNE = 2
 
@@ -71,6 +81,15 @@ SIGNATURES = {
     "rr_get_bvh": (_I, [_P, _I, _P, _P, _P, _P, _P, ctypes.POINTER(ctypes.c_int32)]),
     "rr_synth_if_from_hits_noalloc": (_I, [ctypes.POINTER(rr_radar), _I, _I64, _P, _P, _P, _P, _P]),
     "rr_batch_run": (_I, [_P, ctypes.POINTER(rr_job), _I, ctypes.POINTER(rr_radar), _I, _I, _P, _P, _I]),
+    "rr_surrogate_create": (_I, [_P, _P, _I]),
+    "rr_surrogate_num_params": (_I64, [_P]),
+    "rr_surrogate_set_params": (_I, [_P, _P, _I]),
+    "rr_surrogate_get_params": (_I, [_P, _P]),
+    "rr_surrogate_forward": (_I, [_P, _P, _I64, _P]),
+    "rr_surrogate_gradients": (_I, [_P, _P, _P, _I64, _P, _P]),
+    "rr_surrogate_train_step": (_I, [_P, _P, _P, _I64, ctypes.POINTER(rr_adamw), _P]),
+    "rr_surrogate_train": (_I, [_P, ctypes.POINTER(rr_train_cfg), _P, _P, _I64]),
+    "rr_surrogate_infer": (_I, [_P, _P, _I64, _P, _P]),
     "rr_timing_enable": (_I, [_P, _I]),
     "rr_timing_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -255,6 +274,48 @@ class Context:
         flags = (RR_BATCH_GRAPH if graph else 0) | (RR_BATCH_AUTOTUNE if autotune else 0)
         self._check(self.lib.rr_batch_run(self.h, arr, len(arr), ctypes.byref(rs), int(variant), int(window),
                                           _ptr(if_out), _ptr(rd_out), flags))
+
+    # ---- learned surrogate (argument marshalling only; see include/rr.h)
+
+    def surrogate_create(self, dims):
+        arr = (ctypes.c_int32 * len(dims))(*[int(d) for d in dims])
+        self._check(self.lib.rr_surrogate_create(self.h, arr, len(dims)))
+
+    def surrogate_num_params(self) -> int:
+        return int(self.lib.rr_surrogate_num_params(self.h))
+
+    def surrogate_set_params(self, params):
+        """params: packed FP32 [W1, b1, W2, b2, ...], numpy (host) or torch CUDA."""
+        on_dev = hasattr(params, "is_cuda") and params.is_cuda
+        if not on_dev:
+            params = np.ascontiguousarray(params, np.float32)
+        self._check(self.lib.rr_surrogate_set_params(self.h, _ptr(params), 1 if on_dev else 0))
+
+    def surrogate_get_params(self, out):
+        self._check(self.lib.rr_surrogate_get_params(self.h, _ptr(out)))
+
+    def surrogate_forward(self, x, y):
+        self._check(self.lib.rr_surrogate_forward(self.h, _ptr(x), int(x.shape[0]), _ptr(y)))
+
+    def surrogate_gradients(self, x, t, grads=None, loss=None):
+        self._check(self.lib.rr_surrogate_gradients(self.h, _ptr(x), _ptr(t), int(x.shape[0]), _ptr(grads), _ptr(loss)))
+
+    def surrogate_train_step(self, x, t, lr=1e-3, beta1=0.9, beta2=0.999, eps=1e-8, weight_decay=0.0, loss=None):
+        o = rr_adamw(lr, beta1, beta2, eps, weight_decay)
+        self._check(self.lib.rr_surrogate_train_step(self.h, _ptr(x), _ptr(t), int(x.shape[0]), ctypes.byref(o),
+                                                     _ptr(loss)))
+
+    def surrogate_train(self, x, t, epochs: int, batch: int, seed: int = 0, lr=1e-3, beta1=0.9, beta2=0.999,
+                        eps=1e-8, weight_decay=0.0):
+        """Returns the mean training loss of every epoch (waits for the stream)."""
+        losses = (ctypes.c_float * max(int(epochs), 1))()
+        cfg = rr_train_cfg(rr_adamw(lr, beta1, beta2, eps, weight_decay), int(epochs), int(batch), int(seed),
+                           ctypes.cast(losses, ctypes.POINTER(ctypes.c_float)))
+        self._check(self.lib.rr_surrogate_train(self.h, ctypes.byref(cfg), _ptr(x), _ptr(t), int(x.shape[0])))
+        return [float(v) for v in losses[:int(epochs)]]
+
+    def surrogate_infer(self, x, y, fell_back=None):
+        self._check(self.lib.rr_surrogate_infer(self.h, _ptr(x), int(x.shape[0]), _ptr(y), _ptr(fell_back)))
 
     def timing_enable(self, n_slots: int):
         self._check(self.lib.rr_timing_enable(self.h, int(n_slots)))
