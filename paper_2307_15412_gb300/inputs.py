@@ -260,6 +260,73 @@ def hand_mesh(n_tri_target: int, angles_deg: Sequence[float],
     return V.astype(np.float32), F.astype(np.int32)
 
 
+def _rot_batch(axis: int, a: np.ndarray) -> np.ndarray:
+    """[P][3][3] rotations by angles a[P] about x (0), y (1) or z (2)."""
+    c, s = np.cos(a), np.sin(a)
+    R = np.zeros((a.size, 3, 3))
+    i, j = [(1, 2), (0, 2), (0, 1)][axis]
+    R[:, axis, axis] = 1.0
+    R[:, i, i] = c
+    R[:, j, j] = c
+    if axis == 1:
+        R[:, 0, 2], R[:, 2, 0] = s, -s
+    else:
+        R[:, i, j], R[:, j, i] = -s, s
+    return R
+
+
+_TEMPLATES = {}
+
+
+def _hand_templates(S: int):
+    """Box and the 15 capsule templates of segment count S (shared by all poses)."""
+    if S not in _TEMPLATES:
+        quad = 7.2 * _CM / S
+        box = _box(PALM_HALF, quad)
+        caps = [[_capsule(S, PHALANX_LEN[k] * FINGER_SCALE[f], FINGER_RADIUS[f]) for k in range(3)] for f in range(5)]
+        _TEMPLATES[S] = (box, caps)
+    return _TEMPLATES[S]
+
+
+def hand_meshes(n_tri_target: int, angles_deg: np.ndarray, centers: np.ndarray):
+    """The procedural hand of hand_mesh for P poses at once: V float32
+    [P][nv][3], F int32 [nt][3] (one topology).  Same construction, evaluated
+    with batched rotations (values agree with hand_mesh to float32 rounding)."""
+    ang = np.atleast_2d(np.asarray(angles_deg, dtype=np.float64))
+    centers = np.atleast_2d(np.asarray(centers, dtype=np.float64))
+    P = ang.shape[0]
+    flex = np.radians(ang[:, 0:15]).reshape(P, 5, 3)
+    small = np.radians((ang[:, 15:27] - 30.0) / 3.0)
+    abd, twist, tilt = small[:, 0:5], small[:, 5:10], small[:, 10:12]
+    S = segments_for_triangles(n_tri_target)
+    (Vb, Fb), caps = _hand_templates(S)
+    parts_v = [np.broadcast_to(Vb, (P,) + Vb.shape)]
+    parts_f = [Fb]
+    nbase = len(Vb)
+    for f in range(5):
+        if f == 0:
+            base = np.broadcast_to(np.array(THUMB_BASE), (P, 3)).copy()
+            Q = np.broadcast_to(_rz(math.radians(THUMB_SPLAY_DEG)), (P, 3, 3)).copy()
+        else:
+            base = np.broadcast_to(np.array([FINGER_BASE_X[f], PALM_HALF[1], 0.0]), (P, 3)).copy()
+            Q = np.broadcast_to(np.eye(3), (P, 3, 3)).copy()
+        Q = Q @ _rot_batch(2, abd[:, f]) @ _rot_batch(1, twist[:, f])
+        pos = base
+        for k in range(3):
+            Q = Q @ _rot_batch(0, -flex[:, f, k])
+            L = PHALANX_LEN[k] * FINGER_SCALE[f]
+            Vc, Fc = caps[f][k]
+            parts_v.append(pos[:, None, :] + np.einsum("vj,pij->pvi", Vc, Q))
+            parts_f.append(Fc + nbase)
+            nbase += len(Vc)
+            pos = pos + L * Q[:, :, 1]
+    V = np.concatenate(parts_v, axis=1)
+    F = np.concatenate(parts_f, axis=0)
+    G = _rot_batch(0, tilt[:, 0]) @ _rot_batch(1, tilt[:, 1])
+    V = np.einsum("pvj,pij->pvi", V, G) + centers[:, None, :]
+    return V.astype(np.float32), F.astype(np.int32)
+
+
 @dataclasses.dataclass
 class Scene:
     V: np.ndarray          # float32 [nv,3]
@@ -421,5 +488,17 @@ def surrogate_scene(raw_row: np.ndarray, n_tri_target: int = SURROGATE_TRIANGLES
     vr, vx = raw_row[N_ANGLES + 3], raw_row[N_ANGLES + 4]
     chat = center / np.linalg.norm(center)
     vel = vr * chat + np.array([vx, 0.0, 0.0])
-    V, F = hand_mesh(n_tri_target, raw_row[:N_ANGLES], center)
-    return Scene(V=V, F=F, vel=vel.astype(np.float32), center=center, angles_deg=raw_row[:N_ANGLES])
+    V, F = hand_meshes(n_tri_target, raw_row[None, :N_ANGLES], center[None])
+    return Scene(V=V[0], F=F, vel=vel.astype(np.float32), center=center, angles_deg=raw_row[:N_ANGLES])
+
+
+def surrogate_scenes(raw: np.ndarray, n_tri_target: int = SURROGATE_TRIANGLES):
+    """Vertices [P][nv][3], shared faces and velocities [P][3] of many
+    parameter vectors at once (the batched form of surrogate_scene)."""
+    raw = np.atleast_2d(np.asarray(raw, np.float64))
+    center = raw[:, N_ANGLES:N_ANGLES + 3]
+    chat = center / np.linalg.norm(center, axis=1, keepdims=True)
+    vel = raw[:, N_ANGLES + 3:N_ANGLES + 4] * chat
+    vel[:, 0] += raw[:, N_ANGLES + 4]
+    V, F = hand_meshes(n_tri_target, raw[:, :N_ANGLES], center)
+    return V, F, vel.astype(np.float32)

@@ -39,3 +39,19 @@ def test_random_hits_layout():
     assert d.shape == a.shape == dd.shape == (3, 100)
     assert d.dtype == np.float32
     assert np.abs(d[1] - d[0]).max() <= 2.5e-3 + 1e-7
+
+
+def test_batched_hand_meshes_equal_single_meshes():
+    r = I.surrogate_inputs(3, 5)
+    V, F, vel = I.surrogate_scenes(r)
+    for i in range(5):
+        s = I.surrogate_scene(r[i])
+        V1, F1 = I.hand_mesh(I.SURROGATE_TRIANGLES, r[i, :27], r[i, 27:30])
+        assert np.array_equal(V[i], V1) and np.array_equal(F, F1)
+        assert np.array_equal(s.V, V1) and np.allclose(s.vel, vel[i])
+
+
+def test_surrogate_features_map_the_box_to_unit_cube():
+    lo, hi = I.SURROGATE_LO, I.SURROGATE_HI
+    f = I.surrogate_features(np.stack([lo, hi, 0.5 * (lo + hi)]))
+    assert np.allclose(f[0], -1) and np.allclose(f[1], 1) and np.allclose(f[2], 0, atol=1e-6)
