@@ -3,12 +3,14 @@
 One step = 16 radar frames of the full-frame workload through the C ABI
 (rr_batch_run): for every frame build_bvh (LBVH of a ~22k-triangle hand),
 trace_frame (512 x 512 rays, echo for 3 receive antennas), synth_if (64
-chirps x 256 samples, plain FP32 path with the FP64 carrier reduction) and
-range_doppler, with one launch per stage over all 16 frames, replayed from
-a CUDA graph.  The 16 seeded scenes (pose, range U(0.2, 0.6) m, radial speed
-U(-1, 1) m/s) are resident in HBM; L2 is flushed (256 MiB write) before
-every timed step.  Device time comes from CUDA events on the library's
-stream.
+chirps x 256 samples as a split-time complex GEMM on the tensor cores,
+split-BF16x3, after the FP64 carrier reduction) and range_doppler, with one
+launch per stage over all 16 frames, replayed from a CUDA graph.  The plain
+FP32 synthesis path is timed beside it on the same steps, and frame 0's IF
+cube is checked against the FP64 oracle.  The 16 seeded scenes (pose, range
+U(0.2, 0.6) m, radial speed U(-1, 1) m/s) are resident in HBM; L2 is
+flushed (256 MiB write) before every timed step.  Device time comes from
+CUDA events on the one stream all work runs on.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 
@@ -35,7 +37,7 @@ sys.path.insert(0, ROOT)
 METRIC = "radar frames/s on 1 GB300 (trace+IF synth) vs plain FP32 path at rel-L2<=1e-3"
 WORKLOAD = ("full frame: seeded ~22k-triangle hand, range U(0.2,0.6) m, radial speed U(-1,1) m/s; "
             "512x512 rays over +-45 deg; 1 TX 3 RX (L, lambda/2); 64 chirps x 256 samples, 60-64 GHz "
-            "in 64 us; LBVH build + trace + echo + FP32 IF synthesis + range-Doppler per frame")
+            "in 64 us; LBVH build + trace + echo + IF synthesis + range-Doppler per frame")
 FRAMES_PER_STEP = 16
 N_SCENES = FRAMES_PER_STEP
 FLUSH_BYTES = 256 << 20
@@ -44,6 +46,8 @@ FP32_LANES_PER_SM = 128
 # tile numbering, traversal, hit prefix, echo, IF synthesis, split-K sum,
 # range FFT rows, Doppler FFT columns
 LAUNCHES_PER_STEP = 9
+SYNTH_FP32, SYNTH_TC_BF16X3 = 0, 1
+VARIANT, VARIANT_NAME = SYNTH_TC_BF16X3, "tensor-core split-BF16x3 (tcgen05)"
 
 
 def _peaks():
@@ -178,7 +182,9 @@ def run_gpu(args):
     from paper_2307_15412_gb300 import rr
 
     dev = torch.device("cuda", local)
-    stream = torch.cuda.current_stream(dev)
+    # one stream for everything: the L2 flush, the copies and the library
+    stream = torch.cuda.Stream(dev)
+    torch.cuda.set_stream(stream)
     ctx = rr.Context(local, stream)
     radar, grid, scenes = make_scenes(rank)
     B = len(scenes)
@@ -189,6 +195,7 @@ def run_gpu(args):
     rd_out = torch.empty_like(if_out)
     flush = torch.empty(FLUSH_BYTES, dtype=torch.uint8, device=dev)
     jobs = [(k, grid) for k in range(B)]
+    variant = VARIANT
 
     # hit counts per scene (deterministic per scene) for the flop count
     counts = []
@@ -198,17 +205,28 @@ def run_gpu(args):
         ctx.sync()
         counts.append(box[0])
 
-    def step(graph=True):
-        ctx.batch_run(jobs, radar, if_out=if_out, rd_out=rd_out, graph=graph, autotune=True)
+    def step(v=variant, graph=True):
+        ctx.batch_run(jobs, radar, if_out=if_out, rd_out=rd_out, variant=v, graph=graph, autotune=True)
+
+    def timed_steps(v, K):
+        """Device ms of K graph-replayed steps (L2 flushed before each)."""
+        ctx.timing_enable(K)
+        for i in range(K):
+            flush.zero_()  # L2 flush, outside the step's events
+            step(v)
+        ctx.sync()
+        ms = np.array([ctx.timing_read(i)[4] for i in range(K)])
+        ctx.timing_enable(0)
+        return ms
 
     # warm-up: the first call autotunes, the first graph call captures
-    for i in range(max(args.warmup, 3)):
-        step()
+    for v in (variant, SYNTH_FP32):
+        for i in range(max(args.warmup, 3)):
+            step(v)
     ctx.sync()
     torch.cuda.synchronize()
 
     K = args.steps
-    ctx.timing_enable(K)
     props = torch.cuda.get_device_properties(dev)
     uuid = getattr(props, "uuid", None)
     sampler = ClockSampler(("GPU-%s" % uuid) if uuid is not None else local)
@@ -218,17 +236,12 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
-    for i in range(K):
-        flush.zero_()  # L2 flush, outside the step's events
-        step()
+    step_ms = timed_steps(variant, K)
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
-    ctx.sync()
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    step_ms = np.array([ctx.timing_read(i)[4] for i in range(K)])
-    ctx.timing_enable(0)
     t_dev = float(step_ms.sum()) / 1e3
     if ws > 1:
         tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
@@ -236,30 +249,52 @@ def run_gpu(args):
         t_dev = float(tt.item())
     value = ws * B * K / t_dev
 
+    # the plain FP32 path beside it, same steps and timing
+    K32 = max(10, min(K, 100))
+    fp32_ms = timed_steps(SYNTH_FP32, K32)
+    fp32_value = ws * B * K32 / (float(fp32_ms.sum()) / 1e3)
+
     # stage breakdown: the same steps run eagerly (a graph replay has no
     # events between its kernels), L2 flushed before each
     KS = max(5, min(K, 50))
     ctx.timing_enable(KS)
     for i in range(KS):
         flush.zero_()
-        step(graph=False)
+        step(variant, graph=False)
     ctx.sync()
     stages = np.array([ctx.timing_read(i) for i in range(KS)])  # build, trace, synth, rd, whole (ms)
     ctx.timing_enable(0)
 
-    # dominant kernel: the IF synthesis (k_synth_fp32 over all frames of the step + its split-K sum)
+    # dominant kernel: the IF synthesis of all frames of a step on the tensor
+    # cores (k_synth_tc + its split-K sum); algorithmic work = 8 flop per
+    # complex multiply-add of Eq. 4's sum over (hit, rx, chirp, sample)
     flops_step = sum(8.0 * counts[k] * n_rx * M * N for k in range(B))
     achieved = flops_step / (float(stages[:, 2].mean()) / 1e3) / 1e12
     peaks = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "synth_fp32_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            traffic = json.load(open(tfile)).get("bytes_per_launch")
-        except Exception:
-            traffic = None
+    peak_tc = float(peaks.get("bf16_tflops_sustained", 1700.0))
+    peak_fp32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+
+    # accuracy of the timed configuration: frame 0 through the same kernels,
+    # its IF cube against the FP64 oracle's sum over the same hit list
+    acc = None
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        one = torch.empty((n_rx, M, N, 2), dtype=torch.float32, device=dev)
+        ctx.build_bvh(0)
+        box = ctx.trace_frame(0, radar, grid)
+        ctx.sync()
+        Kh = box[0]
+        hd = torch.empty((n_rx, Kh), dtype=torch.float32, device=dev)
+        ha, hdd = torch.empty_like(hd), torch.empty_like(hd)
+        ctx.get_hits(0, Kh, None, None, None, hd, ha, hdd)
+        ctx.synth_if(0, radar, one, variant=variant)
+        ctx.sync()
+        ref = oracle.synth(hd.cpu().numpy(), ha.cpu().numpy(), hdd.cpu().numpy(), radar)
+        got = one.double().cpu().numpy()
+        got = got[..., 0] + 1j * got[..., 1]
+        acc = {"rel_l2_if_vs_fp64_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+               "frame": "scene 0 (%d hits), same hit list on both sides" % Kh, "bound": 1e-3}
 
     # end to end through the public API: every step copies the frames' meshes
     # from pinned host memory to the device, uploads them into the scene
@@ -311,18 +346,25 @@ def run_gpu(args):
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,
                 "warmup": args.warmup, "ms_per_step": 1e3 * t_dev / K, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-                "config": {"workload": WORKLOAD, "frames_per_step": B, "synth": "fp32",
+                "config": {"workload": WORKLOAD, "frames_per_step": B, "synth": VARIANT_NAME,
                            "mean_hits_per_frame": float(np.mean(counts)),
                            "l2": "flushed before every timed step (256 MiB write, outside the events)",
                            "execution": "rr_batch_run: one launch per stage over all frames of the step, "
                                         "replayed from a CUDA graph; autotuned tile shape and split-K",
                            "parallelism": "replicas (independent frames per GPU)"},
-                "roofline": {"bound": "alu", "kernel": "k_synth_fp32 (+ split-K sum), all frames of a step",
-                             "achieved": achieved, "peak": peak, "unit": "TFLOP/s", "frac": achieved / peak,
-                             "traffic": traffic,
+                "roofline": {"bound": "tensor", "kernel": "k_synth_tc<BF16x3> (+ split-K sum), all frames of a step",
+                             "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s", "frac": achieved / peak_tc,
+                             "traffic": None,
+                             "work": "algorithmic: 8 flop per complex MAC of Eq. 4 (the kernel issues 12x as many "
+                                     "tensor flops: 4 expansion terms x 3 BF16 products)",
                              "timing": "synthesis stage of %d eager steps (CUDA events on the library stream)" % KS,
-                             "peak_source": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
-                                            % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max)},
+                             "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"},
+                "plain_fp32": {"value": fp32_value, "unit": "frames/s", "steps": K32,
+                               "ms_per_step": float(fp32_ms.mean()),
+                               "roofline_peak_fp32_tflops": peak_fp32,
+                               "peak_source": "%d SMs x %d FP32 lanes x 2 flop x %.0f MHz (max SM clock)"
+                                              % (props.multi_processor_count, FP32_LANES_PER_SM, sm_max)},
+                "accuracy": acc,
                 "cpu_baseline": cpu,
                 "e2e": {"value": ws * B * K_e2e / t_e2e, "unit": "frames/s", "h2d_bytes_per_step": h2d,
                         "d2h_bytes_per_step": d2h, "steps": K_e2e},

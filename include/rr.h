@@ -87,7 +87,9 @@ typedef enum {
 /* ---- context ----------------------------------------------------------- */
 
 /* Creates a context on CUDA device `device`.  cuda_stream: a cudaStream_t
- * to issue all work on (not owned), or NULL for a context-owned stream. */
+ * to issue all work on (not owned; cudaStreamLegacy and cudaStreamPerThread
+ * are accepted), or NULL for a context-owned non-blocking stream, which is
+ * not ordered with work the caller issues on other streams. */
 rr_status rr_create(rr_ctx **out, int device, void *cuda_stream);
 rr_status rr_destroy(rr_ctx *ctx);
 /* Replaces the stream used by later calls (not owned; NULL = own stream). */
@@ -169,6 +171,16 @@ rr_status rr_synth_if_from_hits(rr_ctx *ctx, const rr_radar *radar, rr_synth_var
 rr_status rr_range_doppler(rr_ctx *ctx, const float *if_in, int n_rx, int n_chirps, int n_samples,
                            int window, float *rd_out);
 
+/* Phase-referenced cube: out[f][j][c] = in[f][j][c] conj(r) / |r| with
+ * r = in[f][0][c], for n_frames frames of n_rx channels of `cells` complex
+ * values (device complex64; in == out allowed).  Channel 0 becomes |r|, the
+ * other channels keep their phase relative to channel 0.  The common phase
+ * of a cell changes by 2 pi for every lambda / 2 of path; this removes it
+ * and keeps what varies smoothly with the scene (magnitude and the
+ * phase differences between antennas), the form in which the learned
+ * surrogate represents a frame.  A cell with r = 0 is copied unchanged. */
+rr_status rr_phase_reference(rr_ctx *ctx, const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out);
+
 /* ---- whole frame --------------------------------------------------------- */
 
 /* One frame of the hot path on a scene already uploaded: build_bvh,
@@ -247,6 +259,10 @@ typedef struct {
  * layer widths (n_dims >= 2, every width a multiple of 8, at most 8
  * layers); parameters start at zero until rr_surrogate_set_params. */
 rr_status rr_surrogate_create(rr_ctx *ctx, const int32_t *dims, int n_dims);
+/* Unit of the targets and outputs (default 1): the network is trained on
+ * t / scale and its outputs are multiplied by scale, so that data of any
+ * magnitude meet weights of order one.  scale > 0. */
+rr_status rr_surrogate_set_scale(rr_ctx *ctx, float scale);
 /* Number of packed FP32 parameters. */
 int64_t rr_surrogate_num_params(rr_ctx *ctx);
 /* Loads packed FP32 parameters (host if ptr_is_device == 0, else device);

@@ -57,6 +57,7 @@ struct rr_ctx {
     int64_t if_tmp_cap = 0;
     // CUDA graph of the last batch
     cudaGraphExec_t exec = nullptr;
+    cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
     uint64_t key = 0;
     // autotuner choices per batch shape: (ray-tile width log2, split-K)
     std::map<uint64_t, std::pair<int, int>> tuned;
@@ -270,6 +271,7 @@ rr_status rr_destroy(rr_ctx *c) {
     if (b.h_btab) cudaFreeHost(b.h_btab);
     if (b.staged) cudaEventDestroy(b.staged);
     if (b.exec) cudaGraphExecDestroy(b.exec);
+    if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
   }
   if (c->sur) rr::surrogate_free(c->sur);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
@@ -498,6 +500,16 @@ rr_status rr_range_doppler(rr_ctx *c, const float *if_in, int n_rx, int n_chirps
   return RR_OK;
 }
 
+rr_status rr_phase_reference(rr_ctx *c, const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out) {
+  if (!c) return RR_EINVAL;
+  if (!in || !out || n_frames < 0 || n_rx < 1 || n_rx > RR_MAX_RX || cells < 1)
+    return fail(c, RR_EINVAL, "phase_reference: bad arguments");
+  if (n_frames == 0) return RR_OK;
+  DeviceGuard g(c->device);
+  RR_CUDA(c, rr::launch_phase_reference(in, n_frames, n_rx, cells, out, c->stream), "phase_reference launch");
+  return RR_OK;
+}
+
 rr_status rr_timing_enable(rr_ctx *c, int n_slots) {
   if (!c) return RR_EINVAL;
   if (n_slots < 0 || n_slots > 1 << 20) return fail(c, RR_EINVAL, "n_slots out of range");
@@ -624,20 +636,18 @@ int64_t batch_partials_need(const BatchPlan &P, int split) {
   return rr::synth_tc_partial_floats(P.rd, P.kmax, P.n_jobs, split);
 }
 
-cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split) {
+cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split, cudaStream_t st) {
   auto &b = c->batch;
   if (P.variant == RR_SYNTH_FP32)
-    return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb,
-                                       c->stream);
+    return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb, st);
   return rr::launch_synth_tc(P.rd, P.variant == RR_SYNTH_TC_TF32, nullptr, P.kmax, 0, nullptr, nullptr, nullptr, b.ftab,
-                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, c->stream);
+                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, st);
 }
 
-// Enqueues one batch on the context stream: no allocation, no host wait, so
-// the same sequence runs eagerly and under stream capture.
-cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaEvent_t *ev = nullptr) {
+// Enqueues one batch on stream st: no allocation, no host wait, so the same
+// sequence runs eagerly and under stream capture.
+cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEvent_t *ev = nullptr) {
   auto &b = c->batch;
-  cudaStream_t st = c->stream;
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b.ftab, b.h_ftab, sizeof(rr::FrameJob) * P.n_jobs, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
@@ -652,7 +662,7 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaEvent_t *ev = nullp
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
-  if ((e = batch_synth(c, P, P.split)) != cudaSuccess) return e;
+  if ((e = batch_synth(c, P, P.split, st)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
   if (P.rd_out &&
       (e = rr::launch_range_doppler(P.ifb, P.n_jobs * P.rd.n_rx, P.rd.M, P.rd.N, P.window, P.rd_out, st)) != cudaSuccess)
@@ -675,7 +685,7 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
   // builds and tables once, then each traversal tile shape twice (the second run is timed)
   P.tw = 3;
   P.split = 0;
-  e = batch_enqueue(c, P);
+  e = batch_enqueue(c, P, st);
   const int tws[3] = {2, 3, 4};
   for (int k = 0; k < 3 && e == cudaSuccess; ++k) {
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
@@ -700,7 +710,7 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
     if (batch_partials_need(P, splits[k]) > b.partials_cap) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-      if ((e = batch_synth(c, P, splits[k])) != cudaSuccess) break;
+      if ((e = batch_synth(c, P, splits[k], st)) != cudaSuccess) break;
       if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
       float ms = 0.f;
@@ -897,13 +907,17 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaGraphLaunch(b.exec, c->stream), "batch graph launch");
     if (ev) RR_CUDA(c, cudaEventRecord(ev[4], c->stream), "timing");
   } else {
-    RR_CUDA(c, batch_enqueue(c, P, ev), "batch launch");
+    RR_CUDA(c, batch_enqueue(c, P, c->stream, ev), "batch launch");
     if (flags & RR_BATCH_GRAPH) {
+      // capture on a stream of the context's own (the caller's stream may be
+      // the legacy default stream, which cannot be captured); nothing runs
+      // during capture, and the graph is launched on the caller's stream
       if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+      if (!b.cap_stream) RR_CUDA(c, cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking), "capture stream");
       cudaGraph_t graph = nullptr;
-      RR_CUDA(c, cudaStreamBeginCapture(c->stream, cudaStreamCaptureModeThreadLocal), "batch capture");
-      const cudaError_t ee = batch_enqueue(c, P);
-      const cudaError_t ec = cudaStreamEndCapture(c->stream, &graph);
+      RR_CUDA(c, cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal), "batch capture");
+      const cudaError_t ee = batch_enqueue(c, P, b.cap_stream);
+      const cudaError_t ec = cudaStreamEndCapture(b.cap_stream, &graph);
       if (ee != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(c, ee, "batch capture"); }
       RR_CUDA(c, ec, "batch capture");
       const cudaError_t ei = cudaGraphInstantiate(&b.exec, graph, 0);

@@ -370,6 +370,11 @@ __global__ void k_outside_box(const float *__restrict__ x, int64_t n, int cols, 
 
 __global__ void k_accumulate_scalar(float *dst, const float *src, float scale) { *dst += scale * *src; }
 
+__global__ void k_scale(float *__restrict__ dst, const float *__restrict__ src, int64_t n, float s) {
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x)
+    dst[i] = s * src[i];
+}
+
 typedef CUresult (*EncodeTiledFn)(CUtensorMap *, CUtensorMapDataType, cuuint32_t, void *, const cuuint64_t *,
                                   const cuuint64_t *, const cuuint32_t *, const cuuint32_t *, CUtensorMapInterleave,
                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
@@ -463,6 +468,11 @@ cudaError_t adamw(float *p, const float *g, float *m, float *v, int64_t n, float
 
 cudaError_t gather_rows(const float *src, int cols, const int64_t *idx, int64_t count, float *dst, cudaStream_t st) {
   k_gather_rows<<<grid_for(count * cols, 256), 256, 0, st>>>(src, cols, idx, count, dst);
+  return cudaGetLastError();
+}
+
+cudaError_t scale_copy(float *dst, const float *src, int64_t n, float s, cudaStream_t st) {
+  k_scale<<<grid_for(n, 256), 256, 0, st>>>(dst, src, n, s);
   return cudaGetLastError();
 }
 

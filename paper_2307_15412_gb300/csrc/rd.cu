@@ -90,6 +90,23 @@ __global__ void k_rd_cols(float2 *__restrict__ io, int M, int N, int lm, int CW)
   }
 }
 
+// out[f][j][c] = in[f][j][c] conj(in[f][0][c]) / |in[f][0][c]| (c = cell)
+__global__ void k_phase_reference(const float2 *__restrict__ in, int64_t n_frames, int n_rx, int64_t cells,
+                                  float2 *__restrict__ out) {
+  const int64_t total = n_frames * cells;
+  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
+    const int64_t f = i / cells, c = i - f * cells;
+    const float2 r = in[f * n_rx * cells + c];
+    const float mag = hypotf(r.x, r.y);
+    const float ux = mag > 0.f ? r.x / mag : 1.f, uy = mag > 0.f ? -r.y / mag : 0.f;  // conj(r) / |r|
+    for (int j = 0; j < n_rx; ++j) {
+      const int64_t o = (f * n_rx + j) * cells + c;
+      const float2 v = in[o];
+      out[o] = make_float2(v.x * ux - v.y * uy, v.x * uy + v.y * ux);
+    }
+  }
+}
+
 int ilog2(int x) {
   int l = 0;
   while ((1 << l) < x) ++l;
@@ -112,6 +129,17 @@ cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int wi
   const int groups = (N + CW - 1) / CW;
   k_rd_cols<<<n_rx * groups, 256, (size_t)M * CW * sizeof(float2), st>>>(reinterpret_cast<float2 *>(out), M, N,
                                                                          ilog2(M), CW);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_phase_reference(const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out,
+                                   cudaStream_t st) {
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t want = (n_frames * cells + 255) / 256;
+  const int blocks = (int)(want < 1 ? 1 : (want > 8 * sms ? 8 * sms : want));
+  k_phase_reference<<<blocks, 256, 0, st>>>(reinterpret_cast<const float2 *>(in), n_frames, n_rx, cells,
+                                            reinterpret_cast<float2 *>(out));
   return cudaGetLastError();
 }
 

@@ -195,8 +195,13 @@ cudaError_t adamw(float *p, const float *g, float *m, float *v, int64_t n, float
                   float wd, int step, const uint8_t *decay_mask, cudaStream_t st);
 cudaError_t gather_rows(const float *src, int cols, const int64_t *idx, int64_t count, float *dst, cudaStream_t st);
 cudaError_t outside_box(const float *x, int64_t n, int cols, uint8_t *out, cudaStream_t st);
+// dst[i] = s src[i] (may alias)
+cudaError_t scale_copy(float *dst, const float *src, int64_t n, float s, cudaStream_t st);
 // *dst += scale * *src (one thread)
 cudaError_t accumulate_scalar(float *dst, const float *src, float scale, cudaStream_t st);
+// out[f][j][c] = in[f][j][c] conj(in[f][0][c]) / |in[f][0][c]| (complex; may alias)
+cudaError_t launch_phase_reference(const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out,
+                                   cudaStream_t st);
 cudaError_t launch_range_doppler(const float *in, int n_rx, int M, int N, int window, float *out,
                                  cudaStream_t st);
 

@@ -36,6 +36,7 @@ struct Surrogate {
   uint8_t *decay = nullptr;
   __nv_bfloat16 *w16[kMaxLayers] = {}, *w16t[kMaxLayers] = {};
   int step = 0;
+  float out_scale = 1.f;           // targets and outputs are in units of out_scale
   // activations for up to bcap samples
   int64_t bcap = 0;
   __nv_bfloat16 *x16 = nullptr, *x16t = nullptr;
@@ -246,6 +247,16 @@ rr_status rr_surrogate_create(rr_ctx *c, const int32_t *dims, int n_dims) {
   return RR_OK;
 }
 
+rr_status rr_surrogate_set_scale(rr_ctx *c, float scale) {
+  if (!c) return RR_EINVAL;
+  Surrogate *s;
+  rr_status st;
+  if ((st = rr::get_sur(c, &s)) != RR_OK) return st;
+  if (!(scale > 0.f) || !(scale < 3.0e38f)) return rr_ctx_fail(c, RR_EINVAL, "scale must be positive and finite");
+  s->out_scale = scale;
+  return RR_OK;
+}
+
 int64_t rr_surrogate_num_params(rr_ctx *c) {
   if (!c || !rr_ctx_surrogate(c)) return 0;
   return rr_ctx_surrogate(c)->n_params;
@@ -293,7 +304,7 @@ rr_status rr_surrogate_forward(rr_ctx *c, const float *x, int64_t B, float *y) {
   cudaStream_t cs = rr_ctx_stream(c);
   SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
   SUR_CUDA(c, rr::forward(s, x, B, false, rr_ctx_err(c), cs), "surrogate forward");
-  SUR_CUDA(c, cudaMemcpyAsync(y, s->y, sizeof(float) * B * s->dims[s->L], cudaMemcpyDeviceToDevice, cs), "forward");
+  SUR_CUDA(c, rr::scale_copy(y, s->y, B * s->dims[s->L], s->out_scale, cs), "forward");
   return RR_OK;
 }
 
@@ -308,8 +319,9 @@ rr_status rr_surrogate_gradients(rr_ctx *c, const float *x, const float *t, int6
   cudaStream_t cs = rr_ctx_stream(c);
   SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
   SUR_CUDA(c, cudaMemsetAsync(s->loss, 0, sizeof(float), cs), "gradients");
+  SUR_CUDA(c, rr::scale_copy(s->tb, t, B * s->dims[s->L], 1.f / s->out_scale, cs), "gradients");
   SUR_CUDA(c, rr::forward(s, x, B, true, rr_ctx_err(c), cs), "surrogate forward");
-  SUR_CUDA(c, rr::backward(s, t, B, rr_ctx_err(c), cs), "surrogate backward");
+  SUR_CUDA(c, rr::backward(s, s->tb, B, rr_ctx_err(c), cs), "surrogate backward");
   if (grads)
     SUR_CUDA(c, cudaMemcpyAsync(grads, s->g, sizeof(float) * s->n_params, cudaMemcpyDeviceToDevice, cs), "gradients");
   if (loss) SUR_CUDA(c, cudaMemcpyAsync(loss, s->loss, sizeof(float), cudaMemcpyDeviceToDevice, cs), "gradients");
@@ -376,6 +388,8 @@ rr_status rr_surrogate_train(rr_ctx *c, const rr_train_cfg *cfg, const float *x,
     for (int64_t k = 0; k < steps && e == cudaSuccess; ++k) {
       e = rr::gather_rows(x, s->dims[0], s->idx + k * B, B, s->xb, cs);
       if (e == cudaSuccess) e = rr::gather_rows(t, s->dims[s->L], s->idx + k * B, B, s->tb, cs);
+      if (e == cudaSuccess && s->out_scale != 1.f)
+        e = rr::scale_copy(s->tb, s->tb, B * s->dims[s->L], 1.f / s->out_scale, cs);
       if (e == cudaSuccess) e = cudaMemsetAsync(s->loss, 0, sizeof(float), cs);
       if (e == cudaSuccess) e = rr::forward(s, s->xb, B, true, rr_ctx_err(c), cs);
       if (e == cudaSuccess) e = rr::backward(s, s->tb, B, rr_ctx_err(c), cs);
@@ -418,8 +432,7 @@ rr_status rr_surrogate_infer(rr_ctx *c, const float *x, int64_t n, float *y_out,
       xin = s->xb;
     }
     SUR_CUDA(c, rr::forward(s, xin, padded, false, rr_ctx_err(c), cs), "surrogate forward");
-    SUR_CUDA(c, cudaMemcpyAsync(y_out + r0 * dout, s->y, sizeof(float) * rows * dout, cudaMemcpyDeviceToDevice, cs),
-             "infer");
+    SUR_CUDA(c, rr::scale_copy(y_out + r0 * dout, s->y, rows * dout, s->out_scale, cs), "infer");
   }
   if (fell_back) SUR_CUDA(c, rr::outside_box(x, n, din, fell_back, cs), "infer");
   return RR_OK;

@@ -502,3 +502,17 @@ def surrogate_scenes(raw: np.ndarray, n_tri_target: int = SURROGATE_TRIANGLES):
     vel[:, 0] += raw[:, N_ANGLES + 4]
     V, F = hand_meshes(n_tri_target, raw[:, :N_ANGLES], center)
     return V, F, vel.astype(np.float32)
+
+
+def surrogate_init_params(dims, seed: int) -> np.ndarray:
+    """Seeded starting parameters of the surrogate network, packed FP32
+    [W_1, b_1, W_2, b_2, ...] with W_l [out][in]: He-uniform weights
+    (bound sqrt(6 / in)), zero biases."""
+    rng = np.random.default_rng(seed)
+    parts = []
+    for i in range(len(dims) - 1):
+        n_in, n_out = int(dims[i]), int(dims[i + 1])
+        bound = math.sqrt(6.0 / n_in)
+        parts.append(rng.uniform(-bound, bound, size=n_out * n_in))
+        parts.append(np.zeros(n_out))
+    return np.concatenate(parts).astype(np.float32)

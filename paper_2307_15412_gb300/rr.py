@@ -83,6 +83,7 @@ SIGNATURES = {
     "rr_batch_run": (_I, [_P, ctypes.POINTER(rr_job), _I, ctypes.POINTER(rr_radar), _I, _I, _P, _P, _I]),
     "rr_surrogate_create": (_I, [_P, _P, _I]),
     "rr_surrogate_num_params": (_I64, [_P]),
+    "rr_surrogate_set_scale": (_I, [_P, ctypes.c_float]),
     "rr_surrogate_set_params": (_I, [_P, _P, _I]),
     "rr_surrogate_get_params": (_I, [_P, _P]),
     "rr_surrogate_forward": (_I, [_P, _P, _I64, _P]),
@@ -90,6 +91,7 @@ SIGNATURES = {
     "rr_surrogate_train_step": (_I, [_P, _P, _P, _I64, ctypes.POINTER(rr_adamw), _P]),
     "rr_surrogate_train": (_I, [_P, ctypes.POINTER(rr_train_cfg), _P, _P, _I64]),
     "rr_surrogate_infer": (_I, [_P, _P, _I64, _P, _P]),
+    "rr_phase_reference": (_I, [_P, _P, _I64, _I, _I64, _P]),
     "rr_timing_enable": (_I, [_P, _I]),
     "rr_timing_read": (_I, [_P, _I, ctypes.POINTER(ctypes.c_float)]),
 }
@@ -156,9 +158,21 @@ def _ptr(x) -> Optional[int]:
     return int(x)
 
 
+CUDA_STREAM_LEGACY = 1  # cudaStreamLegacy: the legacy default stream
+
+
+def _raw_stream(stream) -> int:
+    """cudaStream_t of a torch stream or int; torch's default stream (handle
+    0) is passed as cudaStreamLegacy, because NULL asks the library for a
+    stream of its own, which would not be ordered with torch's work."""
+    raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+    return CUDA_STREAM_LEGACY if raw == 0 else raw
+
+
 class Context:
     """Owns one rr_ctx.  stream: a torch.cuda.Stream, a raw cudaStream_t
-    (int), or None for torch's current stream on `device` at creation."""
+    (int), or None for torch's current stream on `device` at creation; the
+    library's work is then ordered with torch's work on that stream."""
 
     def __init__(self, device: int = 0, stream=None):
         import torch
@@ -166,7 +180,7 @@ class Context:
         self.device = device
         if stream is None:
             stream = torch.cuda.current_stream(device)
-        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else int(stream)
+        raw = _raw_stream(stream)
         h = _P()
         st = self.lib.rr_create(ctypes.byref(h), device, raw)
         if st != RR_OK:
@@ -190,7 +204,7 @@ class Context:
             raise RRError(st, self.lib.rr_last_error(self.h).decode())
 
     def set_stream(self, stream):
-        raw = stream.cuda_stream if hasattr(stream, "cuda_stream") else (0 if stream is None else int(stream))
+        raw = None if stream is None else _raw_stream(stream)
         self._check(self.lib.rr_set_stream(self.h, raw))
 
     def sync(self):
@@ -281,6 +295,9 @@ class Context:
         arr = (ctypes.c_int32 * len(dims))(*[int(d) for d in dims])
         self._check(self.lib.rr_surrogate_create(self.h, arr, len(dims)))
 
+    def surrogate_set_scale(self, scale: float):
+        self._check(self.lib.rr_surrogate_set_scale(self.h, float(scale)))
+
     def surrogate_num_params(self) -> int:
         return int(self.lib.rr_surrogate_num_params(self.h))
 
@@ -316,6 +333,12 @@ class Context:
 
     def surrogate_infer(self, x, y, fell_back=None):
         self._check(self.lib.rr_surrogate_infer(self.h, _ptr(x), int(x.shape[0]), _ptr(y), _ptr(fell_back)))
+
+    def phase_reference(self, cube_in, cube_out):
+        """cube_in/out: CUDA float32 [frames, n_rx, ..., 2] (out may be in)."""
+        n, n_rx = int(cube_in.shape[0]), int(cube_in.shape[1])
+        cells = int(cube_in[0, 0].numel() // 2)
+        self._check(self.lib.rr_phase_reference(self.h, _ptr(cube_in), n, n_rx, cells, _ptr(cube_out)))
 
     def timing_enable(self, n_slots: int):
         self._check(self.lib.rr_timing_enable(self.h, int(n_slots)))

@@ -1,0 +1,117 @@
+"""Learned surrogate of the radar frame, with the ray tracer as its data
+source, fallback and judge.
+
+  frames(raw)      range-Doppler cubes of parameter vectors from the tracer
+                   (rr_batch_run over batches of seeded hand scenes)
+  Surrogate.fit    trains the BF16 MLP (rr_surrogate_train) on such frames
+  Surrogate.infer  network prediction (rr_surrogate_infer) for every row;
+                   rows outside the training box are traced instead
+
+Everything numerical runs in the C library's kernels; this module only
+generates the seeded input meshes (inputs.py), moves tensors and calls the
+C ABI.  Cubes are [n][3 RX][32 Doppler][32 range][re, im] float32, flattened
+to 6144 values per frame, phase-referenced to RX 0 per cell: the common
+phase of a cell turns over every lambda / 2 = 2.4 mm of path and is no
+smooth function of the pose, while the magnitudes and the phase
+differences between antennas are.
+"""
+from __future__ import annotations
+
+from typing import Optional, Tuple
+
+import numpy as np
+
+from . import inputs as I
+from . import rr
+
+ARCH = (32, 1024, 1024, 1024, 6144)
+
+
+def frames(ctx: "rr.Context", raw: np.ndarray, slot0: int = 1024, chunk: int = 256, graph: bool = False,
+           referenced: bool = True):
+    """Tracer range-Doppler cubes (torch CUDA float32 [n][6144]) of the
+    parameter vectors raw [n][32] (degrees, metres, m/s): each chunk of
+    frames goes through one rr_batch_run in scene slots slot0 ...  With
+    `referenced` the cubes are phase-referenced to RX 0 (rr_phase_reference),
+    the representation the surrogate learns."""
+    import torch
+    radar, grid = I.surrogate_radar_grid()
+    raw = np.atleast_2d(np.asarray(raw, np.float64))
+    n = raw.shape[0]
+    out = torch.empty((n, radar.n_rx * radar.n_chirps * radar.n_samples * 2), dtype=torch.float32,
+                      device="cuda:%d" % ctx.device)
+    rd = torch.empty((chunk, radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32,
+                     device="cuda:%d" % ctx.device)
+    rs, gs = rr.make_radar(radar), rr.make_grid(grid)
+    for c0 in range(0, n, chunk):
+        c1 = min(n, c0 + chunk)
+        V, F, vel = I.surrogate_scenes(raw[c0:c1])
+        for k in range(c1 - c0):
+            ctx.scene_upload(slot0 + k, V[k], F, vel[k])
+        jobs = [(slot0 + k, gs) for k in range(c1 - c0)]
+        ctx.batch_run(jobs, rs, rd_out=rd[:c1 - c0], graph=graph)
+        if referenced:
+            ctx.phase_reference(rd[:c1 - c0], rd[:c1 - c0])
+        out[c0:c1].copy_(rd[:c1 - c0].reshape(c1 - c0, -1))
+    ctx.sync()
+    return out
+
+
+def rel_l2_rows(got, ref) -> Tuple[np.ndarray, np.ndarray]:
+    """Per-frame relative L2 error of the complex cube and of its magnitude."""
+    g = got.double().reshape(got.shape[0], -1, 2)
+    r = ref.double().reshape(ref.shape[0], -1, 2)
+    gc = g[..., 0] + 1j * g[..., 1]
+    rc = r[..., 0] + 1j * r[..., 1]
+    num = (gc - rc).abs().norm(dim=1)
+    den = rc.abs().norm(dim=1).clamp_min(1e-30)
+    mag = (gc.abs() - rc.abs()).norm(dim=1) / den
+    return (num / den).cpu().numpy(), mag.cpu().numpy()
+
+
+class Surrogate:
+    """The context's BF16 MLP plus the target scale it was trained with."""
+
+    def __init__(self, ctx: "rr.Context", dims=ARCH, seed: int = 0):
+        self.ctx = ctx
+        self.dims = tuple(int(d) for d in dims)
+        ctx.surrogate_create(self.dims)
+        ctx.surrogate_set_params(I.surrogate_init_params(self.dims, seed))
+        self.scale = 1.0
+
+    def fit(self, raw: np.ndarray, targets, epochs: int = 20, batch: int = 512, seed: int = 0, lr: float = 1e-3,
+            weight_decay: float = 1e-4):
+        """Trains on parameter vectors raw [n][32] and tracer cubes
+        targets [n][6144] (device); targets are scaled by their RMS.
+        Returns the mean training loss of every epoch."""
+        import torch
+        x = torch.from_numpy(I.surrogate_features(raw)).to(targets.device)
+        # unit of the data: RMS of a seeded sample of the targets
+        rows = np.random.default_rng(seed).choice(targets.shape[0], min(256, targets.shape[0]), replace=False)
+        sample = targets[torch.from_numpy(rows).to(targets.device)].cpu().numpy().astype(np.float64)
+        self.scale = float(np.sqrt(np.mean(sample * sample))) or 1.0
+        self.ctx.surrogate_set_scale(self.scale)
+        return self.ctx.surrogate_train(x, targets.contiguous(), epochs=epochs, batch=batch, seed=seed, lr=lr,
+                                        weight_decay=weight_decay)
+
+    def predict(self, raw: np.ndarray):
+        """Network output for every row (no fallback): (cubes [n][6144],
+        outside-the-box flags [n] uint8), both torch CUDA tensors."""
+        import torch
+        dev = "cuda:%d" % self.ctx.device
+        x = torch.from_numpy(I.surrogate_features(np.atleast_2d(raw))).to(dev)
+        n = x.shape[0]
+        y = torch.empty((n, self.dims[-1]), dtype=torch.float32, device=dev)
+        fb = torch.empty(n, dtype=torch.uint8, device=dev)
+        self.ctx.surrogate_infer(x, y, fb)
+        return y, fb
+
+    def infer(self, raw: np.ndarray, slot0: int = 1024):
+        """Prediction with the tracer as fallback: rows whose parameters lie
+        outside the training box are traced.  Returns (cubes, flags)."""
+        y, fb = self.predict(raw)
+        self.ctx.sync()
+        rows = np.nonzero(fb.cpu().numpy())[0]
+        if rows.size:
+            y[rows] = frames(self.ctx, np.atleast_2d(raw)[rows], slot0=slot0)
+        return y, fb
