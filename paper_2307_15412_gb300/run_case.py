@@ -2,12 +2,15 @@
 
   python -m paper_2307_15412_gb300.run_case [--workload full|tiny] [--steps N]
          [--scenes S] [--batch] [--variant 0|1|2] [--no-flush]
+  python -m paper_2307_15412_gb300.run_case --mlp [--steps N] [--mlp-batch B]
 
 Each step runs every one of the S resident seeded scenes: one rr_run_frame
 per scene, or with --batch one rr_batch_run over all of them.  --variant
 selects the synthesis (0 FP32, 1 tensor-core BF16x3, 2 tensor-core TF32).
 L2 is flushed (256 MiB write) before each step unless --no-flush, as in the
-benchmark.
+benchmark.  --mlp instead runs the learned surrogate (32-1024-1024-1024-6144,
+seeded parameters): per step one training step and one inference on a
+batch of B seeded inputs.
 """
 from __future__ import annotations
 
@@ -24,6 +27,8 @@ def main():
     ap.add_argument("--batch", action="store_true")
     ap.add_argument("--variant", type=int, default=0, choices=[0, 1, 2])
     ap.add_argument("--no-flush", action="store_true")
+    ap.add_argument("--mlp", action="store_true")
+    ap.add_argument("--mlp-batch", type=int, default=4096)
     args = ap.parse_args()
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     sys.path.insert(0, root)
@@ -32,6 +37,8 @@ def main():
     from paper_2307_15412_gb300 import inputs as I
     from paper_2307_15412_gb300 import rr
 
+    if args.mlp:
+        return run_mlp(args, torch, I, rr)
     if args.workload == "full":
         radar, grid, nt = I.workload_full_frame()
         scenes = [I.hand_scene(k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
@@ -58,6 +65,24 @@ def main():
     torch.cuda.synchronize()
     ctx.close()
     print("ran %d steps of %d scenes" % (args.steps, S))
+
+
+def run_mlp(args, torch, I, rr):
+    dims = (32, 1024, 1024, 1024, 6144)
+    ctx = rr.Context(0)
+    ctx.surrogate_create(dims)
+    ctx.surrogate_set_params(I.surrogate_init_params(dims, 0))
+    B = args.mlp_batch
+    x = torch.from_numpy(I.surrogate_features(I.surrogate_inputs(0, B))).cuda()
+    t = torch.randn((B, dims[-1]), generator=torch.Generator().manual_seed(0)).cuda()
+    y = torch.empty((B, dims[-1]), dtype=torch.float32, device="cuda:0")
+    for i in range(args.steps):
+        ctx.surrogate_train_step(x, t, lr=1e-4)
+        ctx.surrogate_forward(x, y)
+    ctx.sync()
+    torch.cuda.synchronize()
+    ctx.close()
+    print("ran %d surrogate steps at batch %d" % (args.steps, B))
 
 
 if __name__ == "__main__":
