@@ -2,12 +2,11 @@
 //
 // gemm_tn: C[M][N] = A[M][K] B[N][K]^T (both operands K-major, BF16) on the
 // 5th-generation tensor cores.  One CTA computes a 128 x 128 tile:
-//   warp 0  loads operand tiles with TMA (cp.async.bulk.tensor, no swizzle,
-//           boxes of 8 K-elements x 128 rows, so that each box is one column
-//           of 8 x 16-byte core matrices of the canonical K-major layout:
-//           SBO = 128 B between 8-row groups, LBO = 2048 B between
-//           K-neighbouring core matrices) into a 4-stage ring, completing
-//           each stage's `full` mbarrier by transaction bytes;
+//   warp 0  loads operand tiles with TMA (cp.async.bulk.tensor, one box of
+//           64 K-elements x 128 rows per operand and stage, 128-byte swizzle,
+//           which is the canonical K-major SWIZZLE_128B layout of the MMA:
+//           1024-byte atoms of 8 rows, SBO = 1024 B) into a 4-stage ring,
+//           completing each stage's `full` mbarrier by transaction bytes;
 //   warp 1  allocates 128 tensor-memory columns and issues
 //           tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = N = 128, K = 16)
 //           per stage, committing to the stage's `empty` mbarrier;
@@ -69,9 +68,14 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   return true;
 }
 
-__device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
-  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)((lbo >> 4) & 0x3FFFu) << 16) |
-         ((uint64_t)((sbo >> 4) & 0x3FFFu) << 32) | (1ull << 46);
+// Shared-memory matrix descriptor of a K-major operand tile in the 128-byte
+// swizzled canonical layout (what TMA writes with SWIZZLE_128B): rows of
+// 128 bytes, 8-row atoms of 1024 bytes stacked along M/N (SBO = 1024), the
+// leading byte offset unused; a K-step inside the atom advances the start
+// address by its byte offset and the hardware applies the same XOR swizzle.
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
 }
 
 // kind::f16 instruction descriptor: D F32, A and B BF16, K-major, N = 128, M = 128
@@ -142,11 +146,8 @@ k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
                      : "memory");
         const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
         const int k0 = kt * kBK;
-#pragma unroll
-        for (int c = 0; c < kBK / 8; ++c) {
-          tma_box(a + c * 2048, &mapA, k0 + 8 * c, m0, bar);
-          tma_box(b + c * 2048, &mapB, k0 + 8 * c, n0, bar);
-        }
+        tma_box(a, &mapA, k0, m0, bar);
+        tma_box(b, &mapB, k0, n0, bar);
       }
     }
     __syncwarp();
@@ -164,7 +165,7 @@ k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
         const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
 #pragma unroll
         for (int ks = 0; ks < kBK / 16; ++ks) {
-          const uint64_t da = smem_desc(a + ks * 4096, 2048, 128), db = smem_desc(b + ks * 4096, 2048, 128);
+          const uint64_t da = smem_desc_sw128(a + ks * 32), db = smem_desc_sw128(b + ks * 32);
           const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
           asm volatile(
               "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
@@ -267,28 +268,43 @@ k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
 // MSE of y against t over B x O entries: loss_acc += sum (y - t)^2 (FP32
 // block partials, one atomic per block); dy = 2 (y - t) / (B O) as BF16,
-// row-major and transposed.
+// row-major and transposed (32 x 32 tiles through shared memory, so both
+// stores are coalesced).
 __global__ void k_mse_grad(const float *__restrict__ y, const float *__restrict__ t, int64_t B, int O,
                            __nv_bfloat16 *__restrict__ dy, __nv_bfloat16 *__restrict__ dyt, float *loss_acc) {
-  __shared__ float s_part[32];
-  const int64_t total = B * O;
-  const float scale = 2.f / (float)total;
+  __shared__ float tile[32][33];
+  __shared__ float s_part[8];
+  const int64_t b0 = (int64_t)blockIdx.y * 32;
+  const int o0 = blockIdx.x * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;  // 32 x 8 threads
+  const float scale = 2.f / ((float)B * (float)O);
   float part = 0.f;
-  for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < total; i += (int64_t)gridDim.x * blockDim.x) {
-    const float e = y[i] - t[i];
-    part += e * e;
-    const __nv_bfloat16 gv = __float2bfloat16_rn(scale * e);
-    dy[i] = gv;
-    const int64_t b = i / O, o = i - b * O;
-    dyt[o * B + b] = gv;
+  for (int k = ty; k < 32; k += 8) {
+    const int64_t b = b0 + k;
+    const int o = o0 + tx;
+    float gv = 0.f;
+    if (b < B && o < O) {
+      const int64_t i = b * O + o;
+      const float e = y[i] - t[i];
+      part += e * e;
+      gv = scale * e;
+      dy[i] = __float2bfloat16_rn(gv);
+    }
+    tile[k][tx] = gv;
+  }
+  __syncthreads();
+  for (int k = ty; k < 32; k += 8) {
+    const int o = o0 + k;
+    const int64_t b = b0 + tx;
+    if (b < B && o < O) dyt[(int64_t)o * B + b] = __float2bfloat16_rn(tile[tx][k]);
   }
   for (int o = 16; o > 0; o >>= 1) part += __shfl_xor_sync(0xffffffffu, part, o);
-  if ((threadIdx.x & 31) == 0) s_part[threadIdx.x >> 5] = part;
+  if (tx == 0) s_part[ty] = part;
   __syncthreads();
-  if (threadIdx.x < 32) {
-    float v = threadIdx.x < (blockDim.x >> 5) ? s_part[threadIdx.x] : 0.f;
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    if (threadIdx.x == 0 && loss_acc) atomicAdd(loss_acc, v);
+  if (threadIdx.x == 0 && loss_acc) {
+    float v = 0.f;
+    for (int w = 0; w < 8; ++w) v += s_part[w];
+    atomicAdd(loss_acc, v);
   }
 }
 
@@ -392,17 +408,17 @@ EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of a row-major BF16 matrix [rows][cols] (cols = K, contiguous):
-// boxes of 8 columns x 128 rows, no swizzle, zero fill outside.
+// boxes of 64 columns x 128 rows, 128-byte swizzle, zero fill outside.
 cudaError_t make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((cols & 7) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {8, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
-                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+                        CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   return r == CUDA_SUCCESS ? cudaSuccess : cudaErrorInvalidValue;
 }
@@ -442,7 +458,8 @@ cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N
 
 cudaError_t mse_grad(const float *y, const float *t, int64_t B, int O, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
                      float *loss_acc, cudaStream_t st) {
-  k_mse_grad<<<grid_for(B * O, 256), 256, 0, st>>>(y, t, B, O, dy, dyt, loss_acc);
+  dim3 grid((O + 31) / 32, (unsigned)((B + 31) / 32));
+  k_mse_grad<<<grid, 256, 0, st>>>(y, t, B, O, dy, dyt, loss_acc);
   return cudaGetLastError();
 }
 
