@@ -35,6 +35,8 @@ struct rr_ctx {
   // synthesis scratch
   float *partials = nullptr;
   int64_t partials_cap = 0;        // floats
+  float4 *tc_cst = nullptr;        // per-hit constants of the tensor-core synthesis
+  int64_t tc_cst_cap = 0;
   float *if_tmp = nullptr;         // internal IF cube for rr_run_frame(if_out = NULL)
   int64_t if_tmp_cap = 0;          // floats
   // batches (rr_batch_run): hit-list segments, tables and scratch
@@ -55,6 +57,7 @@ struct rr_ctx {
     int64_t partials_cap = 0;
     float *if_tmp = nullptr;
     int64_t if_tmp_cap = 0;
+    float4 *tc_cst = nullptr;               // per-hit constants, laid out like d (RR_MAX_RX rows of cap)
     // CUDA graph of the last batch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
@@ -207,8 +210,9 @@ rr_status run_synth(rr_ctx *c, const rr_radar *r, rr_synth_variant v, const uint
   }
   const int64_t need = rr::synth_tc_partial_floats(rd, kmax, 1, 0);
   RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
+  RR_CUDA(c, grow(c->tc_cst, c->tc_cst_cap, (int64_t)r->n_rx * (ld > 0 ? ld : 1)), "synth constants");
   RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, 0, c->partials,
-                                 c->partials_cap, out, c->d_err, c->stream),
+                                 c->partials_cap, out, c->d_err, c->tc_cst, d, c->stream),
           "synth_if launch (tensor cores)");
   return RR_OK;
 }
@@ -260,11 +264,12 @@ rr_status rr_destroy(rr_ctx *c) {
   if (c->h_roots) cudaFreeHost(c->h_roots);
   if (c->partials) cudaFree(c->partials);
   if (c->if_tmp) cudaFree(c->if_tmp);
+  if (c->tc_cst) cudaFree(c->tc_cst);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   {
     auto &b = c->batch;
     void *dev[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd, b.counts, b.ftab, b.btab, b.jt, b.prefix,
-                   b.partials, b.if_tmp};
+                   b.partials, b.if_tmp, b.tc_cst};
     for (void *p : dev)
       if (p) cudaFree(p);
     if (b.h_ftab) cudaFreeHost(b.h_ftab);
@@ -641,7 +646,7 @@ cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split, cudaStream_t s
   if (P.variant == RR_SYNTH_FP32)
     return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb, st);
   return rr::launch_synth_tc(P.rd, P.variant == RR_SYNTH_TC_TF32, nullptr, P.kmax, 0, nullptr, nullptr, nullptr, b.ftab,
-                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, st);
+                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, b.tc_cst, b.d, st);
 }
 
 // Enqueues one batch on stream st: no allocation, no host wait, so the same
@@ -774,11 +779,12 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
 
   // buffers (grown before anything is enqueued or captured)
   if (total > b.cap || !b.ray) {
-    void *old[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd};
+    void *old[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd, b.tc_cst};
     for (void *p : old)
       if (p) cudaFree(p);
     b.ray = b.tri = b.pos = nullptr;
     b.t = b.d = b.a = b.dd = nullptr;
+    b.tc_cst = nullptr;
     b.cap = 0;
     RR_CUDA(c, cudaMalloc((void **)&b.ray, sizeof(int32_t) * total), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.tri, sizeof(int32_t) * total), "batch hit list");
@@ -787,6 +793,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaMalloc((void **)&b.d, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.a, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.dd, sizeof(float) * total * RR_MAX_RX), "batch hit list");
+    RR_CUDA(c, cudaMalloc((void **)&b.tc_cst, sizeof(float4) * total * RR_MAX_RX), "batch hit list");
     b.cap = total;
     if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
   }

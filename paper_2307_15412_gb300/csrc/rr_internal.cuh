@@ -175,10 +175,13 @@ cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int
 // frames; tf32 selects kind::tf32, else split-BF16x3.
 bool synth_tc_supported(const RadarDev &r);
 int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+// cst: float4 scratch laid out like the hit arrays (at least n_rx * ld
+// entries past d_base: d_base = d for one frame, the base of the batch hit
+// arrays for a batch) for the per-hit constants.
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
                             int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
-                            cudaStream_t st);
+                            float4 *cst, const float *d_base, cudaStream_t st);
 // Learned-surrogate kernels (see mlp.cu).  gemm_tn: C = A B^T with A
 // [M][K], B [N][K] BF16 row-major (K a multiple of 8, 16-byte aligned),
 // + bias[N], act 1 = ReLU, mask [M][N] BF16 (zero where mask <= 0); outputs

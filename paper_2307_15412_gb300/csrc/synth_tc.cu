@@ -83,6 +83,10 @@ struct SynthTcParams {
   float *partials;        // [jobs][S][n_rx][M][N] complex
   const FrameJob *jobs;
   uint32_t *err;
+  // per-hit constants (c0, c1, b0, b1) laid out like the hit arrays: entry
+  // (hit_d pointer - d_base) + j * ld + k for hit k of channel j
+  float4 *cst;
+  const float *d_base;
 };
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -187,16 +191,27 @@ __device__ __forceinline__ void put2(unsigned char *hi_base, unsigned char *lo_b
 }
 
 // Byte offset of (row or column x, block-local hit k) in an operand region
-// of 4 KB per MMA k-step (128 rows x 32 bytes).  BF16: 8 hits per k-step,
-// core K-index (k % 8) / 4, 4 bytes per hit in a core row; TF32: 4 hits
-// per k-step, core K-index (k % 4) / 2, 8 bytes per hit.
+// in the 128-byte swizzled K-major layout: 128-byte rows (x), the 16-byte
+// chunk c of row x stored at chunk c ^ (x % 8).  BF16: one 128-byte atom
+// holds the 2 entries of all 32 hits (4 hits per chunk); TF32: two atoms of
+// 16 KB, 16 hits each (2 hits per chunk).
 template <bool TF32>
 __device__ __forceinline__ uint32_t op_off(int x, int k) {
-  if (TF32)
-    return (uint32_t)(k >> 2) * 4096u + (uint32_t)(x >> 3) * 256u + (uint32_t)((k >> 1) & 1) * 128u +
-           (uint32_t)(x & 7) * 16u + (uint32_t)(k & 1) * 8u;
-  return (uint32_t)(k >> 3) * 4096u + (uint32_t)(x >> 3) * 256u + (uint32_t)((k >> 2) & 1) * 128u +
-         (uint32_t)(x & 7) * 16u + (uint32_t)(k & 3) * 4u;
+  if (TF32) {
+    const int kk = k & 15;
+    return (uint32_t)(k >> 4) * 16384u + (uint32_t)x * 128u + (uint32_t)(((kk >> 1) ^ (x & 7)) << 4) +
+           (uint32_t)(kk & 1) * 8u;
+  }
+  return (uint32_t)x * 128u + (uint32_t)(((k >> 2) ^ (x & 7)) << 4) + (uint32_t)(k & 3) * 4u;
+}
+
+// Shared-memory matrix descriptor of a K-major operand in the 128-byte
+// swizzled canonical layout (1024-byte atoms of 8 rows, SBO = 1024 B, LBO
+// unused); a K-step inside an atom advances the start address by its byte
+// offset (the atom base must be 1024-byte aligned).
+__device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
+  return (uint64_t)((addr >> 4) & 0x3FFFu) | ((uint64_t)1 << 16) | ((uint64_t)(1024 >> 4) << 32) | (1ull << 46) |
+         (2ull << 61);
 }
 
 // Warp roles: warps 0..15 produce operands (and warps 0..3 run the
@@ -308,19 +323,17 @@ k_synth_tc(const SynthTcParams p) {
     for (int q = 0; q < 2 * kLO; ++q) fold[my_row * kFoldStride + q] = 0.f;
 
   if (warp < 16) {
-    // ---- producers: warp w owns hits 4 (w % 8) + g of every block (g =
-    // lane / 8), the A units 8 (w / 8) + c8 and the B offsets l = 8 (w / 8) + c8
-    // (c8 = lane % 8); a store of the warp covers 4 hits x 8 rows or columns,
-    // the rows staggered so that it fills one 128-byte bank window
-    const int g = lane >> 3, c8 = lane & 7;
-    const int kh = 4 * (warp & 7) + g;
-    const int uo = warp >> 3;
+    // ---- producers: lane = block-local hit; warp w writes the A rows
+    // 8 w .. 8 w + 7 (unit w: chirp w / nseg, segment w % nseg) and the eight
+    // B columns of fast-time offset l = w (4 terms x Re / Im).  In the
+    // 128-byte swizzled layout one warp store covers a whole 128-byte row
+    // (32 hits), so the stores are free of bank conflicts.
     const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
     const int nseg = HE / 8;                         // 8-row units per chirp (16 per tile)
-    const int u = 8 * uo + c8;
-    const int mi = u / nseg, seg = u - mi * nseg;
+    const int mi = warp / nseg, seg = warp - mi * nseg;
     const int hbase = 8 * seg;
-    const int l = 8 * uo + c8;
+    const int l = warp;
+    const float4 *cj = p.cst + (dj - p.d_base);      // this channel's constants
     for (int b = 0; b < nb; ++b) {
       if (s_abort) break;
       if (warp < 4 && b > 0 && b % kMaxChain == 0) {
@@ -343,56 +356,32 @@ k_synth_tc(const SynthTcParams p) {
         s_abort = 1;
         break;
       }
-      // hit constants: lanes 0..3 load and reduce the warp's 4 hits, then broadcast
-      const int64_t kb0 = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + 4 * (warp & 7);
-      float c0 = 0.f, c1 = 0.f, b0 = 0.f, b1 = 0.f, a = 0.f;
-      if (lane < 4 && kb0 + lane < K) {
-        const int64_t k = kb0 + lane;
-        const float d = dj[k], dd = ddj[k];
-        const double x = p.f0_c * (double)d;  // FP64 carrier reduction
-        c0 = (float)(x - floor(x));
-        c1 = p.c1k * dd;
-        b0 = (float)(p.kb * (double)d);
-        b1 = p.b1k * dd;
+      const int64_t k = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + lane;
+      float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
+      float a = 0.f;
+      if (k < K) {
+        cv = cj[k];
         a = aj[k];
-        const float xm = 6.2831853f * fabsf(b1) * mu_max * (float)(kLO - 1);
-        if (xm > 0.157f && uo == 0) atomicOr(p.err, ERR_TC_BOUND);
       }
-      c0 = __shfl_sync(0xffffffffu, c0, g);
-      c1 = __shfl_sync(0xffffffffu, c1, g);
-      b0 = __shfl_sync(0xffffffffu, b0, g);
-      b1 = __shfl_sync(0xffffffffu, b1, g);
-      a = __shfl_sync(0xffffffffu, a, g);
-      // A: unit (chirp mi, segment seg) = 8 rows of this hit
+      const float c0 = cv.x, c1 = cv.y, b0 = cv.z, b1 = cv.w;
+      // A: rows (chirp mi, h = hbase .. hbase + 7) of this hit
       {
-        float2 P = make_float2(0.f, 0.f), P0 = P, W = make_float2(1.f, 0.f);
+        float2 P = make_float2(0.f, 0.f), W = make_float2(1.f, 0.f);
         if (mi < mvalid) {
           const float fm = (float)(m0 + mi);
           const float beta = fmaf(fm, b1, b0);
           const float cyc = fmaf(fm, c1, c0);
           W = expm2pi(beta * (float)kLO);
-          P = expm2pi(fmaf(beta * (float)kLO, (float)(hbase + c8), cyc));
-          P0 = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
-          P.x *= a; P.y *= a; P0.x *= a; P0.y *= a;
+          P = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
+          P.x *= a;
+          P.y *= a;
         }
-        const uint32_t rbase = op_off<TF32>(mi * HE + hbase, kh);  // row hbase; rows are 16 B apart
-        if (p.HI >= 8) {
+        const int row0 = mi * HE + hbase;
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int hh = (c8 + q) & 7;
-            if (hh == 0) P = P0;
-            put2<TF32>(A, A + lo_a, rbase + 16u * hh, P.x, P.y);
-            P = cmul(P, W);
-          }
-        } else {  // rows h >= HI pad a short chirp to 8 rows
-#pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            const int hh = (c8 + q) & 7;
-            if (hh == 0) P = P0;
-            const bool live = hh < p.HI;
-            put2<TF32>(A, A + lo_a, rbase + 16u * hh, live ? P.x : 0.f, live ? P.y : 0.f);
-            P = cmul(P, W);
-          }
+        for (int q = 0; q < 8; ++q) {
+          const bool live = hbase + q < p.HI;  // rows h >= HI pad a short chirp to 8 rows
+          put2<TF32>(A, A + lo_a, op_off<TF32>(row0 + q, lane), live ? P.x : 0.f, live ? P.y : 0.f);
+          P = cmul(P, W);
         }
       }
       // B: terms t = 0..3, halves Re / Im of offset l: column 32 t + 16 half + l
@@ -404,8 +393,8 @@ k_synth_tc(const SynthTcParams p) {
 #pragma unroll
         for (int t = 0; t < kTerms; ++t) {
           const float re = w * B0.x, im = w * B0.y;
-          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, kh), re, -im);        // Re half
-          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, kh), im, re);   // Im half
+          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, lane), re, -im);        // Re half
+          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, lane), im, re);   // Im half
           w *= bl;
         }
       }
@@ -434,14 +423,16 @@ k_synth_tc(const SynthTcParams p) {
         const uint32_t a0 = smem_u32(smem + stg * kStageBytes), bb0 = a0 + kABytes;
         if (TF32) {
 #pragma unroll 1
-          for (int ks = 0; ks < kHitsPerBlock / 4; ++ks)
-            mma<true>(tmem, smem_desc(a0 + ks * 4096u, 128, 256), smem_desc(bb0 + ks * 4096u, 128, 256),
-                      (!fresh || ks > 0) ? 1u : 0u);
+          for (int ks = 0; ks < kHitsPerBlock / 4; ++ks) {
+            const uint32_t ko = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
+            mma<true>(tmem, smem_desc_sw128(a0 + ko), smem_desc_sw128(bb0 + ko), (!fresh || ks > 0) ? 1u : 0u);
+          }
         } else {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
-            const uint64_t ahi = smem_desc(a0 + ks * 4096u, 128, 256), alo = smem_desc(a0 + lo_a + ks * 4096u, 128, 256);
-            const uint64_t bhi = smem_desc(bb0 + ks * 4096u, 128, 256), blo = smem_desc(bb0 + lo_b + ks * 4096u, 128, 256);
+            const uint32_t ko = (uint32_t)ks * 32u;
+            const uint64_t ahi = smem_desc_sw128(a0 + ko), alo = smem_desc_sw128(a0 + lo_a + ko);
+            const uint64_t bhi = smem_desc_sw128(bb0 + ko), blo = smem_desc_sw128(bb0 + lo_b + ko);
             mma<false>(tmem, alo, bhi, (!fresh || ks > 0) ? 1u : 0u);
             mma<false>(tmem, ahi, blo, 1u);
             mma<false>(tmem, ahi, bhi, 1u);
@@ -486,6 +477,35 @@ k_synth_tc(const SynthTcParams p) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
+}
+
+// Per-hit constants of the synthesis, once per (frame, channel, hit) for all
+// tiles: c0 = frac(f0 d / c) (the FP64 carrier reduction), c1 = f0 d-dot
+// T_rep / c, b0 = S dt d / c, b1 = S dt d-dot T_rep / c; and the check of
+// the coupling expansion's bound for the widest tile.
+__global__ void k_tc_consts(const SynthTcParams p, float mu_max) {
+  const int job = blockIdx.z, j = blockIdx.y;
+  const float *dbase = p.d, *ddbase = p.dd;
+  int64_t ld = p.ld;
+  int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+  if (p.jobs) {
+    const FrameJob &J = p.jobs[job];
+    dbase = J.hit_d;
+    ddbase = J.hit_dd;
+    ld = J.ld;
+    K = min((int64_t)*J.count, J.cap);
+  }
+  const float *dj = dbase + (int64_t)j * ld, *ddj = ddbase + (int64_t)j * ld;
+  float4 *cj = p.cst + (dj - p.d_base);
+  bool bad = false;
+  for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
+    const float d = dj[k], dd = ddj[k];
+    const double x = p.f0_c * (double)d;
+    const float b1 = p.b1k * dd;
+    cj[k] = make_float4((float)(x - floor(x)), p.c1k * dd, (float)(p.kb * (double)d), b1);
+    if (6.2831853f * fabsf(b1) * mu_max * (float)(kLO - 1) > 0.157f) bad = true;
+  }
+  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_TC_BOUND);
 }
 
 __global__ void k_tc_reduce(const float2 *__restrict__ partials, int S, int64_t total, int n_jobs,
@@ -559,7 +579,8 @@ int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
                             int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
-                            cudaStream_t st) {
+                            float4 *cst, const float *d_base, cudaStream_t st) {
+  if (!cst) return cudaErrorInvalidValue;  // d_base may be null with no hits
   if (!synth_tc_supported(r) || n_jobs < 1) return cudaErrorInvalidValue;
   const TcPlan pl = tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split);
   const int64_t total = (int64_t)r.n_rx * r.M * r.N;
@@ -576,6 +597,20 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
   p.partials = partials;
   p.jobs = jobs;
   p.err = err;
+  p.cst = cst;
+  p.d_base = d_base;
+  {
+    int sms = 152, dev = 0;
+    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int64_t per = (kmax + 255) / 256;
+    int bx = (int)(per < 1 ? 1 : per);
+    const int cap = (4 * sms + r.n_rx * n_jobs - 1) / (r.n_rx * n_jobs);
+    if (bx > cap) bx = cap < 1 ? 1 : cap;
+    const float mu_max = 0.5f * (float)((pl.mc < r.M ? pl.mc : r.M) - 1);
+    k_tc_consts<<<dim3(bx, r.n_rx, n_jobs), 256, 0, st>>>(p, mu_max);
+    const cudaError_t ec = cudaGetLastError();
+    if (ec != cudaSuccess) return ec;
+  }
   cudaError_t e = tf32 ? launch_tc<true>(p, n_jobs, st) : launch_tc<false>(p, n_jobs, st);
   if (e != cudaSuccess) return e;
   const int threads = 256;
