@@ -431,9 +431,15 @@ int cluster_build_capacity() { return 16 * kMaxCap; }
 
 bool cluster_build_usable() { return cluster_usable(); }
 
-int cluster_size_for(int n) { return n <= 8 * 2048 ? 8 : 16; }
+// One frame: 8 CTAs up to 16384 triangles, else 16 (the shorter sort
+// passes win).  Batches: 8 CTAs as long as they fit (twice as many meshes
+// build at once on the 152 SMs, which matters more than each one's time).
+int cluster_size_for(int n, bool batch) {
+  if (batch) return n <= 8 * kMaxCap ? 8 : 16;
+  return n <= 8 * 2048 ? 8 : 16;
+}
 
-BuildJob build_job_for(const SceneDev &s) {
+BuildJob build_job_for(const SceneDev &s, int C) {
   BuildJob j;
   j.V = s.V;
   j.F = s.F;
@@ -443,7 +449,6 @@ BuildJob build_job_for(const SceneDev &s) {
   j.ids = s.ids;
   j.hdr = s.hdr;
   j.n = (int)s.nt;
-  const int C = cluster_size_for(j.n);
   j.cap = (j.n + C - 1) / C;
   return j;
 }
@@ -453,8 +458,9 @@ cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used) {
   const int n = (int)s.nt;
   if (n < 2 || n > 16 * kMaxCap) return cudaSuccess;
   if (!cluster_usable()) return cudaSuccess;
-  const BuildJob j = build_job_for(s);
-  const cudaError_t e = launch_clusters(j, nullptr, 1, cluster_size_for(n), j.cap, st);
+  const int C = cluster_size_for(n, false);
+  const BuildJob j = build_job_for(s, C);
+  const cudaError_t e = launch_clusters(j, nullptr, 1, C, j.cap, st);
   if (e == cudaSuccess) *used = true;
   return e;
 }

@@ -766,7 +766,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
     const int n = (int)sc[j]->nt;
     const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
-    if (cl && rr::cluster_size_for(n) == 8) ++P.n8;
+    if (cl && rr::cluster_size_for(n, true) == 8) ++P.n8;
     else if (cl) ++P.n16;
     else P.others.push_back(sc[j]);
   }
@@ -861,8 +861,9 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.h_ftab[j] = f;
     const int n = (int)s->nt;
     if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
-      const rr::BuildJob bj = rr::build_job_for(*s);
-      if (rr::cluster_size_for(n) == 8) {
+      const int C = rr::cluster_size_for(n, true);
+      const rr::BuildJob bj = rr::build_job_for(*s, C);
+      if (C == 8) {
         b.h_btab[i8++] = bj;
         P.max_cap8 = std::max(P.max_cap8, bj.cap);
       } else {

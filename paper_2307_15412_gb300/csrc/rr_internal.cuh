@@ -138,9 +138,10 @@ cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used);
 int cluster_build_capacity();
 // Whether the current device runs the 16-CTA cluster builder (checked once per device).
 bool cluster_build_usable();
-// Cluster size (8 or 16 CTAs) the builder uses for n triangles.
-int cluster_size_for(int n);
-BuildJob build_job_for(const SceneDev &s);
+// Cluster size (8 or 16 CTAs) the builder uses for n triangles, for a single
+// frame or inside a batch.
+int cluster_size_for(int n, bool batch);
+BuildJob build_job_for(const SceneDev &s, int C);
 // One launch building every job of a device table, all with cluster size C
 // (jobs with cluster_size_for(n) == C) and dynamic shared memory for
 // max_cap keys per CTA.  cudaErrorNotSupported if clusters are unusable.

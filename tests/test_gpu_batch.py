@@ -160,3 +160,45 @@ def test_batch_rejects_bad_arguments(ctx):
     with pytest.raises(rr.RRError, match="RR_EINVAL"):
         ctx.batch_run([(500, I.RayGrid(0, 4, 0.1, 0.1))], radar, if_out=out)
     ctx.sync()
+
+
+@pytest.mark.parametrize("nt_target", [600, 20000, 28000, 50000])
+def test_batch_built_bvh_is_the_oracle_tree(ctx, nt_target):
+    """Inside a batch meshes up to 29 600 triangles are built by 8-CTA
+    clusters (up to 3700 keys per CTA), larger ones by 16: the sorted codes
+    and ids must still be the oracle's integers, every leaf box exact."""
+    from oracle import bvh as obvh
+    radar, grid, _ = I.workload_tiny()
+    s = I.hand_scene(90, nt_target)
+    n = s.F.shape[0]
+    ctx.scene_upload(700, s.V, s.F, s.vel)
+    ctx.scene_upload(701, s.V, s.F, s.vel)
+    out = _cube(2, radar)
+    ctx.batch_run([(700, grid), (701, grid)], radar, if_out=out)
+    codes = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    left = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
+    right = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
+    boxes = torch.empty((n - 1, 12), dtype=torch.float32, device="cuda:0")
+    root = ctx.get_bvh(700, codes, ids, left, right, boxes)
+    ctx.sync()
+    ref_codes = obvh.morton_codes(s.V, s.F)
+    order = obvh.sorted_order(ref_codes)
+    g_ids = ids.cpu().numpy()
+    assert np.array_equal(g_ids, order)
+    assert np.array_equal(codes.cpu().numpy().view(np.uint32), ref_codes[order])
+    if n <= 5000:
+        L, R, rl, rr_, rt = obvh.radix_tree(ref_codes[order])
+        assert root[0] == rt
+        assert np.array_equal(left.cpu().numpy(), L) and np.array_equal(right.cpu().numpy(), R)
+    bx = boxes.cpu().numpy()
+    tri_lo, tri_hi = s.V[s.F].min(axis=1), s.V[s.F].max(axis=1)
+    for side, kids in ((0, left.cpu().numpy()), (1, right.cpu().numpy())):
+        leaf = kids < 0
+        tid = g_ids[~kids[leaf]]
+        off = 4 * side
+        lo = np.stack([bx[leaf, off + 0], bx[leaf, off + 2], bx[leaf, 8 + 2 * side]], 1)
+        hi = np.stack([bx[leaf, off + 1], bx[leaf, off + 3], bx[leaf, 9 + 2 * side]], 1)
+        assert np.array_equal(lo, tri_lo[tid]) and np.array_equal(hi, tri_hi[tid])
+    g = to_complex(out)
+    assert rel_l2(g[1], g[0]) <= 1e-5  # same mesh twice: same frame
