@@ -334,6 +334,16 @@ k_synth_tc(const SynthTcParams p) {
     const int hbase = 8 * seg;
     const int l = warp;
     const float4 *cj = p.cst + (dj - p.d_base);      // this channel's constants
+    // the constants of block b + 1 are loaded while block b is generated
+    float4 cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
+    float a_next = 0.f;
+    {
+      const int64_t k = (int64_t)s_idx * kHitsPerBlock + lane;
+      if (nb > 0 && k < K) {
+        cv_next = cj[k];
+        a_next = aj[k];
+      }
+    }
     for (int b = 0; b < nb; ++b) {
       if (s_abort) break;
       if (warp < 4 && b > 0 && b % kMaxChain == 0) {
@@ -356,12 +366,16 @@ k_synth_tc(const SynthTcParams p) {
         s_abort = 1;
         break;
       }
-      const int64_t k = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + lane;
-      float4 cv = make_float4(0.f, 0.f, 0.f, 0.f);
-      float a = 0.f;
-      if (k < K) {
-        cv = cj[k];
-        a = aj[k];
+      const float4 cv = cv_next;
+      const float a = a_next;
+      {
+        const int64_t kn = ((int64_t)s_idx + (int64_t)(b + 1) * p.S) * kHitsPerBlock + lane;
+        cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        a_next = 0.f;
+        if (b + 1 < nb && kn < K) {
+          cv_next = cj[kn];
+          a_next = aj[kn];
+        }
       }
       const float c0 = cv.x, c1 = cv.y, b0 = cv.z, b1 = cv.w;
       // A: rows (chirp mi, h = hbase .. hbase + 7) of this hit
