@@ -160,11 +160,14 @@ __device__ __forceinline__ float2 cmul(float2 x, float2 y) {
   return make_float2(x.x * y.x - x.y * y.y, x.x * y.y + x.y * y.x);
 }
 
-// e^{-j 2 pi x} for any FP32 x (x is first reduced to [-1/2, 1/2])
+// e^{-j 2 pi x} for any FP32 x: x is reduced to r in [-1/2, 1/2] exactly
+// (x - rint(x)), then the hardware sine/cosine (__sincosf) of 2 pi r, whose
+// absolute error on [-pi, pi] (about 2^-21) is far below the BF16x3 and
+// TF32 operand rounding this path applies afterwards.
 __device__ __forceinline__ float2 expm2pi(float x) {
   const float r = x - rintf(x);
   float s, c;
-  sincospif(2.f * r, &s, &c);
+  __sincosf(6.28318530717958647692f * r, &s, &c);
   return make_float2(c, -s);
 }
 
@@ -203,6 +206,14 @@ __device__ __forceinline__ uint32_t op_off(int x, int k) {
            (uint32_t)(kk & 1) * 8u;
   }
   return (uint32_t)x * 128u + (uint32_t)(((k >> 2) ^ (x & 7)) << 4) + (uint32_t)(k & 3) * 4u;
+}
+
+// Offset of row base_row + q (base_row % 8 == 0, base = op_off(base_row, k)):
+// the row moves by q * 128 bytes and the swizzled chunk by XOR with q.
+template <bool TF32>
+__device__ __forceinline__ uint32_t row_off(uint32_t base, int q, int k) {
+  const int chunk = TF32 ? ((k & 15) >> 1) : (k >> 2);
+  return base + (uint32_t)q * 128u + (uint32_t)(((chunk ^ q) - chunk) << 4);
 }
 
 // Shared-memory matrix descriptor of a K-major operand in the 128-byte
@@ -390,12 +401,21 @@ k_synth_tc(const SynthTcParams p) {
           P.x *= a;
           P.y *= a;
         }
-        const int row0 = mi * HE + hbase;
+        // rows row0 .. row0 + 7 (row0 % 8 == 0, so row % 8 == q)
+        const uint32_t base = op_off<TF32>(mi * HE + hbase, lane);
+        if (p.HI >= 8) {
 #pragma unroll
-        for (int q = 0; q < 8; ++q) {
-          const bool live = hbase + q < p.HI;  // rows h >= HI pad a short chirp to 8 rows
-          put2<TF32>(A, A + lo_a, op_off<TF32>(row0 + q, lane), live ? P.x : 0.f, live ? P.y : 0.f);
-          P = cmul(P, W);
+          for (int q = 0; q < 8; ++q) {
+            put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), P.x, P.y);
+            P = cmul(P, W);
+          }
+        } else {
+#pragma unroll
+          for (int q = 0; q < 8; ++q) {
+            const bool live = q < p.HI;  // rows h >= HI pad a short chirp to 8 rows
+            put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), live ? P.x : 0.f, live ? P.y : 0.f);
+            P = cmul(P, W);
+          }
         }
       }
       // B: terms t = 0..3, halves Re / Im of offset l: column 32 t + 16 half + l
