@@ -140,6 +140,40 @@ def cpu_oracle_frame_time(scene, radar, grid, frac: int):
     return (t1 - t0) * frac + (t2 - t1), int(hit.sum()), len(sel)
 
 
+def cpu_baseline_leg(ctx, scene, radar, grid, variant, dev):
+    """The FP64 oracle beside the GPU (rank 0, one GPU): (1) its time on a
+    sample of frame 0 (every 8th ray), scaled to a frame; (2) the accuracy
+    of the timed configuration: frame 0 through the same kernels and
+    variant, its IF cube against the oracle's direct sum (Eq. 4) over the
+    same hit list."""
+    import torch
+    import oracle
+    oracle.build()
+    frac = 8
+    ft, kh, nr = cpu_oracle_frame_time(scene, radar, grid, frac)
+    cpu = {"value": 1.0 / ft, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
+           "sample": "scene 0: every %d-th ray (%d rays, %d hits) traced brute force against all "
+                     "triangles, echoed and synthesised in FP64, time x%d; range-Doppler of that IF cube "
+                     "by direct DFT in full" % (frac, nr, kh, frac)}
+    n_rx, M, N = radar.n_rx, radar.n_chirps, radar.n_samples
+    one = torch.empty((n_rx, M, N, 2), dtype=torch.float32, device=dev)
+    ctx.build_bvh(0)
+    box = ctx.trace_frame(0, radar, grid)
+    ctx.sync()
+    Kh = box[0]
+    hd = torch.empty((n_rx, Kh), dtype=torch.float32, device=dev)
+    ha, hdd = torch.empty_like(hd), torch.empty_like(hd)
+    ctx.get_hits(0, Kh, None, None, None, hd, ha, hdd)
+    ctx.synth_if(0, radar, one, variant=variant)
+    ctx.sync()
+    ref = oracle.synth(hd.cpu().numpy(), ha.cpu().numpy(), hdd.cpu().numpy(), radar)
+    got = one.double().cpu().numpy()
+    got = got[..., 0] + 1j * got[..., 1]
+    acc = {"rel_l2_if_vs_fp64_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
+           "frame": "scene 0 (%d hits), same hit list on both sides" % Kh, "bound": 1e-3}
+    return cpu, acc
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -275,27 +309,6 @@ def run_gpu(args):
     peak_tc = float(peaks.get("bf16_tflops_sustained", 1700.0))
     peak_fp32 = props.multi_processor_count * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
 
-    # accuracy of the timed configuration: frame 0 through the same kernels,
-    # its IF cube against the FP64 oracle's sum over the same hit list
-    acc = None
-    if rank == 0 and not args.no_cpu_baseline:
-        import oracle
-        one = torch.empty((n_rx, M, N, 2), dtype=torch.float32, device=dev)
-        ctx.build_bvh(0)
-        box = ctx.trace_frame(0, radar, grid)
-        ctx.sync()
-        Kh = box[0]
-        hd = torch.empty((n_rx, Kh), dtype=torch.float32, device=dev)
-        ha, hdd = torch.empty_like(hd), torch.empty_like(hd)
-        ctx.get_hits(0, Kh, None, None, None, hd, ha, hdd)
-        ctx.synth_if(0, radar, one, variant=variant)
-        ctx.sync()
-        ref = oracle.synth(hd.cpu().numpy(), ha.cpu().numpy(), hdd.cpu().numpy(), radar)
-        got = one.double().cpu().numpy()
-        got = got[..., 0] + 1j * got[..., 1]
-        acc = {"rel_l2_if_vs_fp64_oracle": float(np.linalg.norm(got - ref) / np.linalg.norm(ref)),
-               "frame": "scene 0 (%d hits), same hit list on both sides" % Kh, "bound": 1e-3}
-
     # end to end through the public API: every step copies the frames' meshes
     # from pinned host memory to the device, uploads them into the scene
     # slots, runs the batch and reads the range-Doppler cubes back into
@@ -331,16 +344,9 @@ def run_gpu(args):
     d2h = rd_out.numel() * 4
     ctx.sync()
 
-    cpu = None
+    cpu, acc = None, None
     if rank == 0 and ws == 1 and not args.no_cpu_baseline:
-        import oracle
-        oracle.build()
-        frac = 8
-        ft, kh, nr = cpu_oracle_frame_time(scenes[0], radar, grid, frac)
-        cpu = {"value": 1.0 / ft, "unit": "frames/s", "cores": oracle.num_threads(), "kind": "oracle",
-               "sample": "scene 0: every %d-th ray (%d rays, %d hits) traced brute force against all "
-                         "triangles, echoed and synthesised in FP64, time x%d; range-Doppler of that IF cube "
-                         "by direct DFT in full" % (frac, nr, kh, frac)}
+        cpu, acc = cpu_baseline_leg(ctx, scenes[0], radar, grid, variant, dev)
 
     if rank == 0:
         line = {"metric": METRIC, "value": value, "unit": "frames/s", "n_gpus": ws, "steps": K,

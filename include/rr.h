@@ -217,7 +217,10 @@ typedef struct {
  * uploaded scenes.  if_out: device complex64 [n_jobs][n_rx][n_chirps]
  * [n_samples] (may be NULL when rd_out is given); rd_out: device complex64
  * of the same shape (fft-shifted Doppler axis, see rr_range_doppler) or
- * NULL.  Sizes as for rr_synth_if / rr_range_doppler; only RR_SYNTH_FP32.
+ * NULL.  Sizes and variants as for rr_synth_if / rr_range_doppler (a
+ * tensor-core variant reports RR_EINVAL at rr_sync when a path rate moves
+ * a hit's range within a chirp tile beyond its expansion's bound, as for
+ * a single frame).
  * flags: RR_BATCH_GRAPH captures the enqueued work as a CUDA graph on the
  * first call of a batch (after one eager run) and replays it on later calls
  * with identical jobs, radar, outputs and scene buffers (any change

@@ -57,7 +57,8 @@ struct rr_ctx {
     int64_t partials_cap = 0;
     float *if_tmp = nullptr;
     int64_t if_tmp_cap = 0;
-    float4 *tc_cst = nullptr;               // per-hit constants, laid out like d (RR_MAX_RX rows of cap)
+    float4 *tc_cst = nullptr;               // per-hit constants, laid out like d (tc_cst_rows rows of cap)
+    int tc_cst_rows = 0;
     // CUDA graph of the last batch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
@@ -211,7 +212,7 @@ rr_status run_synth(rr_ctx *c, const rr_radar *r, rr_synth_variant v, const uint
   const int64_t need = rr::synth_tc_partial_floats(rd, kmax, 1, 0);
   RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
   RR_CUDA(c, grow(c->tc_cst, c->tc_cst_cap, (int64_t)r->n_rx * (ld > 0 ? ld : 1)), "synth constants");
-  RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, 0, c->partials,
+  RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, nullptr, 0, c->partials,
                                  c->partials_cap, out, c->d_err, c->tc_cst, d, c->stream),
           "synth_if launch (tensor cores)");
   return RR_OK;
@@ -326,7 +327,7 @@ rr_status rr_sync(rr_ctx *c) {
   else if (err & rr::ERR_BAD_INPUT) st = fail(c, RR_EINVAL, "kernel rejected its input");
   else if (err & rr::ERR_TC_BOUND)
     st = fail(c, RR_EINVAL, "tensor-core synthesis: a path rate moves the range within a chirp tile beyond the "
-                            "first-order bound; use RR_SYNTH_FP32 for this hit list");
+                            "bound of the four-term expansion; use RR_SYNTH_FP32 for this hit list");
   return st;
 }
 
@@ -641,12 +642,16 @@ int64_t batch_partials_need(const BatchPlan &P, int split) {
   return rr::synth_tc_partial_floats(P.rd, P.kmax, P.n_jobs, split);
 }
 
+// The frames of a batch by decreasing hit count (written by the trace
+// launch's hit-prefix scan), stored after the prefix.
+int *batch_order(rr_ctx *c, int n_jobs) { return reinterpret_cast<int *>(c->batch.prefix + n_jobs + 1); }
+
 cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split, cudaStream_t st) {
   auto &b = c->batch;
   if (P.variant == RR_SYNTH_FP32)
     return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb, st);
   return rr::launch_synth_tc(P.rd, P.variant == RR_SYNTH_TC_TF32, nullptr, P.kmax, 0, nullptr, nullptr, nullptr, b.ftab,
-                             P.n_jobs, split, b.partials, b.partials_cap, P.ifb, c->d_err, b.tc_cst, b.d, st);
+                             P.n_jobs, batch_order(c, P.n_jobs), split, b.partials, b.partials_cap, P.ifb, c->d_err, b.tc_cst, b.d, st);
 }
 
 // Enqueues one batch on stream st: no allocation, no host wait, so the same
@@ -665,7 +670,7 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
   for (SceneDev *s : P.others)
     if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
-  if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
+  if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, batch_order(c, P.n_jobs), P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
   if ((e = batch_synth(c, P, P.split, st)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[3], st)) != cudaSuccess) return e;
@@ -696,7 +701,7 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) break;
       if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
-      if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, tws[k])) != cudaSuccess) break;
+      if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, batch_order(c, P.n_jobs), P.rd, c->d_err, st, tws[k])) != cudaSuccess) break;
       if ((e = cudaEventRecord(e1, st)) != cudaSuccess) break;
       if ((e = cudaEventSynchronize(e1)) != cudaSuccess) break;
       float ms = 0.f;
@@ -707,7 +712,7 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
   // split-K candidates on the hit lists of the chosen shape
   if (e == cudaSuccess) {
     e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st);
-    if (e == cudaSuccess) e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, P.rd, c->d_err, st, best_tw);
+    if (e == cudaSuccess) e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, batch_order(c, P.n_jobs), P.rd, c->d_err, st, best_tw);
   }
   best = INFINITY;
   const int splits[4] = {0, 1, 2, 4};
@@ -785,6 +790,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.ray = b.tri = b.pos = nullptr;
     b.t = b.d = b.a = b.dd = nullptr;
     b.tc_cst = nullptr;
+    b.tc_cst_rows = 0;
     b.cap = 0;
     RR_CUDA(c, cudaMalloc((void **)&b.ray, sizeof(int32_t) * total), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.tri, sizeof(int32_t) * total), "batch hit list");
@@ -793,8 +799,16 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaMalloc((void **)&b.d, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.a, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.dd, sizeof(float) * total * RR_MAX_RX), "batch hit list");
-    RR_CUDA(c, cudaMalloc((void **)&b.tc_cst, sizeof(float4) * total * RR_MAX_RX), "batch hit list");
     b.cap = total;
+    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  }
+  // per-hit constants of the tensor-core synthesis: n_rx rows of `cap`
+  if (variant != RR_SYNTH_FP32 && (b.tc_cst_rows < n_rx || !b.tc_cst)) {
+    if (b.tc_cst) cudaFree(b.tc_cst);
+    b.tc_cst = nullptr;
+    b.tc_cst_rows = 0;
+    RR_CUDA(c, cudaMalloc((void **)&b.tc_cst, sizeof(float4) * b.cap * n_rx), "batch synthesis constants");
+    b.tc_cst_rows = n_rx;
     if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
   }
   if (n_jobs > b.jobs_cap || !b.counts) {
@@ -812,7 +826,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaMalloc((void **)&b.ftab, sizeof(rr::FrameJob) * nj), "batch tables");
     RR_CUDA(c, cudaMalloc((void **)&b.btab, sizeof(rr::BuildJob) * nj), "batch tables");
     RR_CUDA(c, cudaMalloc((void **)&b.jt, sizeof(rr::JobTiles) * (nj + 1)), "batch tables");
-    RR_CUDA(c, cudaMalloc((void **)&b.prefix, sizeof(int64_t) * (nj + 1)), "batch tables");
+    // prefix: int64[nj + 1], then the launch order int[nj]
+    RR_CUDA(c, cudaMalloc((void **)&b.prefix, sizeof(int64_t) * (nj + 1) + sizeof(int) * nj), "batch tables");
     RR_CUDA(c, cudaMallocHost((void **)&b.h_ftab, sizeof(rr::FrameJob) * nj), "batch tables");
     RR_CUDA(c, cudaMallocHost((void **)&b.h_btab, sizeof(rr::BuildJob) * nj), "batch tables");
     b.jobs_cap = n_jobs;

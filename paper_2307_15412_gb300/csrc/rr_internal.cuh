@@ -16,7 +16,7 @@ enum : uint32_t {
   ERR_STACK_OVERFLOW = 1u << 1,
   ERR_TIMEOUT = 1u << 2,
   ERR_BAD_INPUT = 1u << 3,
-  ERR_TC_BOUND = 1u << 4,  // tensor-core synthesis: range migration inside a tile beyond the first-order bound
+  ERR_TC_BOUND = 1u << 4,  // tensor-core synthesis: range migration inside a tile beyond the coupling expansion's bound
 };
 
 constexpr double kC = 299792458.0;  // speed of light, m/s
@@ -153,8 +153,9 @@ cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64
                          uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 // Trace + echo of n_jobs frames in three launches plus two one-CTA scans.
 // table: device FrameJob[n_jobs] (counters zeroed by the caller); jt: device
-// JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1].
-cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix,
+// JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1]; order (may be
+// null): device int[n_jobs], filled with the frames by decreasing hit count.
+cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix, int *order,
                                const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,
                               int64_t ld, const float *d, const float *a, const float *dd,
@@ -179,9 +180,10 @@ int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int
 // cst: float4 scratch laid out like the hit arrays (at least n_rx * ld
 // entries past d_base: d_base = d for one frame, the base of the batch hit
 // arrays for a batch) for the per-hit constants.
+// order (may be null): device int[n_jobs], the frames in launch order.
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
-                            int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
+                            const int *order, int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
                             float4 *cst, const float *d_base, cudaStream_t st);
 // Learned-surrogate kernels (see mlp.cu).  gemm_tn: C = A B^T with A
 // [M][K], B [N][K] BF16 row-major (K a multiple of 8, 16-byte aligned),

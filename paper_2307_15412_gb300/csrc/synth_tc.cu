@@ -11,42 +11,43 @@
 // its reduction index the hits.  A tile of 128 rows holds mc chirps of
 // HE = max(HI, 8) rows each (HI = N / 16; rows h >= HI are zero padding, so
 // mc = 128 / HE <= 16).  Around the tile's centre chirp m_c, m = m_c + mu:
-//   phi = [c0 + c1 m + beta_m LO h] + beta_c l + b1 mu l,
-//   beta_m = b0 + b1 m, beta_c = b0 + b1 m_c.
-// The coupling exp(-j 2 pi b1 mu l) is expanded to third order,
-//   exp(-j x) = sum_{t<4} (-j sigma)^t l^t / t!,  sigma = 2 pi b1 mu, x = sigma l,
-// which gives four exact-rank terms per hit:
-//   s[(m,h)][l] = sum_k sum_{t<4} A_t[(m,h)][k] B_t[k][l],
-//   A_t = a e^{-j 2 pi [c0 + c1 m + beta_m LO h]} (-j sigma)^t / t!,
-//   B_t = l^t e^{-j 2 pi beta_c l}.
-// The remainder is below x^4 / 24, x <= 2 pi |b1| max|mu| (LO - 1); every
-// hit checks x <= 0.157 (remainder <= 1e-6 relative) and latches
-// ERR_TC_BOUND otherwise.  For the full-frame radar (N = 256, 8 chirps per
-// tile) at |d-dot| = 2 m/s, x = 2.2e-3; for N = 128 (16 chirps), 9.4e-3.
+//   phi = [c0 + c1 m + beta_m LO h + b1 mu l_c] + beta_c l + b1 mu (l - l_c),
+//   beta_m = b0 + b1 m, beta_c = b0 + b1 m_c, l_c = (LO - 1) / 2.
+// The coupling exp(-j 2 pi b1 mu (l - l_c)) is expanded to third order,
+//   exp(-j x) = sum_{t<4} (-j 2 pi mu)^t (b1 (l - l_c))^t / t!,
+// which gives four exact-rank terms per hit.  The remainder is below
+// x^4 / 24, x <= 2 pi |b1| max|mu| (LO - 1) / 2 (centring l halves x); every
+// hit checks x <= 0.157 (remainder <= 2.6e-5 relative, a quarter of the
+// split-BF16x3 tolerance) and latches ERR_TC_BOUND otherwise.  For the
+// full-frame radar (N = 256, 8 chirps per tile) at |d-dot| = 2 m/s,
+// x = 1.1e-3; for N = 128 (16 chirps), 4.7e-3.
 //
 // The b1 factor of each term belongs to the hit and mu to the row, so the
 // terms are carried in the GEMM's N dimension:
-//   D_t[(m,h)][l] = sum_k A[(m,h)][k] B_t[k][l],   A = a e^{-j 2 pi [c0 + c1 m + beta_m LO h]},
-//                                                  B_t = (b1 l)^t e^{-j 2 pi beta_c l},
+//   D_t[(m,h)][l] = sum_k A[(m,h)][k] B_t[k][l],   A = a e^{-j 2 pi [c0 + c1 m + beta_m LO h + b1 mu l_c]},
+//                                                  B_t = (b1 (l - l_c))^t e^{-j 2 pi beta_c l},
 //   s[(m,h)][l] = sum_t kappa_t(mu) D_t,           kappa_t = (-j 2 pi mu)^t / t!,
-// with kappa applied per row in the epilogue.  Complex values are made real
-// by doubling the columns: D = [t][Re | Im][l] is 128 x 128 (M = N = 128);
-// the reduction runs over (hit, re/im), 2 entries per hit, with
+// with kappa applied per row in the epilogue.  Each CTA uses the T <= 4
+// terms its hits need (x^T / T! below the variant's rounding; T = 1 for a
+// static scene or a one-chirp tile).  Complex values are made real by
+// doubling the columns: D = [t][Re | Im][l] is 128 x 32 T (M = 128,
+// N = 32 T); the reduction runs over (hit, re/im), 2 entries per hit, with
 // B = [[Re B_t, Im B_t], [-Im B_t, Re B_t]].  Variants: BF16x3
 // (x = x_hi + x_lo in bfloat16, products lo*hi + hi*lo + hi*hi, kind::f16)
 // and TF32 (inputs rounded to TF32 in the producer, kind::tf32); FP32
-// accumulation in tensor memory (128 columns) in both.
+// accumulation in tensor memory in both.
 //
 // Per CTA: one (frame, channel, 128-row tile) and an interleaved share of
-// its hits (split-K).  Blocks of 32 hits are generated by all 256 threads
-// into one of three 64 KB shared-memory stages (canonical K-major layout
-// without swizzle: 8 x 16-byte core matrices, LBO = 128 B between
-// K-neighbours, SBO = 256 B between 8-row groups) while the tensor core
-// consumes the others; thread 0 issues the MMAs and commits them to the
-// stage's mbarrier.  A warp writes 4 hits x 8 rows (or columns) per store,
-// the rows staggered so that they fill one 128-byte bank window.  All waits
-// are bounded; a wait that runs out latches ERR_TIMEOUT, drains what it can
-// and frees the tensor memory.
+// its hits (split-K).  Sixteen producer warps generate blocks of 32 hits
+// (lane = hit) into a ring of three 64 KB shared-memory stages in the
+// 128-byte swizzled K-major layout (one warp store fills one 128-byte row,
+// free of bank conflicts); warp w writes the 8 A rows of its (chirp,
+// h-segment) unit and the B columns of offset l = w.  One lane of warp 16
+// issues the MMAs of a full stage and commits them to the stage's empty
+// barrier.  Every 64 blocks warps 0-3 fold the accumulator into an FP32
+// row buffer (long chains in tensor memory lose precision).  All waits are
+// bounded; a wait that runs out latches ERR_TIMEOUT, drains what it can and
+// frees the tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -61,6 +62,7 @@ constexpr int kTcThreads = 544;  // 16 producer warps + 1 MMA warp
 constexpr int kLO = 16;
 constexpr int kHitsPerBlock = 32;
 constexpr int kTerms = 4;                         // terms of the coupling expansion
+constexpr float kLC = 0.5f * (float)(kLO - 1);    // centre l_c of the fast-time offsets
 constexpr int kStages = 3;
 // Long accumulation chains in tensor memory lose precision (2.4e-4 rel-L2
 // for 37k hits in one accumulator against 1.3e-5 for 1.7k, split-BF16x3), so
@@ -69,7 +71,7 @@ constexpr int kStages = 3;
 constexpr int kMaxChain = 64;                      // blocks (of 32 hits) per accumulation chain
 constexpr int kStageBytes = 64 * 1024;           // A region 32 KB + B region 32 KB
 constexpr int kABytes = 32 * 1024;
-constexpr int kTmemCols = 128;
+constexpr int kTmemCols = 256;  // accumulator: 32 T columns (TF32) or 64 T (BF16x3, hi and lo products)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 struct SynthTcParams {
@@ -82,6 +84,7 @@ struct SynthTcParams {
   float c1k, b1k;
   float *partials;        // [jobs][S][n_rx][M][N] complex
   const FrameJob *jobs;
+  const int *order;       // frames in launch order (largest hit lists first) or null
   uint32_t *err;
   // per-hit constants (c0, c1, b0, b1) laid out like the hit arrays: entry
   // (hit_d pointer - d_base) + j * ld + k for hit k of channel j
@@ -131,23 +134,24 @@ __device__ __forceinline__ uint64_t smem_desc(uint32_t addr, uint32_t lbo, uint3
 }
 
 // Instruction descriptor: D f32, A/B of type `ab` (1 = BF16 under kind::f16,
-// 2 = TF32 under kind::tf32), both K-major, N = 128, M = 128.
-__host__ __device__ constexpr uint32_t idesc(uint32_t ab) {
-  return (1u << 4) | (ab << 7) | (ab << 10) | ((128u >> 3) << 17) | ((128u >> 4) << 24);
+// 2 = TF32 under kind::tf32), both K-major, M = 128, N = n (a multiple of
+// 16 up to 256).
+__host__ __device__ constexpr uint32_t idesc(uint32_t ab, uint32_t n) {
+  return (1u << 4) | (ab << 7) | (ab << 10) | ((n >> 3) << 17) | ((128u >> 4) << 24);
 }
 
 template <bool TF32>
-__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t accumulate) {
+__device__ __forceinline__ void mma(uint32_t tmem, uint64_t da, uint64_t db, uint32_t id, uint32_t accumulate) {
   if (TF32) {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc(2)), "r"(accumulate));
+        "l"(da), "l"(db), "r"(id), "r"(accumulate));
   } else {
     asm volatile(
         "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
         "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-        "l"(da), "l"(db), "r"(idesc(1)), "r"(accumulate));
+        "l"(da), "l"(db), "r"(id), "r"(accumulate));
   }
 }
 
@@ -225,6 +229,23 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
          (2ull << 61);
 }
 
+// Terms the coupling expansion needs for a largest phase x = 2 pi |b1|
+// mu_max l_c: the smallest T with remainder x^T / T! <= eps, eps = 2^-20
+// for BF16x3 (twenty times below its operand rounding, about 2^-16 per
+// product) and 2^-14 for TF32 (seven times below 2^-11); at most kTerms
+// (x <= 0.157 is checked per hit).
+template <bool TF32>
+__device__ __forceinline__ int expansion_terms(float x) {
+  const float eps = TF32 ? 6.103515625e-05f : 9.5367431640625e-07f;
+  float r = x;  // x^T / T! for T = 1, 2, 3
+  if (r <= eps) return 1;
+  r *= 0.5f * x;
+  if (r <= eps) return 2;
+  r *= x * (1.f / 3.f);
+  if (r <= eps) return 3;
+  return kTerms;
+}
+
 // Warp roles: warps 0..15 produce operands (and warps 0..3 run the
 // epilogue), warp 16 allocates tensor memory and issues the MMAs.
 // Barriers per stage: full (512 producer arrivals: the stage holds block b)
@@ -234,27 +255,41 @@ constexpr int kProducers = 512;
 constexpr int kFoldStride = 33;  // floats per row of the fold buffer (padded against bank conflicts)
 constexpr int kFoldBytes = 128 * kFoldStride * 4;
 
-// Adds sum_t kappa_t D_t of this thread's accumulator row (TMEM lane
-// 32 w + lane, w = warp % 4) into acc[0..15] (Re) and acc[16..31] (Im);
-// kappa = (1, -j sg, k2, j k3), k2 = -sg^2 / 2, k3 = sg^3 / 6.
-__device__ __forceinline__ void fold_row(uint32_t tmem, int warp, float sg, float k2, float k3, float *acc) {
+// Loads 32 accumulator columns of this thread's row (TMEM lane 32 w + lane).
+__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+      : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+        "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+        "=r"(r[30]), "=r"(r[31])
+      : "r"(taddr + 16u));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Adds sum_{t < nt} kappa_t D_t of this thread's accumulator row (TMEM
+// lane 32 w + lane, w = warp % 4) into acc[0..15] (Re) and acc[16..31] (Im);
+// kappa = (1, -j sg, k2, j k3), k2 = -sg^2 / 2, k3 = sg^3 / 6.  D_t sits in
+// columns 32 t; with `second` (BF16x3) the hi x lo product of term t sits in
+// columns 32 (nt + t) and is added to it.
+__device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
+                                         float *acc) {
   const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
 #pragma unroll
   for (int t = 0; t < kTerms; ++t) {
+    if (t >= nt) break;
     uint32_t r[32];
-    const uint32_t taddr = tbase + 32u * t;
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-          "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-        : "r"(taddr));
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-        : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-          "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-          "=r"(r[30]), "=r"(r[31])
-        : "r"(taddr + 16u));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+    tmem_ld32(tbase + 32u * t, r);
+    if (second) {
+      uint32_t r2[32];
+      tmem_ld32(tbase + 32u * (nt + t), r2);
+#pragma unroll
+      for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
+    }
 #pragma unroll
     for (int q = 0; q < kLO; ++q) {
       const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[kLO + q]);
@@ -272,13 +307,14 @@ k_synth_tc(const SynthTcParams p) {
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done, s_fold, s_folded;
   __shared__ uint32_t s_tmem;
+  __shared__ uint32_t s_bmax;  // largest |b1| among this CTA's hits (FP32 bits)
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int j = blockIdx.x % p.n_rx;
   const int tile = blockIdx.x / p.n_rx;
   const int s_idx = blockIdx.y;
-  const int job = blockIdx.z;
+  const int job = p.order ? p.order[blockIdx.z] : (int)blockIdx.z;
   const int m0 = tile * p.mc;
   const int mvalid = min(p.mc, p.M - m0);
   const float mcen = m0 + 0.5f * (float)(mvalid - 1);  // centre chirp of the tile
@@ -316,13 +352,29 @@ k_synth_tc(const SynthTcParams p) {
     mbar_init(smem_u32(&s_fold), 1);
     mbar_init(smem_u32(&s_folded), 128);
     s_abort = 0;
+    s_bmax = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 16384u;
+  const float4 *cj = p.cst + (dj - p.d_base);  // this channel's per-hit constants
+  // the expansion's terms for this CTA, from the largest |b1| of its hits
+  if (warp < 16) {
+    float bm = 0.f;
+    for (int b = warp; b < nb; b += 16) {
+      const int64_t k = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + lane;
+      if (k < K) bm = fmaxf(bm, fabsf(cj[k].w));
+    }
+    for (int o = 16; o; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+    if (lane == 0 && bm > 0.f) atomicMax(&s_bmax, __float_as_uint(bm));  // non-negative: bits order as values
+  }
+  __syncthreads();
+  const int nterms = expansion_terms<TF32>(6.2831853f * __uint_as_float(s_bmax) * mu_max * kLC);
+  // lo halves (BF16x3): A_lo 16 KB after A_hi; B_lo right after the 32 T
+  // rows of B_hi, so that one MMA of N = 64 T reads [B_hi | B_lo]
+  const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 4096u * (uint32_t)nterms;
   // accumulator rows of warps 0-3: row 32 w + lane = (chirp, h); fold buffer
   float *fold = reinterpret_cast<float *>(smem + kStages * kStageBytes);
   const int my_row = 32 * (warp & 3) + lane;
@@ -344,7 +396,6 @@ k_synth_tc(const SynthTcParams p) {
     const int mi = warp / nseg, seg = warp - mi * nseg;
     const int hbase = 8 * seg;
     const int l = warp;
-    const float4 *cj = p.cst + (dj - p.d_base);      // this channel's constants
     // the constants of block b + 1 are loaded while block b is generated
     float4 cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
     float a_next = 0.f;
@@ -365,7 +416,7 @@ k_synth_tc(const SynthTcParams p) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        fold_row(tmem, warp, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * kFoldStride);
+        fold_row(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * kFoldStride);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
       }
@@ -395,26 +446,32 @@ k_synth_tc(const SynthTcParams p) {
         if (mi < mvalid) {
           const float fm = (float)(m0 + mi);
           const float beta = fmaf(fm, b1, b0);
-          const float cyc = fmaf(fm, c1, c0);
+          const float cyc = fmaf(fm, c1, c0) + b1 * ((fm - mcen) * kLC);
           W = expm2pi(beta * (float)kLO);
           P = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
           P.x *= a;
           P.y *= a;
         }
-        // rows row0 .. row0 + 7 (row0 % 8 == 0, so row % 8 == q)
+        // rows row0 .. row0 + 7 (row0 % 8 == 0, so row % 8 == q): P W^q
+        // by a tree of depth 3 (W^2, W^4) instead of a chain of 7 products
+        float2 R[8];
+        R[0] = P;
+        R[1] = cmul(P, W);
+        const float2 W2 = cmul(W, W);
+        R[2] = cmul(P, W2);
+        R[3] = cmul(R[1], W2);
+        const float2 W4 = cmul(W2, W2);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) R[4 + q] = cmul(R[q], W4);
         const uint32_t base = op_off<TF32>(mi * HE + hbase, lane);
         if (p.HI >= 8) {
 #pragma unroll
-          for (int q = 0; q < 8; ++q) {
-            put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), P.x, P.y);
-            P = cmul(P, W);
-          }
+          for (int q = 0; q < 8; ++q) put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), R[q].x, R[q].y);
         } else {
 #pragma unroll
           for (int q = 0; q < 8; ++q) {
             const bool live = q < p.HI;  // rows h >= HI pad a short chirp to 8 rows
-            put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), live ? P.x : 0.f, live ? P.y : 0.f);
-            P = cmul(P, W);
+            put2<TF32>(A, A + lo_a, row_off<TF32>(base, q, lane), live ? R[q].x : 0.f, live ? R[q].y : 0.f);
           }
         }
       }
@@ -422,10 +479,11 @@ k_synth_tc(const SynthTcParams p) {
       {
         const float beta_c = fmaf(mcen, b1, b0);
         const float2 B0 = expm2pi(beta_c * (float)l);
-        const float bl = b1 * (float)l;
-        float w = 1.f;  // (b1 l)^t
+        const float bl = b1 * ((float)l - kLC);
+        float w = 1.f;  // (b1 (l - l_c))^t
 #pragma unroll
         for (int t = 0; t < kTerms; ++t) {
+          if (t >= nterms) break;  // columns 32 t .. of unused terms are not read
           const float re = w * B0.x, im = w * B0.y;
           put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, lane), re, -im);        // Re half
           put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, lane), im, re);   // Im half
@@ -439,6 +497,10 @@ k_synth_tc(const SynthTcParams p) {
   } else {
     // ---- MMA issuer (warp 16, one lane)
     if (lane == 0) {
+      // N = 32 columns per term; BF16x3: A_hi [B_hi | B_lo] with N = 64 T,
+      // then A_lo B_hi into the first 32 T columns
+      const uint32_t id = idesc(TF32 ? 2u : 1u, 32u * (uint32_t)nterms);
+      const uint32_t id2 = idesc(1u, 64u * (uint32_t)nterms);
       for (int b = 0; b < nb; ++b) {
         if (s_abort) break;
         const int stg = b % kStages;
@@ -459,17 +521,16 @@ k_synth_tc(const SynthTcParams p) {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 4; ++ks) {
             const uint32_t ko = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
-            mma<true>(tmem, smem_desc_sw128(a0 + ko), smem_desc_sw128(bb0 + ko), (!fresh || ks > 0) ? 1u : 0u);
+            mma<true>(tmem, smem_desc_sw128(a0 + ko), smem_desc_sw128(bb0 + ko), id, (!fresh || ks > 0) ? 1u : 0u);
           }
         } else {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
             const uint32_t ko = (uint32_t)ks * 32u;
             const uint64_t ahi = smem_desc_sw128(a0 + ko), alo = smem_desc_sw128(a0 + lo_a + ko);
-            const uint64_t bhi = smem_desc_sw128(bb0 + ko), blo = smem_desc_sw128(bb0 + lo_b + ko);
-            mma<false>(tmem, alo, bhi, (!fresh || ks > 0) ? 1u : 0u);
-            mma<false>(tmem, ahi, blo, 1u);
-            mma<false>(tmem, ahi, bhi, 1u);
+            const uint64_t bhi = smem_desc_sw128(bb0 + ko);
+            mma<false>(tmem, ahi, bhi, id2, (!fresh || ks > 0) ? 1u : 0u);  // [hi x hi | hi x lo]
+            mma<false>(tmem, alo, bhi, id, 1u);                               // += lo x hi
           }
         }
         mma_commit(smem_u32(&s_empty[stg]));
@@ -494,7 +555,7 @@ k_synth_tc(const SynthTcParams p) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     have = __all_sync(0xffffffffu, have);
     float *acc = fold + my_row * kFoldStride;
-    if (have) fold_row(tmem, warp, my_sg, my_k2, my_k3, acc);
+    if (have) fold_row(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, acc);
     const int m = m0 + my_mi;
     if (my_mi < mvalid && my_h < p.HI) {
       float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
@@ -537,7 +598,7 @@ __global__ void k_tc_consts(const SynthTcParams p, float mu_max) {
     const double x = p.f0_c * (double)d;
     const float b1 = p.b1k * dd;
     cj[k] = make_float4((float)(x - floor(x)), p.c1k * dd, (float)(p.kb * (double)d), b1);
-    if (6.2831853f * fabsf(b1) * mu_max * (float)(kLO - 1) > 0.157f) bad = true;
+    if (6.2831853f * fabsf(b1) * mu_max * kLC > 0.157f) bad = true;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_TC_BOUND);
 }
@@ -612,7 +673,7 @@ int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int
 
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
-                            int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
+                            const int *order, int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
                             float4 *cst, const float *d_base, cudaStream_t st) {
   if (!cst) return cudaErrorInvalidValue;  // d_base may be null with no hits
   if (!synth_tc_supported(r) || n_jobs < 1) return cudaErrorInvalidValue;
@@ -630,6 +691,7 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
   p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
   p.partials = partials;
   p.jobs = jobs;
+  p.order = order;
   p.err = err;
   p.cst = cst;
   p.d_base = d_base;

@@ -344,16 +344,24 @@ k_batch_tiles(const FrameJob *__restrict__ table, int n_jobs, const RadarDev r, 
 }
 
 // Hit-list prefix of a batch: pre[j] = sum of min(count, cap) over frames
-// before j, pre[n_jobs] = total (one CTA of 1024 threads).
+// before j, pre[n_jobs] = total; and order[] = the frames by decreasing hit
+// count (ties by index), the launch order of the synthesis so that the
+// longest CTAs start first (one CTA of 1024 threads, n_jobs <= 4096).
 __global__ void __launch_bounds__(1024)
-k_batch_hit_prefix(const FrameJob *__restrict__ table, int n_jobs, int64_t *__restrict__ pre) {
+k_batch_hit_prefix(const FrameJob *__restrict__ table, int n_jobs, int64_t *__restrict__ pre,
+                   int *__restrict__ order) {
   __shared__ int64_t s_wsum[32];
+  __shared__ uint32_t s_cnt[RR_MAX_SCENES];
   const int per = (n_jobs + 1023) / 1024;
   const int j0 = threadIdx.x * per;
   int64_t local = 0;
   for (int k = 0; k < per; ++k) {
     const int j = j0 + k;
-    if (j < n_jobs) local += min((int64_t)*table[j].count, table[j].cap);
+    if (j < n_jobs) {
+      const int64_t c = min((int64_t)*table[j].count, table[j].cap);
+      local += c;
+      s_cnt[j] = (uint32_t)min(c, (int64_t)0xffffffff);
+    }
   }
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   int64_t incl = local;
@@ -382,6 +390,14 @@ k_batch_hit_prefix(const FrameJob *__restrict__ table, int n_jobs, int64_t *__re
     }
   }
   if (threadIdx.x == 1023) pre[n_jobs] = run;
+  if (order) {
+    for (int j = threadIdx.x; j < n_jobs; j += blockDim.x) {
+      const uint32_t cj = s_cnt[j];
+      int rank = 0;
+      for (int i = 0; i < n_jobs; ++i) rank += (s_cnt[i] > cj || (s_cnt[i] == cj && i < j)) ? 1 : 0;
+      order[rank] = j;
+    }
+  }
 }
 
 __device__ __forceinline__ int job_of_hit(const int64_t *__restrict__ pre, int n_jobs, int64_t h) {
@@ -498,7 +514,8 @@ cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64
 }
 
 cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix,
-                               const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2) {
+                               int *order, const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2) {
+  if (n_jobs > RR_MAX_SCENES) return cudaErrorInvalidValue;
   if (n_jobs <= 0) return cudaSuccess;
   const int sms = sm_count();
   FrameJob none = {};
@@ -508,7 +525,7 @@ cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, 
   k_trace<<<8 * sms, kTraceThreads, 0, st>>>(none, table, jt, n_jobs, r, tw_log2, err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_batch_hit_prefix<<<1, 1024, 0, st>>>(table, n_jobs, hit_prefix);
+  k_batch_hit_prefix<<<1, 1024, 0, st>>>(table, n_jobs, hit_prefix, order);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_echo<<<4 * sms, 128, 0, st>>>(none, table, hit_prefix, n_jobs, r);

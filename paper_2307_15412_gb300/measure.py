@@ -1,0 +1,210 @@
+"""Measurements of the workloads beside the benchmark's full frame.
+
+  python -m paper_2307_15412_gb300.measure batch      [--jobs 256] [--steps 5]
+  python -m paper_2307_15412_gb300.measure surrogate  [--train 200000] [--test 4096] [--epochs 40]
+  python -m paper_2307_15412_gb300.measure tiny       [--jobs 256] [--steps 5]
+
+batch: 256 independent seeded hand scenes, mesh sizes log-uniform in
+5k-50k triangles, ray grids drawn from {128^2, 256^2, 512^2, 1024^2} over
++-45 deg, 1 TX 3 RX, 32 chirps x 128 samples, one rr_batch_run per step
+(CUDA graph, autotuned) for each synthesis variant; frames/s from CUDA
+events, L2 flushed before each step.
+
+surrogate: the BF16 MLP 32-1024-1024-1024-6144 trained by the project's
+kernels on `train` frames the tracer generates (seeded parameters of the
+surrogate box), judged on `test` held-out frames against the tracer;
+inference throughput at batch 4096 from CUDA events.
+
+tiny: the ~2k-triangle hand at 0.30 m, 64 x 64 rays over +-30 deg, 1 TX
+1 RX, one chirp of 64 samples: one frame per rr_run_frame call (FP32
+synthesis, latency of a lone frame), and `jobs` seeded poses per
+rr_batch_run (CUDA graph, autotuned) for each synthesis variant.
+
+Each prints one JSON line.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import sys
+import time
+
+import numpy as np
+
+
+def _setup():
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    sys.path.insert(0, root)
+    import torch
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import inputs as I
+    from paper_2307_15412_gb300 import rr
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    return torch, I, rr, rr.Context(0, stream)
+
+
+def measure_batch(args):
+    torch, I, rr, ctx = _setup()
+    rng = np.random.default_rng(2024)
+    radar = I.Radar(n_samples=128, n_chirps=32, rx=I.rx_l_array())
+    half = math.radians(45.0)
+    tris = np.exp(rng.uniform(math.log(5000), math.log(50000), size=args.jobs)).astype(int)
+    sizes = rng.choice([128, 256, 512, 1024], size=args.jobs)
+    jobs = []
+    for k in range(args.jobs):
+        s = I.hand_scene(5000 + k, int(tris[k]), range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+        ctx.scene_upload(k, s.V, s.F, s.vel)
+        jobs.append((k, I.RayGrid(int(sizes[k]), int(sizes[k]), half, half)))
+    out = torch.empty((args.jobs, 3, 32, 128, 2), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    res = {}
+    for name, v in (("fp32", 0), ("tc_bf16x3", 1), ("tc_tf32", 2)):
+        for _ in range(3):
+            ctx.batch_run(jobs, radar, rd_out=out, variant=v, graph=True, autotune=True)
+        ctx.sync()
+        ctx.timing_enable(args.steps)
+        for _ in range(args.steps):
+            flush.zero_()
+            ctx.batch_run(jobs, radar, rd_out=out, variant=v, graph=True, autotune=True)
+        ctx.sync()
+        ms = np.array([ctx.timing_read(i)[4] for i in range(args.steps)])
+        ctx.timing_enable(0)
+        ctx.timing_enable(2)
+        for _ in range(2):
+            flush.zero_()
+            ctx.batch_run(jobs, radar, rd_out=out, variant=v, graph=False, autotune=True)
+        ctx.sync()
+        st = np.array([ctx.timing_read(i) for i in range(2)]).mean(0)
+        ctx.timing_enable(0)
+        res[name] = {"frames_per_s": args.jobs / (ms.mean() / 1e3), "ms_per_batch": float(ms.mean()),
+                     "stage_ms": {"build": float(st[0]), "trace": float(st[1]), "synth": float(st[2]),
+                                  "rd": float(st[3])}}
+    print(json.dumps({"workload": "batch: %d hand scenes, 5k-50k triangles log-uniform (total %d), grids "
+                                  "{128,256,512,1024}^2 over +-45 deg, 1 TX 3 RX, 32 chirps x 128 samples"
+                                  % (args.jobs, int(tris.sum())),
+                      "rays_total": int((sizes.astype(np.int64) ** 2).sum()), "results": res}))
+    ctx.close()
+
+
+def measure_surrogate(args):
+    torch, I, rr, ctx = _setup()
+    from paper_2307_15412_gb300 import surrogate as S
+    t0 = time.perf_counter()
+    raw_train = I.surrogate_inputs(7, args.train)
+    raw_test = I.surrogate_inputs(8, args.test)
+    t_train = S.frames(ctx, raw_train)
+    t_test = S.frames(ctx, raw_test)
+    gen_s = time.perf_counter() - t0
+    sur = S.Surrogate(ctx, seed=3)
+    t0 = time.perf_counter()
+    losses = sur.fit(raw_train, t_train, epochs=args.epochs, batch=512, seed=4, lr=args.lr, weight_decay=1e-4)
+    train_s = time.perf_counter() - t0
+    y, fb = sur.predict(raw_test)
+    err_c, err_m = S.rel_l2_rows(y, t_test)
+    mean = t_train.mean(dim=0, keepdim=True).expand_as(t_test).contiguous()
+    base_c, base_m = S.rel_l2_rows(mean, t_test)
+    # inference throughput at batch 4096 (device time)
+    xb = torch.from_numpy(I.surrogate_features(raw_test[:4096])).cuda()
+    yb = torch.empty((xb.shape[0], 6144), dtype=torch.float32, device="cuda")
+    for _ in range(3):
+        ctx.surrogate_infer(xb, yb)
+    ctx.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record()
+    for _ in range(20):
+        ctx.surrogate_infer(xb, yb)
+    e1.record()
+    torch.cuda.synchronize()
+    inf_ms = e0.elapsed_time(e1) / 20
+    # the tracer on the same frames (device time of the batched path, 256 per batch)
+    radar, grid = I.surrogate_radar_grid()
+    V, F, vel = I.surrogate_scenes(raw_test[:256])
+    for k in range(256):
+        ctx.scene_upload(1024 + k, V[k], F, vel[k])
+    rd = torch.empty((256, 3, 32, 32, 2), dtype=torch.float32, device="cuda")
+    jobs = [(1024 + k, grid) for k in range(256)]
+    for _ in range(3):
+        ctx.batch_run(jobs, radar, rd_out=rd, graph=True, autotune=True)
+    ctx.sync()
+    ctx.timing_enable(10)
+    for _ in range(10):
+        ctx.batch_run(jobs, radar, rd_out=rd, graph=True, autotune=True)
+    ctx.sync()
+    tr_ms = float(np.mean([ctx.timing_read(i)[4] for i in range(10)]))
+    ctx.timing_enable(0)
+    print(json.dumps({
+        "workload": "surrogate: BF16 MLP 32-1024-1024-1024-6144; %d training frames from the tracer, %d held out; "
+                    "frames of the tiny hand (64 x 64 rays), 1 TX 3 RX, 32 chirps x 32 samples, range-Doppler "
+                    "cube phase-referenced to RX 0" % (args.train, args.test),
+        "epochs": args.epochs, "loss_first_last": [losses[0], losses[-1]],
+        "held_out_rel_l2": {"complex_mean": float(err_c.mean()), "complex_median": float(np.median(err_c)),
+                            "magnitude_mean": float(err_m.mean()), "magnitude_median": float(np.median(err_m))},
+        "constant_mean_prediction_rel_l2": {"complex_mean": float(base_c.mean()), "magnitude_mean": float(base_m.mean())},
+        "fell_back": int(fb.sum().item()),
+        "inference_frames_per_s_batch4096": 4096 / (inf_ms / 1e3),
+        "tracer_frames_per_s_batch256": 256 / (tr_ms / 1e3),
+        "dataset_generation_s": gen_s, "training_s": train_s}))
+    ctx.close()
+
+
+def measure_tiny(args):
+    torch, I, rr, ctx = _setup()
+    radar, grid, nt = I.workload_tiny()
+    for k in range(args.jobs):
+        s = I.hand_scene(k, nt)
+        ctx.scene_upload(k, s.V, s.F, s.vel)
+    out = torch.empty((args.jobs, 1, 1, 64, 2), dtype=torch.float32, device="cuda")
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    for _ in range(3):
+        ctx.run_frame(0, radar, grid, if_out=out[0])
+    ctx.sync()
+    n1 = 200
+    e0.record()
+    for i in range(n1):
+        ctx.run_frame(i % args.jobs, radar, grid, if_out=out[i % args.jobs])
+    e1.record()
+    torch.cuda.synchronize()
+    single_ms = e0.elapsed_time(e1) / n1
+    jobs = [(k, grid) for k in range(args.jobs)]
+    res = {"single_frame_fp32": {"frames_per_s": 1e3 / single_ms, "ms_per_frame": single_ms}}
+    for name, v in (("fp32", 0), ("tc_bf16x3", 1), ("tc_tf32", 2)):
+        for _ in range(3):
+            ctx.batch_run(jobs, radar, if_out=out, variant=v, graph=True, autotune=True)
+        ctx.sync()
+        ctx.timing_enable(args.steps)
+        for _ in range(args.steps):
+            ctx.batch_run(jobs, radar, if_out=out, variant=v, graph=True, autotune=True)
+        ctx.sync()
+        ms = float(np.mean([ctx.timing_read(i)[4] for i in range(args.steps)]))
+        ctx.timing_enable(0)
+        res["batch_" + name] = {"frames_per_s": args.jobs / (ms / 1e3), "ms_per_batch": ms}
+    print(json.dumps({"workload": "tiny: ~2k-triangle hand at 0.30 m, 64x64 rays over +-30 deg, 1 TX 1 RX, one "
+                                  "64-sample chirp; single frames and batches of %d poses (inputs resident, "
+                                  "L2 not flushed: the whole batch fits in L2)" % args.jobs, "results": res}))
+    ctx.close()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("what", choices=["batch", "surrogate", "tiny"])
+    ap.add_argument("--jobs", type=int, default=256)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--train", type=int, default=200000)
+    ap.add_argument("--test", type=int, default=4096)
+    ap.add_argument("--epochs", type=int, default=40)
+    ap.add_argument("--lr", type=float, default=1e-3)
+    args = ap.parse_args()
+    if args.what == "batch":
+        measure_batch(args)
+    elif args.what == "tiny":
+        measure_tiny(args)
+    else:
+        measure_surrogate(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,119 @@
+"""GPU: precision of the IF synthesis variants over a hand trajectory.
+
+Workload: the ~2k-triangle hand of the tiny workload at 0.30 m, 8
+consecutive frames of a seeded joint-angle trajectory (the 27 angles move
+linearly from one U(0, 60 deg) draw to another), 1 TX 1 RX, one chirp of
+256 samples (split as t = 16 hi x 16 lo), 60 -> 64 GHz in 64 us.  Two ray
+grids: 64 x 64 over +-30 deg (the tiny workload's) and 512 x 512 over
++-20 deg (2^18 rays, so up to 2^18 hits per frame).  The GPU traces each
+frame; its hit list then goes through the three synthesis variants and
+through the FP64 oracle's direct sum (Eq. 4), so the comparison isolates
+the synthesis arithmetic.
+
+Bounds (rel-L2 over the chirp): FP32 1e-5 and split-BF16x3 1e-4 on every
+frame (the reasons are stated in the FP32 and tensor-core synthesis tests).
+TF32 keeps 11 significant bits: rounding a complex operand to nearest gives
+a relative error of rms 2^-11 / sqrt(3), so one product of two operands is
+off by sigma = sqrt(2/3) 2^-11 = 4.0e-4 rms, and a sum of K products with
+independent errors by sigma sqrt(sum_k |a_k|^2) per output.  Relative to
+the cube that is sigma rho with rho = sqrt(n_out sum_k |a_k|^2) / ||ref||,
+the incoherent over the coherent norm (about 1 for random phases, larger
+when the echoes cancel).  When the echoes add coherently (rho << 1: tens
+of thousands of hits at nearly one range) nearby operands round alike, the
+errors add coherently too and the relative error tends to sigma itself.
+A TF32 frame is held to 3 sigma max(1, rho), and the mean over the 8
+frames to 1e-3; single frames of a few hundred hits do exceed 1e-3
+(printed).
+
+The 64 x 64 frames are also traced by the oracle end to end (brute
+force), the FP32 frame held to 1e-3 (hit-set differences at silhouette
+edges allowed by the trace parity rule).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import rel_l2, to_complex, trace_scene
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+TOL = {0: 1e-5, 1: 1e-4, 2: 1e-3}
+SIGMA_TF32 = (2.0 / 3.0) ** 0.5 * 2.0 ** -11
+NAMES = {0: "fp32", 1: "tc_bf16x3", 2: "tc_tf32"}
+FRAMES = 8
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def trajectory(seed: int, n_frames: int, n_tri: int = 2000):
+    rng = np.random.default_rng(seed)
+    a0, a1 = I.random_hand_angles(rng), I.random_hand_angles(rng)
+    out = []
+    for f in range(n_frames):
+        ang = a0 + (a1 - a0) * f / max(n_frames - 1, 1)
+        out.append(I.hand_scene(0, n_tri, angles_deg=ang, center=(0.0, 0.0, 0.30)))
+    return out
+
+
+def _synth(ctx, radar, h, variant):
+    out = torch.empty((radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda:0")
+    ctx.synth_if_from_hits(radar, h["d_dev"], h["a_dev"], h["dd_dev"], out, variant=variant)
+    ctx.sync()
+    return to_complex(out)
+
+
+@pytest.mark.parametrize("n_rays,half_deg", [(64, 30.0), (512, 20.0)])
+def test_trajectory_precision_per_variant(ctx, n_rays, half_deg):
+    radar = I.Radar(n_samples=256, n_chirps=1, rx=((0.0, 0.0, 0.0),))
+    grid = I.RayGrid(n_rays, n_rays, math.radians(half_deg), math.radians(half_deg))
+    errs = {v: [] for v in TOL}
+    hits, rhos = [], []
+    for f, s in enumerate(trajectory(11, FRAMES)):
+        h = trace_scene(ctx, 600 + f, s, radar, grid)
+        K = h["d"].shape[1]
+        assert K > 0
+        hits.append(K)
+        ref = oracle.synth(h["d"], h["a"], h["dd"], radar)
+        rho = math.sqrt(ref.size * float(np.sum(h["a"].astype(np.float64) ** 2))) / np.linalg.norm(ref)
+        rhos.append(rho)
+        for v in TOL:
+            errs[v].append(rel_l2(_synth(ctx, radar, h, v), ref))
+    print("\nprecision, %dx%d rays over +-%g deg, 8 frames, hits %d..%d, rho %.2f..%.2f:"
+          % (n_rays, n_rays, half_deg, min(hits), max(hits), min(rhos), max(rhos)))
+    for v in TOL:
+        print("  %-10s rel-L2 vs FP64 oracle: max %.2e  mean %.2e  (bound %.0e)"
+              % (NAMES[v], max(errs[v]), float(np.mean(errs[v])), TOL[v]))
+    for v in (0, 1):
+        assert max(errs[v]) <= TOL[v], (NAMES[v], errs[v])
+    for e, rho in zip(errs[2], rhos):
+        assert e <= 3.0 * SIGMA_TF32 * max(1.0, rho), (e, rho)
+    assert float(np.mean(errs[2])) <= TOL[2], errs[2]
+
+
+def test_trajectory_tiny_frames_end_to_end(ctx):
+    """Config-1 frames (64-sample chirp, 64 x 64 rays) of the trajectory,
+    traced and synthesised on the GPU, against the oracle's whole frame."""
+    radar, grid, nt = I.workload_tiny()
+    for f, s in enumerate(trajectory(12, FRAMES, nt)):
+        ctx.scene_upload(620 + f, s.V, s.F, s.vel)
+        out = torch.empty((1, 1, 64, 2), dtype=torch.float32, device="cuda:0")
+        ctx.run_frame(620 + f, radar, grid, if_out=out)
+        ctx.sync()
+        ref = oracle.frame(s.V, s.F, s.vel, radar, grid)["if_cube"]
+        assert rel_l2(to_complex(out), ref) <= 1e-3

@@ -5,8 +5,9 @@ Tolerances (relative L2 over the cube, oracle fed the same float32 hits):
   * split-BF16x3: <= 1e-4.  Each operand is carried as bf16 hi + lo (about
     2^-17 relative representation error) and the dropped lo*lo product is
     below 2^-16 relative, so one term is off by ~1e-5 at most; the sum of K
-    terms of random phase keeps that order.  The first-order chirp-coupling
-    expansion adds < 5e-7 (its bound is checked on the device).
+    terms of random phase keeps that order.  The third-order chirp-coupling
+    expansion adds < x^4/24 relative, x <= 0.157 checked on the device
+    (< 2.6e-5; x grows with the chirps per 128-row tile and the path rate).
   * TF32: <= 1e-3 (the bound stated for the tensor-core variants).  Inputs
     are rounded to 10 explicit mantissa bits (2^-11 relative), so a product
     is off by up to ~1e-3 and the sum by ~2-5e-4 in rel-L2.
@@ -114,7 +115,8 @@ def test_tc_point_target_bins(ctx, variant):
 
 def test_tc_rejects_path_rates_beyond_the_expansion_bound(ctx):
     """A path rate of 1000 m/s moves the range inside a 32-chirp tile far
-    beyond the first-order bound: the device flags it, rr_sync reports."""
+    beyond the coupling expansion's bound: the device flags it, rr_sync
+    reports."""
     from paper_2307_15412_gb300 import rr
     radar = I.Radar(n_samples=64, n_chirps=32)
     d, a, dd = I.random_hits(3, 64, 1)
@@ -122,7 +124,7 @@ def test_tc_rejects_path_rates_beyond_the_expansion_bound(ctx):
     out = torch.empty((1, 32, 64, 2), dtype=torch.float32, device="cuda:0")
     dt = lambda x: torch.from_numpy(np.ascontiguousarray(x, np.float32)).cuda()
     ctx.synth_if_from_hits(radar, dt(d), dt(a), dt(dd), out, variant=1)
-    with pytest.raises(rr.RRError, match="first-order bound"):
+    with pytest.raises(rr.RRError, match="bound of the four-term expansion"):
         ctx.sync()
     ctx.sync()  # the error word was cleared
 
