@@ -33,7 +33,7 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 4;       // keys per thread and pass (cap <= 4096)
 constexpr int kCnt = 33;        // padded [digit][warp] counter row
-constexpr int kMaxCap = 3700;   // keys per CTA that fit the shared-memory plan below
+constexpr int kMaxCap = 4000;   // keys per CTA that fit the shared-memory plan below
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   v &= 0x3FFu;
@@ -52,12 +52,13 @@ __device__ __forceinline__ int exch_acq_rel_cluster(int *p, int v) {
   return old;
 }
 
-// Shared-memory plan (4-byte words): keyA[cap] idA[cap] | region R, where R
-// holds keyB[cap] idB[cap] cnt[256*33] dtot[16][256] during the sort and
-// nbox[12][cap] nflag[cap] hb[cap bytes] during the climb.  hb[x] is the
-// index of the highest bit in which the augmented keys at x and x + 1
-// differ; comparing two of them decides the parent (the two boundary
-// differences of a tree node never share their highest bit).
+// Shared-memory plan (4-byte words): idA[cap] keyA[cap] keyB[cap] idB[cap]
+// cnt[256*33] dtot[16][256] during the sort; during the climb the region
+// from keyA on holds nbox[12][cap] nflag[cap] hb[cap bytes] (the sorted keys
+// are dead once hb is computed, the ids stay).  hb[x] is the index of the
+// highest bit in which the augmented keys at x and x + 1 differ; comparing
+// two of them decides the parent (the two boundary differences of a tree
+// node never share their highest bit).
 struct Plan {
   uint32_t *keyA;
   int32_t *idA;
@@ -72,16 +73,17 @@ struct Plan {
 
 __device__ __forceinline__ Plan plan(uint32_t *base, int cap) {
   Plan p;
-  p.keyA = base;
-  p.idA = reinterpret_cast<int32_t *>(base + cap);
+  p.idA = reinterpret_cast<int32_t *>(base);
+  p.keyA = base + cap;
   uint32_t *R = base + 2 * cap;
   p.keyB = R;
   p.idB = reinterpret_cast<int32_t *>(R + cap);
   p.cnt = R + 2 * cap;
   p.dtot = p.cnt + 256 * kCnt;
-  p.nbox = reinterpret_cast<float *>(R);
-  p.nflag = reinterpret_cast<int32_t *>(R + 12 * cap);
-  p.hb = reinterpret_cast<uint8_t *>(R + 13 * cap);
+  uint32_t *H = base + cap;  // climb region, over keyA
+  p.nbox = reinterpret_cast<float *>(H);
+  p.nflag = reinterpret_cast<int32_t *>(H + 12 * cap);
+  p.hb = reinterpret_cast<uint8_t *>(H + 13 * cap);
   return p;
 }
 
@@ -374,9 +376,9 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
 int g_cluster_ok[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
 
 size_t smem_bytes(int cap) {
-  const size_t sortR = (size_t)2 * cap + 256 * kCnt + 16 * 256;
-  const size_t hierR = (size_t)13 * cap + (cap + 3) / 4;
-  return 4 * ((size_t)2 * cap + (sortR > hierR ? sortR : hierR));
+  const size_t sortR = (size_t)3 * cap + 256 * kCnt + 16 * 256;  // keyA, keyB, idB, cnt, dtot
+  const size_t hierR = (size_t)13 * cap + (cap + 3) / 4;          // nbox, nflag, hb
+  return 4 * ((size_t)cap + (sortR > hierR ? sortR : hierR));
 }
 
 // Whether this device runs 16-CTA clusters of the builder (checked once).
@@ -428,6 +430,47 @@ cudaError_t launch_clusters(const BuildJob &one, const BuildJob *table, int n_jo
 }  // namespace
 
 int cluster_build_capacity() { return 16 * kMaxCap; }
+
+int cluster_keys_per_cta() { return kMaxCap; }
+
+// Clusters of C CTAs (1024 threads, shared memory for kMaxCap keys) that can
+// be resident at once on this device: a cluster stays inside one GPC, so
+// this is not SMs / C (on 152 SMs, 15 clusters of 8).  Queried once per
+// device and size.
+int cluster_max_active(int C) {
+  static int cache[64][17] = {};
+  int dev = 0;
+  if (C < 1 || C > 16 || cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return 0;
+  if (cache[dev][C] == 0) {
+    cache[dev][C] = -1;
+    if (cluster_usable()) {
+      cudaLaunchConfig_t cfg = {};
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeClusterDimension;
+      attr[0].val.clusterDim.x = C;
+      attr[0].val.clusterDim.y = 1;
+      attr[0].val.clusterDim.z = 1;
+      cfg.gridDim = dim3(C * 64);
+      cfg.blockDim = dim3(kThreads);
+      cfg.dynamicSmemBytes = smem_bytes(kMaxCap);
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      int nc = 0;
+      if (cudaOccupancyMaxActiveClusters(&nc, k_build_cluster, &cfg) == cudaSuccess && nc > 0) cache[dev][C] = nc;
+      cudaGetLastError();
+    }
+  }
+  return cache[dev][C] > 0 ? cache[dev][C] : 0;
+}
+
+// Cluster size for the n_jobs meshes of a batch that need at least cmin
+// CTAs each (cmin <= 8): the largest size whose resident clusters hold all
+// of them at once (one wave, each mesh on as many CTAs as possible), else 8.
+int batch_cluster_size(int n_jobs, int cmin) {
+  for (int C = 8; C >= cmin && C >= 1; --C)
+    if (n_jobs <= cluster_max_active(C)) return C;
+  return 8;
+}
 
 bool cluster_build_usable() { return cluster_usable(); }
 

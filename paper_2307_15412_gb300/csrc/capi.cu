@@ -626,7 +626,8 @@ uint64_t fnv(uint64_t h, const void *p, size_t n) {
 // Everything a batch enqueues, decided on the host before any work is issued.
 struct BatchPlan {
   int n_jobs = 0;
-  int n8 = 0, n16 = 0;              // cluster-built frames (table order: 8-CTA group, 16-CTA group)
+  int n8 = 0, n16 = 0;              // cluster-built frames (table order: group of <= 8 CTAs, 16-CTA group)
+  int c_small = 8;                  // cluster size of the first group
   int max_cap8 = 0, max_cap16 = 0;
   std::vector<SceneDev *> others;   // frames built by the per-scene path (fewer than 2 or very many triangles)
   int64_t kmax = 0;                 // largest hit segment
@@ -665,7 +666,7 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
       (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) return e;
-  if (P.n8 && (e = rr::launch_build_bvh_cluster_table(b.btab, P.n8, 8, P.max_cap8, st)) != cudaSuccess) return e;
+  if (P.n8 && (e = rr::launch_build_bvh_cluster_table(b.btab, P.n8, P.c_small, P.max_cap8, st)) != cudaSuccess) return e;
   if (P.n16 && (e = rr::launch_build_bvh_cluster_table(b.btab + P.n8, P.n16, 16, P.max_cap16, st)) != cudaSuccess) return e;
   for (SceneDev *s : P.others)
     if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
@@ -758,6 +759,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   const bool clusters = rr::cluster_build_usable();
   BatchPlan P;
   P.n_jobs = n_jobs;
+  const int kpc = rr::cluster_keys_per_cta();
+  int cmin = 1;  // CTAs the largest mesh of the first group needs
   for (int j = 0; j < n_jobs; ++j) {
     if ((st = get_scene(c, jobs[j].scene, &sc[j])) != RR_OK) return st;
     if (seen[jobs[j].scene]) return fail(c, RR_EINVAL, "scene %d appears twice in the batch", jobs[j].scene);
@@ -771,10 +774,15 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
     const int n = (int)sc[j]->nt;
     const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
-    if (cl && rr::cluster_size_for(n, true) == 8) ++P.n8;
-    else if (cl) ++P.n16;
+    if (cl && rr::cluster_size_for(n, true) == 8) {
+      ++P.n8;
+      cmin = std::max(cmin, (n + kpc - 1) / kpc);
+    } else if (cl) {
+      ++P.n16;
+    }
     else P.others.push_back(sc[j]);
   }
+  if (P.n8) P.c_small = rr::batch_cluster_size(P.n8, cmin);
   const int64_t total = seg[n_jobs];
   const int n_rx = radar->n_rx;
   P.rd = to_dev(radar);
@@ -876,9 +884,10 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.h_ftab[j] = f;
     const int n = (int)s->nt;
     if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
-      const int C = rr::cluster_size_for(n, true);
+      const bool small = rr::cluster_size_for(n, true) == 8;
+      const int C = small ? P.c_small : 16;
       const rr::BuildJob bj = rr::build_job_for(*s, C);
-      if (C == 8) {
+      if (small) {
         b.h_btab[i8++] = bj;
         P.max_cap8 = std::max(P.max_cap8, bj.cap);
       } else {

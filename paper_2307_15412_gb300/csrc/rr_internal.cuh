@@ -141,6 +141,9 @@ bool cluster_build_usable();
 // Cluster size (8 or 16 CTAs) the builder uses for n triangles, for a single
 // frame or inside a batch.
 int cluster_size_for(int n, bool batch);
+int cluster_keys_per_cta();                  // keys one CTA of the cluster builder holds
+int cluster_max_active(int C);               // resident clusters of C builder CTAs (0 if unknown)
+int batch_cluster_size(int n_jobs, int cmin);
 BuildJob build_job_for(const SceneDev &s, int C);
 // One launch building every job of a device table, all with cluster size C
 // (jobs with cluster_size_for(n) == C) and dynamic shared memory for

@@ -162,32 +162,25 @@ def test_batch_rejects_bad_arguments(ctx):
     ctx.sync()
 
 
-@pytest.mark.parametrize("nt_target", [600, 20000, 28000, 50000])
-def test_batch_built_bvh_is_the_oracle_tree(ctx, nt_target):
-    """Inside a batch meshes up to 29 600 triangles are built by 8-CTA
-    clusters (up to 3700 keys per CTA), larger ones by 16: the sorted codes
-    and ids must still be the oracle's integers, every leaf box exact."""
+def _check_tree(ctx, scene_id, s, exact_topology):
+    """The batch-built LBVH of scene s: sorted codes and ids are the
+    oracle's integers, every leaf box is the triangle's exact box, and (for
+    small meshes) the topology is the oracle's."""
     from oracle import bvh as obvh
-    radar, grid, _ = I.workload_tiny()
-    s = I.hand_scene(90, nt_target)
     n = s.F.shape[0]
-    ctx.scene_upload(700, s.V, s.F, s.vel)
-    ctx.scene_upload(701, s.V, s.F, s.vel)
-    out = _cube(2, radar)
-    ctx.batch_run([(700, grid), (701, grid)], radar, if_out=out)
     codes = torch.empty(n, dtype=torch.int32, device="cuda:0")
     ids = torch.empty(n, dtype=torch.int32, device="cuda:0")
     left = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
     right = torch.empty(n - 1, dtype=torch.int32, device="cuda:0")
     boxes = torch.empty((n - 1, 12), dtype=torch.float32, device="cuda:0")
-    root = ctx.get_bvh(700, codes, ids, left, right, boxes)
+    root = ctx.get_bvh(scene_id, codes, ids, left, right, boxes)
     ctx.sync()
     ref_codes = obvh.morton_codes(s.V, s.F)
     order = obvh.sorted_order(ref_codes)
     g_ids = ids.cpu().numpy()
     assert np.array_equal(g_ids, order)
     assert np.array_equal(codes.cpu().numpy().view(np.uint32), ref_codes[order])
-    if n <= 5000:
+    if exact_topology:
         L, R, rl, rr_, rt = obvh.radix_tree(ref_codes[order])
         assert root[0] == rt
         assert np.array_equal(left.cpu().numpy(), L) and np.array_equal(right.cpu().numpy(), R)
@@ -200,5 +193,42 @@ def test_batch_built_bvh_is_the_oracle_tree(ctx, nt_target):
         lo = np.stack([bx[leaf, off + 0], bx[leaf, off + 2], bx[leaf, 8 + 2 * side]], 1)
         hi = np.stack([bx[leaf, off + 1], bx[leaf, off + 3], bx[leaf, 9 + 2 * side]], 1)
         assert np.array_equal(lo, tri_lo[tid]) and np.array_equal(hi, tri_hi[tid])
+
+
+@pytest.mark.parametrize("nt_target", [600, 20000, 28000, 50000])
+def test_batch_built_bvh_is_the_oracle_tree(ctx, nt_target):
+    """Inside a batch meshes up to 32 000 triangles are built by clusters
+    of at most 8 CTAs (up to 4000 keys per CTA), larger ones by 16: the
+    sorted codes and ids must still be the oracle's integers, every leaf box
+    exact."""
+    radar, grid, _ = I.workload_tiny()
+    s = I.hand_scene(90, nt_target)
+    ctx.scene_upload(700, s.V, s.F, s.vel)
+    ctx.scene_upload(701, s.V, s.F, s.vel)
+    out = _cube(2, radar)
+    ctx.batch_run([(700, grid), (701, grid)], radar, if_out=out)
+    _check_tree(ctx, 700, s, s.F.shape[0] <= 5000)
     g = to_complex(out)
     assert rel_l2(g[1], g[0]) <= 1e-5  # same mesh twice: same frame
+
+
+def test_batch_of_sixteen_full_frames_in_one_wave(ctx):
+    """Sixteen ~22.9k-triangle meshes: more clusters of 8 CTAs than can be
+    resident at once (15 on 152 SMs), so the batch builds them on smaller
+    clusters (6 CTAs, up to 3817 keys each) in one wave.  Every tree must
+    still be the oracle's; the frames must match single-frame runs."""
+    radar, grid, nt = I.workload_full_frame()
+    radar = I.Radar(n_samples=64, n_chirps=8, rx=I.rx_l_array())
+    grid = I.RayGrid(128, 128, grid.half_az, grid.half_el)
+    scenes = [I.hand_scene(300 + k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED) for k in range(16)]
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(720 + k, s.V, s.F, s.vel)
+    out = _cube(16, radar)
+    ctx.batch_run([(720 + k, grid) for k in range(16)], radar, if_out=out)
+    ctx.sync()
+    for k in (0, 7, 15):
+        _check_tree(ctx, 720 + k, scenes[k], False)
+    got = to_complex(out)
+    for k in (0, 15):
+        si, _ = _single(ctx, 720 + k, radar, grid)
+        assert rel_l2(got[k], si) <= 1e-5
