@@ -33,7 +33,7 @@ constexpr int kThreads = 1024;
 constexpr int kWarps = kThreads / 32;
 constexpr int kItems = 4;       // keys per thread and pass (cap <= 4096)
 constexpr int kCnt = 33;        // padded [digit][warp] counter row
-constexpr int kMaxCap = 4000;   // keys per CTA that fit the shared-memory plan below
+constexpr int kMaxCap = 3840;   // keys per CTA that fit the shared-memory plan below
 
 __device__ __forceinline__ uint32_t spread10(uint32_t v) {
   v &= 0x3FFu;
@@ -52,13 +52,26 @@ __device__ __forceinline__ int exch_acq_rel_cluster(int *p, int v) {
   return old;
 }
 
+// The same at CTA scope, for nodes whose two subtrees both lie in this CTA's
+// key block (both climbing threads belong to this CTA).
+__device__ __forceinline__ int exch_acq_rel_cta(int *p, int v) {
+  int old;
+  asm volatile("atom.acq_rel.cta.exch.b32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+  return old;
+}
+
 // Shared-memory plan (4-byte words): idA[cap] keyA[cap] keyB[cap] idB[cap]
 // cnt[256*33] dtot[16][256] during the sort; during the climb the region
-// from keyA on holds nbox[12][cap] nflag[cap] hb[cap bytes] (the sorted keys
-// are dead once hb is computed, the ids stay).  hb[x] is the index of the
-// highest bit in which the augmented keys at x and x + 1 differ; comparing
-// two of them decides the parent (the two boundary differences of a tree
-// node never share their highest bit).
+// from keyA on holds nbox[12][cap] nflag[cap] and the bytes hb[cap]
+// pref[cap] suf[cap] (the sorted keys are dead once hb is computed, the ids
+// stay).  hb[x] is the index of the highest bit in which the augmented keys
+// at x and x + 1 differ; comparing two of them decides the parent (the two
+// boundary differences of a tree node never share their highest bit).  The
+// tree is the max-Cartesian tree of hb, so node p spans the leaves between
+// the nearest boundaries on either side with a larger hb: with pref / suf
+// the largest hb + 1 of this block's boundaries before / after p (255 past
+// either end of the keys, 0 for none), p lies inside the block iff both
+// exceed hb[p] + 1.
 struct Plan {
   uint32_t *keyA;
   int32_t *idA;
@@ -69,6 +82,8 @@ struct Plan {
   float *nbox;
   int32_t *nflag;
   uint8_t *hb;
+  uint8_t *pref;
+  uint8_t *suf;
 };
 
 __device__ __forceinline__ Plan plan(uint32_t *base, int cap) {
@@ -84,6 +99,8 @@ __device__ __forceinline__ Plan plan(uint32_t *base, int cap) {
   p.nbox = reinterpret_cast<float *>(H);
   p.nflag = reinterpret_cast<int32_t *>(H + 12 * cap);
   p.hb = reinterpret_cast<uint8_t *>(H + 13 * cap);
+  p.pref = p.hb + cap;
+  p.suf = p.pref + cap;
   return p;
 }
 
@@ -310,8 +327,63 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
 
   auto hb_at = [&](int x) -> int {
     const int r = x / cap;
-    return *cluster.map_shared_rank(&P.hb[x - r * cap], r);
+    return r == crank ? P.hb[x - first] : *cluster.map_shared_rank(&P.hb[x - r * cap], r);
   };
+
+  // block maxima of hb + 1 before / after each boundary (4 consecutive
+  // boundaries per thread; the last key of the mesh ends every range)
+  {
+    uint32_t hv[kItems];
+    uint32_t agg = 0;
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const int e = kItems * tid + q;
+      hv[q] = e < mine ? (first + e < n - 1 ? (uint32_t)P.hb[e] + 1u : 255u) : 0u;
+      agg = max(agg, hv[q]);
+    }
+    // exclusive prefix maximum over threads, seeded with the boundary before the block
+    uint32_t inc = agg;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, o);
+      if (lane >= o) inc = max(inc, t);
+    }
+    if (lane == 31) s_wsum[warp] = inc;
+    __syncthreads();
+    uint32_t run = first == 0 ? 255u : (uint32_t)hb_at(first - 1) + 1u;
+    for (int w = 0; w < warp; ++w) run = max(run, s_wsum[w]);
+    {
+      const uint32_t t = __shfl_up_sync(0xffffffffu, inc, 1);
+      if (lane > 0) run = max(run, t);
+    }
+#pragma unroll
+    for (int q = 0; q < kItems; ++q) {
+      const int e = kItems * tid + q;
+      if (e < cap) P.pref[e] = (uint8_t)run;
+      run = max(run, hv[q]);
+    }
+    __syncthreads();
+    // exclusive suffix maximum (boundaries after the block's last one do not count)
+    inc = agg;
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t t = __shfl_down_sync(0xffffffffu, inc, o);
+      if (lane + o < 32) inc = max(inc, t);
+    }
+    if (lane == 0) s_wsum[warp] = inc;
+    __syncthreads();
+    run = 0u;
+    for (int w = warp + 1; w < kWarps; ++w) run = max(run, s_wsum[w]);
+    {
+      const uint32_t t = __shfl_down_sync(0xffffffffu, inc, 1);
+      if (lane < 31) run = max(run, t);
+    }
+#pragma unroll
+    for (int q = kItems - 1; q >= 0; --q) {
+      const int e = kItems * tid + q;
+      if (e < cap) P.suf[e] = (uint8_t)run;
+      run = max(run, hv[q]);
+    }
+    __syncthreads();
+  }
 
   for (int e = tid; e < mine; e += kThreads) {
     const int i = first + e;
@@ -343,16 +415,23 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
         reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
         np->kids.y = cur;
       }
-      // this child's box for the sibling, in the parent's owner CTA
+      // this child's box for the sibling, in the parent's owner CTA; a
+      // parent inside this CTA's block synchronises at CTA scope
       const int owner = p / cap, slot = p - owner * cap;
       const int side = as_left ? 0 : 1;
-      float *nb = cluster.map_shared_rank(P.nbox, owner);
+      bool local = false;
+      if (owner == crank) {
+        const uint32_t hp = (uint32_t)P.hb[slot] + 1u;
+        local = P.pref[slot] > hp && P.suf[slot] > hp;
+      }
+      float *nb = local ? P.nbox : cluster.map_shared_rank(P.nbox, owner);
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         nb[(side * 6 + x) * cap + slot] = bl[x];
         nb[(side * 6 + 3 + x) * cap + slot] = bh[x];
       }
-      const int other = exch_acq_rel_cluster(cluster.map_shared_rank(&P.nflag[slot], owner), as_left ? l : r);
+      const int other = local ? exch_acq_rel_cta(&P.nflag[slot], as_left ? l : r)
+                              : exch_acq_rel_cluster(cluster.map_shared_rank(&P.nflag[slot], owner), as_left ? l : r);
       if (other < 0) break;  // first to arrive: the sibling's thread goes on
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
@@ -377,7 +456,7 @@ int g_cluster_ok[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
 
 size_t smem_bytes(int cap) {
   const size_t sortR = (size_t)3 * cap + 256 * kCnt + 16 * 256;  // keyA, keyB, idB, cnt, dtot
-  const size_t hierR = (size_t)13 * cap + (cap + 3) / 4;          // nbox, nflag, hb
+  const size_t hierR = (size_t)13 * cap + (3 * cap + 3) / 4;      // nbox, nflag, hb, pref, suf
   return 4 * ((size_t)cap + (sortR > hierR ? sortR : hierR));
 }
 
