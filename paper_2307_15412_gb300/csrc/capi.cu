@@ -39,6 +39,8 @@ struct rr_ctx {
   int64_t tc_cst_cap = 0;
   float *if_tmp = nullptr;         // internal IF cube for rr_run_frame(if_out = NULL)
   int64_t if_tmp_cap = 0;          // floats
+  double2 *dir = nullptr;          // FP64 ray-direction table of the last single-frame trace
+  int64_t dir_cap = 0;
   // batches (rr_batch_run): hit-list segments, tables and scratch
   struct Batch {
     int32_t *ray = nullptr, *tri = nullptr, *pos = nullptr;
@@ -59,6 +61,8 @@ struct rr_ctx {
     int64_t if_tmp_cap = 0;
     float4 *tc_cst = nullptr;               // per-hit constants, laid out like d (tc_cst_rows rows of cap)
     int tc_cst_rows = 0;
+    double2 *dir = nullptr;                 // FP64 ray-direction tables (n_az + n_el per frame)
+    int64_t dir_cap = 0;
     // CUDA graph of the last batch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
@@ -266,11 +270,12 @@ rr_status rr_destroy(rr_ctx *c) {
   if (c->partials) cudaFree(c->partials);
   if (c->if_tmp) cudaFree(c->if_tmp);
   if (c->tc_cst) cudaFree(c->tc_cst);
+  if (c->dir) cudaFree(c->dir);
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   {
     auto &b = c->batch;
     void *dev[] = {b.ray, b.tri, b.pos, b.t, b.d, b.a, b.dd, b.counts, b.ftab, b.btab, b.jt, b.prefix,
-                   b.partials, b.if_tmp, b.tc_cst};
+                   b.partials, b.if_tmp, b.tc_cst, b.dir};
     for (void *p : dev)
       if (p) cudaFree(p);
     if (b.h_ftab) cudaFreeHost(b.h_ftab);
@@ -430,7 +435,8 @@ rr_status rr_trace_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_r
   }
   const rr::RadarDev rd = to_dev(radar);
   const rr::GridDev gd = to_dev(grid);
-  RR_CUDA(c, rr::launch_trace(*s, rd, gd, cap, c->d_err, c->stream), "trace launch");
+  RR_CUDA(c, grow(c->dir, c->dir_cap, (int64_t)grid->n_az + grid->n_el), "ray-direction table");
+  RR_CUDA(c, rr::launch_trace(*s, rd, gd, cap, c->dir, c->d_err, c->stream), "trace launch");
   s->hit_nrx = radar->n_rx;
   s->hit_used_cap = cap;
   s->traced = true;
@@ -756,6 +762,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   std::vector<char> seen(RR_MAX_SCENES, 0);
   std::vector<SceneDev *> sc(n_jobs);
   std::vector<int64_t> seg(n_jobs + 1, 0);
+  std::vector<int64_t> dseg(n_jobs + 1, 0);  // ray-direction table segments
   const bool clusters = rr::cluster_build_usable();
   BatchPlan P;
   P.n_jobs = n_jobs;
@@ -771,6 +778,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     if (!(gr.half_az > 0 && gr.half_az < M_PI) || !(gr.half_el > 0 && gr.half_el < 0.5 * M_PI))
       return fail(c, RR_EINVAL, "job %d: ray grid half angles out of range", j);
     seg[j + 1] = seg[j] + (int64_t)gr.n_az * gr.n_el;
+    dseg[j + 1] = dseg[j] + (int64_t)gr.n_az + gr.n_el;
     P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
     const int n = (int)sc[j]->nt;
     const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
@@ -865,6 +873,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     for (int sp : {0, 1, 2, 4}) need = std::max(need, batch_partials_need(P, sp));
   if (need > b.partials_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
   RR_CUDA(c, grow(b.partials, b.partials_cap, need), "batch partials");
+  if (dseg[n_jobs] > b.dir_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  RR_CUDA(c, grow(b.dir, b.dir_cap, dseg[n_jobs]), "batch ray-direction tables");
 
   // device tables, staged in pinned memory (wait until the last copy out of it is done)
   RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
@@ -881,6 +891,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     f.hit_d = b.d + seg[j];
     f.hit_a = b.a + seg[j];
     f.hit_dd = b.dd + seg[j];
+    f.dir = b.dir + dseg[j];
     b.h_ftab[j] = f;
     const int n = (int)s->nt;
     if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {

@@ -121,13 +121,16 @@ struct FrameJob {
   uint32_t *count;   // the frame's hit counter (true count, may exceed cap)
   int32_t *hit_ray, *hit_tri, *hit_pos;
   float *hit_t, *hit_d, *hit_a, *hit_dd;
+  // (sin, cos) in FP64 of the grid's azimuths [n_az] then elevations [n_el],
+  // written by the trace launch, read by the echo
+  double2 *dir;
 };
 
 // Per-frame tile numbering of a batched trace (written on the device).
 struct JobTiles {
   int rect[4];  // candidate rays [rect0, rect1) x [rect2, rect3) (azimuth x elevation index)
   int tile0;    // first global tile of the frame; entry n_jobs holds the total
-  int pad;
+  int next;     // entry n_jobs: the next tile a warp takes (zeroed by the numbering scan)
 };
 
 // ---- launchers (each returns the launch status) ----
@@ -152,12 +155,14 @@ cudaError_t launch_build_bvh_cluster_table(const BuildJob *table, int n_jobs, in
                                            cudaStream_t st);
 FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap);
 // tw_log2: log2 of the ray-tile width in azimuth (tiles are 2^tw_log2 x 2^(5 - tw_log2))
-cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
+// dir: device double2[n_az + n_el] for the ray-direction table.
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
                          uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 // Trace + echo of n_jobs frames in three launches plus two one-CTA scans.
 // table: device FrameJob[n_jobs] (counters zeroed by the caller); jt: device
 // JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1]; order (may be
 // null): device int[n_jobs], filled with the frames by decreasing hit count.
+// Each table entry's dir must hold n_az + n_el entries.
 cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix, int *order,
                                const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,

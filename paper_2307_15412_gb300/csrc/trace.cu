@@ -8,14 +8,21 @@
 //          leaf triangle is tested with the watertight ray-triangle test of
 //          Woop, Benthin and Wald (JCGT 2013).  Faces are two-sided; equal
 //          distances keep the lowest triangle id.  Hits are appended to the
-//          hit list with one atomic per warp.
+//          hit list with one atomic per warp.  A warp traces a tile of 32
+//          rays and takes the next tile from a counter when it is done
+//          (tiles differ a lot in cost: a silhouette tile walks deep); the
+//          persistent grid fills every resident CTA slot.  As a side job
+//          its CTAs write each frame's table of FP64 (sin, cos) of the grid
+//          azimuths and elevations for the echo.
 // k_echo   one thread per hit: the hit distance is recomputed in FP64 from
-//          the triangle's plane and the exact ray direction (FP32 traversal
-//          decides *which* triangle; FP64 fixes *where*, so distances agree
-//          with an FP64 reference to ~1e-15 even at grazing incidence), then
-//          the echo per receive antenna (Sec. III-A material model, Eq. 1-3
-//          as expected lobes; Sec. III-B path length): d_j = t + |p - rx_j|,
-//          a_j = Omega g_j / (t r_j), d-dot_j = v . (u + u_j).
+//          the triangle's plane and the exact ray direction (from the
+//          table; FP32 traversal decides *which* triangle, FP64 fixes
+//          *where*, so distances agree with an FP64 reference to ~1e-15
+//          even at grazing incidence), then the echo per receive antenna in
+//          FP32 (Sec. III-A material model, Eq. 1-3 as expected lobes;
+//          Sec. III-B path length): d_j = t + |p - rx_j|, a_j = Omega g_j /
+//          (t r_j), d-dot_j = v . (u + u_j).  FP64 is slow on this part, so
+//          it is kept to the plane intersection.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -159,8 +166,24 @@ __device__ __forceinline__ int job_of_tile(const JobTiles *__restrict__ jt, int 
 
 __global__ void __launch_bounds__(kTraceThreads)
 k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *__restrict__ jt, int n_jobs,
-        const RadarDev r, int tw_log2, uint32_t *__restrict__ err) {
+        const RadarDev r, int tw_log2, int *__restrict__ next_tile, uint32_t *__restrict__ err) {
   __shared__ int rect1[4];
+  // side job for the echo: the FP64 (sin, cos) of every azimuth and
+  // elevation of each frame's grid (cpj CTAs per frame)
+  {
+    const int cpj = max(1, (int)gridDim.x / n_jobs), slots = (int)gridDim.x / cpj;
+    if ((int)blockIdx.x < slots * cpj)
+      for (int j = (int)blockIdx.x / cpj; j < n_jobs; j += slots) {
+        const FrameJob &J = table ? table[j] : one;
+        const int na = J.g.n_az, ne = J.g.n_el;
+        for (int e = ((int)blockIdx.x % cpj) * (int)blockDim.x + (int)threadIdx.x; e < na + ne; e += cpj * (int)blockDim.x) {
+          const double ang = e < na ? -J.g.half_az + J.g.daz * ((e) + 0.5) : -J.g.half_el + J.g.del * ((e - na) + 0.5);
+          double sv, cv;
+          sincos(ang, &sv, &cv);
+          J.dir[e] = make_double2(sv, cv);
+        }
+      }
+  }
   int total;
   if (!table) {  // one frame: every CTA derives the candidate rectangle itself
     if (one.hdr->n <= 0) return;
@@ -172,9 +195,13 @@ k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *
   }
   const int lane = threadIdx.x & 31;
   const int tw = 1 << tw_log2;
-  const int gw = blockIdx.x * (kTraceThreads / 32) + (threadIdx.x >> 5);
-  const int nw = gridDim.x * (kTraceThreads / 32);
-  for (int tile = gw; tile < total; tile += nw) {
+  // tiles are handed out one at a time to whichever warp is free
+  auto take_tile = [&]() {
+    int t = 0;
+    if (lane == 0) t = atomicAdd(next_tile, 1);
+    return __shfl_sync(0xffffffffu, t, 0);
+  };
+  for (int tile = take_tile(); tile < total; tile = take_tile()) {
     const int job = table ? job_of_tile(jt, n_jobs, tile) : 0;
     const FrameJob &J = table ? table[job] : one;
     const int *rect = table ? jt[job].rect : rect1;
@@ -310,6 +337,7 @@ k_batch_tiles(const FrameJob *__restrict__ table, int n_jobs, const RadarDev r, 
       int rc[4] = {0, 0, 0, 0};
       if (table[j].hdr->n > 0) ray_rect(table[j].hdr, r, table[j].g, rc);
       for (int q = 0; q < 4; ++q) jt[j].rect[q] = rc[q];
+      jt[j].next = 0;
       local += tiles_of(rc, tw_log2);
     }
   }
@@ -340,7 +368,10 @@ k_batch_tiles(const FrameJob *__restrict__ table, int n_jobs, const RadarDev r, 
       run += tiles_of(jt[j].rect, tw_log2);
     }
   }
-  if (threadIdx.x == 1023) jt[n_jobs].tile0 = run;
+  if (threadIdx.x == 1023) {
+    jt[n_jobs].tile0 = run;
+    jt[n_jobs].next = 0;
+  }
 }
 
 // Hit-list prefix of a batch: pre[j] = sum of min(count, cap) over frames
@@ -421,11 +452,8 @@ k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__
     const int pos = J.hit_pos[hl];
     const int i_el = ray / J.g.n_az, i_az = ray - i_el * J.g.n_az;
     // exact ray direction (FP64), as the grid defines it
-    const double az = -J.g.half_az + J.g.daz * (i_az + 0.5);
-    const double el = -J.g.half_el + J.g.del * (i_el + 0.5);
-    double sa, ca, se, ce;
-    sincos(az, &sa, &ca);
-    sincos(el, &se, &ce);
+    const double2 scA = J.dir[i_az], scE = J.dir[J.g.n_az + i_el];
+    const double sa = scA.x, ca = scA.y, se = scE.x, ce = scE.y;
     const double ur[3] = {ce * sa, se, ce * ca};
     double u[3];
 #pragma unroll
@@ -450,11 +478,13 @@ k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__
     // Eq. 2 mirror direction u - 2 (u . n_f) n_f
     const float mr[3] = {uf[0] + 2.f * ci * nf[0], uf[1] + 2.f * ci * nf[1], uf[2] + 2.f * ci * nf[2]};
     const float omega = (float)(ce * J.g.daz * J.g.del);
+    const float tf = (float)t;
     for (int j = 0; j < r.n_rx; ++j) {
-      const double w[3] = {p[0] - r.rx[j][0], p[1] - r.rx[j][1], p[2] - r.rx[j][2]};
-      const double rj = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-      const float irf = (float)(1.0 / rj);
-      const float uj[3] = {(float)w[0] * irf, (float)w[1] * irf, (float)w[2] * irf};
+      // hit -> RX j in FP32 (the difference taken in FP64): about 1e-7 relative
+      const float w[3] = {(float)(p[0] - r.rx[j][0]), (float)(p[1] - r.rx[j][1]), (float)(p[2] - r.rx[j][2])};
+      const float rj = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+      const float irf = 1.f / rj;
+      const float uj[3] = {w[0] * irf, w[1] * irf, w[2] * irf};
       const float co = -(uj[0] * nf[0] + uj[1] * nf[1] + uj[2] * nf[2]);
       float gj = 0.f;
       if (co > 0.f) {
@@ -463,11 +493,24 @@ k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__
         gj = (1.f - r.alpha) * s + r.alpha * (ci * co);
       }
       const int64_t o = (int64_t)j * J.ld + hl;
-      J.hit_d[o] = (float)(t + rj);
-      J.hit_a[o] = r.amp_mode == 1 ? 1.f : (float)((double)omega * gj / (t * rj));
+      J.hit_d[o] = (float)(t + (double)rj);
+      J.hit_a[o] = r.amp_mode == 1 ? 1.f : omega * gj / (tf * rj);
       J.hit_dd[o] = J.vel[0] * (uf[0] + uj[0]) + J.vel[1] * (uf[1] + uj[1]) + J.vel[2] * (uf[2] + uj[2]);
     }
   }
+}
+
+// Resident CTAs of the traversal kernel per SM (its register use decides),
+// queried once: the persistent grid fills every slot.
+int trace_ctas_per_sm() {
+  static int cached = 0;
+  if (cached == 0) {
+    int nb = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, k_trace, kTraceThreads, 0) != cudaSuccess || nb < 1) nb = 8;
+    cudaGetLastError();
+    cached = nb;
+  }
+  return cached;
 }
 
 int sm_count() {
@@ -495,16 +538,21 @@ FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap) {
   j.hit_d = s.hit_d;
   j.hit_a = s.hit_a;
   j.hit_dd = s.hit_dd;
+  j.dir = nullptr;
   return j;
 }
 
-cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap,
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
                          uint32_t *err, cudaStream_t st, int tw_log2) {
-  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, sizeof(uint32_t), st);
+  if (!dir) return cudaErrorInvalidValue;
+  // hit counter and tile counter
+  cudaError_t e = cudaMemsetAsync(s.hit_count, 0, 2 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
   const int sms = sm_count();
-  const FrameJob one = frame_job_for(s, g, cap);
-  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(one, nullptr, nullptr, 1, r, tw_log2, err);
+  FrameJob one = frame_job_for(s, g, cap);
+  one.dir = dir;
+  k_trace<<<trace_ctas_per_sm() * sms, kTraceThreads, 0, st>>>(one, nullptr, nullptr, 1, r, tw_log2,
+                                                               reinterpret_cast<int *>(s.hit_count + 1), err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   const int64_t want = (cap + 127) / 128;
@@ -522,7 +570,8 @@ cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, 
   k_batch_tiles<<<1, 1024, 0, st>>>(table, n_jobs, r, tw_log2, jt);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_trace<<<8 * sms, kTraceThreads, 0, st>>>(none, table, jt, n_jobs, r, tw_log2, err);
+  k_trace<<<trace_ctas_per_sm() * sms, kTraceThreads, 0, st>>>(none, table, jt, n_jobs, r, tw_log2, &jt[n_jobs].next,
+                                                               err);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
   k_batch_hit_prefix<<<1, 1024, 0, st>>>(table, n_jobs, hit_prefix, order);
