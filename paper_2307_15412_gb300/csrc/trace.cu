@@ -33,6 +33,7 @@ namespace rr {
 namespace {
 
 constexpr int kTraceThreads = 128;        // 4 warps, each tracing 8 x 4 ray tiles
+constexpr int kPend = 4;                  // leaves a lane may queue before the warp tests them
 constexpr float kBoxSlack = 1.0000004f;   // covers FP32 rounding of the slab test
 
 struct RayPre {
@@ -146,9 +147,8 @@ __device__ void ray_rect(const BvhHeader *hdr, const RadarDev &r, const GridDev 
 // Ray tiles: a warp traces one tile of TW x (32 / TW) neighbouring rays of
 // one frame (TW = 1 << tw_log2, chosen by the autotuner).  Tiles of a frame
 // cover only its candidate rectangle; the tiles of all frames of a launch
-// are numbered consecutively (JobTiles::tile0) and taken by the warps in a
-// fixed interleaved order, so the few tiles that contain an object are
-// spread over every SM.
+// are numbered consecutively (JobTiles::tile0) and handed to the warps one
+// at a time from a counter.
 __device__ __forceinline__ int tiles_of(const int *rect, int tw_log2) {
   const int tw = 1 << tw_log2, th = 32 >> tw_log2;
   return ((rect[1] - rect[0] + tw - 1) / tw) * ((rect[3] - rect[2] + th - 1) / th);
@@ -245,20 +245,40 @@ k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *
         else active = true;
       }
     }
-    // Warp-uniform traversal: every iteration each still-active lane takes
-    // one node step and the warp reconverges at the vote, so a warp costs
-    // the longest of its rays' walks, not the sum of its lanes' walks (a
-    // per-lane loop lets divergent lanes run their iterations one after the
-    // other).  A tree of n - 1 internal nodes is walked in at most n - 1
+    // Warp-uniform traversal with postponed leaves (the while-while scheme
+    // of Aila and Laine, HPG 2009): each lane walks internal nodes and queues
+    // the leaves whose boxes it enters (up to kPend); the warp runs the
+    // triangle tests only when at least half of its working lanes have
+    // leaves queued or no lane can take a node step, so the long triangle
+    // test runs with most lanes busy instead of for one lane at a time.
+    // Every iteration ends at the votes, so a warp costs the longest of its
+    // rays' walks, not the sum of its lanes' walks.  Pruning uses the best
+    // distance found so far (a bound on the final one) and equal distances
+    // keep the lowest id, so the hit does not depend on the order of the
+    // tests.  A tree of n - 1 internal nodes is walked in at most n - 1 node
     // steps; more means a malformed tree, reported instead of looping.
     int stack_node[kStackDepth];
     float stack_t[kStackDepth];
-    int sp = 0, node = root, visits = 0;
-    while (__any_sync(0xffffffffu, active)) {
-      if (!active) continue;
+    int sp = 0, node = active ? root : -1, visits = 0;
+    int p0 = 0, p1 = 0, p2 = 0, p3 = 0, np = 0;  // queued leaf positions (kPend = 4)
+    while (true) {
+      const bool can_step = node >= 0 && np <= kPend - 2;
+      const uint32_t working = __ballot_sync(0xffffffffu, node >= 0 || np > 0);
+      if (working == 0u) break;
+      const uint32_t queued = __ballot_sync(0xffffffffu, np > 0);
+      const uint32_t steppers = __ballot_sync(0xffffffffu, can_step);
+      if (steppers == 0u || 2 * __popc(queued) >= __popc(working)) {
+        if (np > 0) tri_test(rp, J.tris, p0, best_t, best_pos, best_id);
+        if (np > 1) tri_test(rp, J.tris, p1, best_t, best_pos, best_id);
+        if (np > 2) tri_test(rp, J.tris, p2, best_t, best_pos, best_id);
+        if (np > 3) tri_test(rp, J.tris, p3, best_t, best_pos, best_id);
+        np = 0;
+        continue;
+      }
+      if (!can_step) continue;
       if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) {
         atomicOr(err, ERR_BAD_INPUT);
-        active = false;
+        node = -1; np = 0; sp = 0;
         continue;
       }
       ++visits;
@@ -271,16 +291,26 @@ k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *
       bool hl = tl < INFINITY, hr = tr < INFINITY;
       if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
         atomicOr(err, ERR_BAD_INPUT);
-        active = false;
+        node = -1; np = 0; sp = 0;
         continue;
       }
-      if (hl && kids.x < 0) { tri_test(rp, J.tris, ~kids.x, best_t, best_pos, best_id); hl = false; }
-      if (hr && kids.y < 0) { tri_test(rp, J.tris, ~kids.y, best_t, best_pos, best_id); hr = false; }
+      if (hl && kids.x < 0) {
+        const int q = ~kids.x;
+        if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
+        ++np;
+        hl = false;
+      }
+      if (hr && kids.y < 0) {
+        const int q = ~kids.y;
+        if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
+        ++np;
+        hr = false;
+      }
       if (hl && hr) {
         const bool lnear = tl <= tr;
         if (sp == kStackDepth) {
           atomicOr(err, ERR_STACK_OVERFLOW);
-          active = false;
+          node = -1; np = 0; sp = 0;
           continue;
         }
         stack_node[sp] = lnear ? kids.y : kids.x;
@@ -292,12 +322,11 @@ k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *
       } else if (hr) {
         node = kids.y;
       } else {
-        bool found = false;
+        node = -1;
         while (sp > 0) {
           --sp;
-          if (stack_t[sp] <= best_t) { node = stack_node[sp]; found = true; break; }
+          if (stack_t[sp] <= best_t) { node = stack_node[sp]; break; }
         }
-        if (!found) active = false;
       }
     }
     // warp-aggregated append
