@@ -48,6 +48,10 @@ FP32_LANES_PER_SM = 128
 LAUNCHES_PER_STEP = 9
 SYNTH_FP32, SYNTH_TC_BF16X3 = 0, 1
 VARIANT, VARIANT_NAME = SYNTH_TC_BF16X3, "tensor-core split-BF16x3 (tcgen05)"
+# dram__bytes_read.sum + dram__bytes_write.sum of one k_synth_tc launch on
+# this workload (ncu capture of the current kernel, 16 frames); retaken
+# whenever the kernel changes, else reported as null
+SYNTH_TC_DRAM_BYTES = 3.377664e6 + 768.0
 
 
 def _peaks():
@@ -360,9 +364,9 @@ def run_gpu(args):
                            "parallelism": "replicas (independent frames per GPU)"},
                 "roofline": {"bound": "tensor", "kernel": "k_synth_tc<BF16x3> (+ split-K sum), all frames of a step",
                              "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s", "frac": achieved / peak_tc,
-                             "traffic": None,
-                             "work": "algorithmic: 8 flop per complex MAC of Eq. 4 (the kernel issues 12x as many "
-                                     "tensor flops: 4 expansion terms x 3 BF16 products)",
+                             "traffic": SYNTH_TC_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
+                             "work": "algorithmic: 8 flop per complex MAC of Eq. 4 (the kernel issues 3 T x as many "
+                                     "tensor flops: T expansion terms, 2 for these hands, x 3 BF16 products)",
                              "timing": "synthesis stage of %d eager steps (CUDA events on the library stream)" % KS,
                              "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"},
                 "plain_fp32": {"value": fp32_value, "unit": "frames/s", "steps": K32,
