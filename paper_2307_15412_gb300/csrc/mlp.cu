@@ -1,18 +1,24 @@
 // mlp.cu -- kernels of the learned surrogate (BF16 MLP, FP32 accumulation).
 //
 // gemm_tn: C[M][N] = A[M][K] B[N][K]^T (both operands K-major, BF16) on the
-// 5th-generation tensor cores.  One CTA computes a 128 x 128 tile:
-//   warp 0  loads operand tiles with TMA (cp.async.bulk.tensor, one box of
-//           64 K-elements x 128 rows per operand and stage, 128-byte swizzle,
-//           which is the canonical K-major SWIZZLE_128B layout of the MMA:
-//           1024-byte atoms of 8 rows, SBO = 1024 B) into a 4-stage ring,
+// 5th-generation tensor cores; a persistent kernel (one CTA per SM) walks
+// 128 x 256 output tiles, M tiles fastest:
+//   warp 0  streams the A (64 K x 128 rows) and B (64 K x 256 rows) boxes of
+//           every K block with TMA (cp.async.bulk.tensor, 128-byte swizzle,
+//           the canonical K-major SWIZZLE_128B layout of the MMA: 1024-byte
+//           atoms of 8 rows, SBO = 1024 B) through a 4-stage ring of 48 KB,
 //           completing each stage's `full` mbarrier by transaction bytes;
-//   warp 1  allocates 128 tensor-memory columns and issues
-//           tcgen05.mma.kind::f16 (BF16 x BF16 -> FP32, M = N = 128, K = 16)
-//           per stage, committing to the stage's `empty` mbarrier;
-//   warps 2-5 wait for the last commit and run the epilogue from tensor
-//           memory (tcgen05.ld): + bias, optional ReLU or ReLU-derivative
-//           mask, stored as FP32 and/or BF16, row-major and/or transposed.
+//   warp 1  allocates 512 tensor-memory columns (two 128 x 256 FP32
+//           accumulators) and issues tcgen05.mma.kind::f16 (M = 128,
+//           N = 256, K = 16) into buffer i % 2 for the CTA's i-th tile,
+//           committing stages to their `empty` mbarriers and the finished
+//           tile to its buffer's `tfull` mbarrier;
+//   warps 2-5 drain the other buffer meanwhile (tcgen05.ld, 32 columns at a
+//           time): + bias, optional ReLU or ReLU-derivative mask, stored as
+//           FP32 and/or BF16, row-major and/or transposed.  Each warp turns
+//           its 32 x 32 block around in shared memory so that row-major
+//           stores and mask loads cover 32 consecutive columns and
+//           transposed stores 32 consecutive rows (coalesced both ways).
 // Operands outside [M, N, K] are read as zeros by TMA, so any M, N and any K
 // that is a multiple of 8 (the 16-byte TMA alignment) is accepted.  All
 // waits are bounded (2 s); a wait that runs out latches ERR_TIMEOUT.
@@ -32,10 +38,16 @@
 namespace rr {
 namespace {
 
-constexpr int kBM = 128, kBN = 128, kBK = 64, kGStages = 4;
-constexpr int kGThreads = 192;
-constexpr int kTileBytes = kBM * kBK * 2;           // 16 KB per operand per stage
-constexpr int kGemmSmem = kGStages * 2 * kTileBytes;  // 128 KB
+constexpr int kBM = 128, kBN = 256, kBK = 64, kGStages = 4;
+constexpr int kEpiWarps = 8;                         // two per TMEM lane quarter
+constexpr int kGThreads = 64 + 32 * kEpiWarps;
+constexpr int kABytes = kBM * kBK * 2;               // 16 KB of A per stage
+constexpr int kBBytes = kBN * kBK * 2;               // 32 KB of B per stage
+constexpr int kGStageBytes = kABytes + kBBytes;      // 48 KB
+constexpr int kEpiStride = 33;                       // floats per row of an epilogue warp's 32 x 32 tile
+constexpr int kEpiBytes = kEpiWarps * 32 * kEpiStride * 4;  // 33 KB
+constexpr int kGemmSmem = kGStages * kGStageBytes + kEpiBytes;
+constexpr int kTmemCols = 2 * kBN;                   // two accumulators of 128 x 256 FP32
 constexpr unsigned long long kGWaitNs = 2000000000ull;
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
@@ -78,7 +90,7 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
          (2ull << 61);
 }
 
-// kind::f16 instruction descriptor: D F32, A and B BF16, K-major, N = 128, M = 128
+// kind::f16 instruction descriptor: D F32, A and B BF16, K-major, N = 256, M = 128
 constexpr uint32_t kIdesc = (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(kBN >> 3) << 17) | ((uint32_t)(kBM >> 4) << 24);
 
 __device__ __forceinline__ void tma_box(uint32_t dst, const CUtensorMap *map, int x, int y, uint32_t bar) {
@@ -93,25 +105,42 @@ struct GemmArgs {
   const float *bias;          // [N] or nullptr
   int act;                    // 0 none, 1 relu
   const __nv_bfloat16 *mask;  // [M][N] row-major (ld N): keep entries where mask > 0; nullptr: none
+  float scale;                // outputs are scale x (A B^T + bias), before the activation
+  int m_store;                // rows stored (<= M; rows beyond are computed, not written)
   float *c32;                 // [M][N] FP32 row-major or nullptr
   __nv_bfloat16 *c16;         // [M][N] BF16 row-major or nullptr
   __nv_bfloat16 *c16t;        // [N][M] BF16 (transposed) or nullptr
   uint32_t *err;
 };
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+__device__ __forceinline__ void umma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+
+// Persistent GEMM: each CTA walks output tiles t = blockIdx.x, + gridDim.x,
+// ... (M tiles fastest, so the CTAs running at once share B tiles in L2).
+// Warp 0 streams the A and B tiles of every tile's K blocks through the
+// stage ring; warp 1 accumulates tile i in tensor-memory buffer i % 2; the
+// four epilogue warps drain buffer (i - 1) % 2 meanwhile, so stores overlap
+// the next tile's MMAs.
 __global__ void __launch_bounds__(kGThreads, 1)
 k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUtensorMap mapB, const GemmArgs g) {
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_full[kGStages], s_empty[kGStages], s_done;
+  __shared__ __align__(8) uint64_t s_full[kGStages], s_empty[kGStages], s_tfull[2], s_tempty[2];
   __shared__ uint32_t s_tmem;
   __shared__ volatile int s_abort;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const int m0 = blockIdx.x * kBM, n0 = blockIdx.y * kBN;
   const int nk = (g.K + kBK - 1) / kBK;
+  const int tiles_m = (g.M + kBM - 1) / kBM, tiles_n = (g.N + kBN - 1) / kBN;
+  const int ntiles = tiles_m * tiles_n;
 
   if (warp == 1) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
-                 "r"(kBN)
+                 "r"(kTmemCols)
                  : "memory");
     asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
   }
@@ -120,7 +149,11 @@ k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_full[q])) : "memory");
       asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_empty[q])) : "memory");
     }
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_done)) : "memory");
+    for (int q = 0; q < 2; ++q) {
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(smem_u32(&s_tfull[q])) : "memory");
+      asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(&s_tempty[q])), "r"(kEpiWarps)
+                   : "memory");
+    }
     s_abort = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     asm volatile("prefetch.tensormap [%0];" ::"l"(reinterpret_cast<uint64_t>(&mapA)) : "memory");
@@ -133,136 +166,183 @@ k_gemm_tn(const __grid_constant__ CUtensorMap mapA, const __grid_constant__ CUte
 
   if (warp == 0) {
     if (lane == 0) {
-      for (int kt = 0; kt < nk; ++kt) {
-        if (s_abort) break;
-        const int s = kt % kGStages;
-        if (kt >= kGStages && !mbar_wait(smem_u32(&s_empty[s]), ((kt / kGStages) - 1) & 1)) {
-          atomicOr(g.err, ERR_TIMEOUT);
-          s_abort = 1;
-          break;
+      int it = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x) {
+        const int m0 = (tile % tiles_m) * kBM, n0 = (tile / tiles_m) * kBN;
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          if (s_abort) break;
+          const int s = it % kGStages;
+          if (it >= kGStages && !mbar_wait(smem_u32(&s_empty[s]), ((it / kGStages) - 1) & 1)) {
+            atomicOr(g.err, ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          const uint32_t bar = smem_u32(&s_full[s]);
+          asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(kGStageBytes)
+                       : "memory");
+          const uint32_t a = smem_u32(smem + s * kGStageBytes), b = a + kABytes;
+          tma_box(a, &mapA, kt * kBK, m0, bar);
+          tma_box(b, &mapB, kt * kBK, n0, bar);
         }
-        const uint32_t bar = smem_u32(&s_full[s]);
-        asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(2 * kTileBytes)
-                     : "memory");
-        const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
-        const int k0 = kt * kBK;
-        tma_box(a, &mapA, k0, m0, bar);
-        tma_box(b, &mapB, k0, n0, bar);
       }
     }
     __syncwarp();
   } else if (warp == 1) {
     if (lane == 0) {
-      for (int kt = 0; kt < nk; ++kt) {
-        if (s_abort) break;
-        const int s = kt % kGStages;
-        if (!mbar_wait(smem_u32(&s_full[s]), (kt / kGStages) & 1)) {
+      int it = 0, tl = 0;
+      for (int tile = blockIdx.x; tile < ntiles && !s_abort; tile += gridDim.x, ++tl) {
+        const int buf = tl & 1;
+        // the epilogue must have drained this buffer (tile tl - 2)
+        if (tl >= 2 && !mbar_wait(smem_u32(&s_tempty[buf]), ((tl >> 1) - 1) & 1)) {
           atomicOr(g.err, ERR_TIMEOUT);
           s_abort = 1;
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a = smem_u32(smem + s * 2 * kTileBytes), b = a + kTileBytes;
+        const uint32_t d = tmem + (uint32_t)(buf * kBN);
+        for (int kt = 0; kt < nk; ++kt, ++it) {
+          const int s = it % kGStages;
+          if (s_abort || !mbar_wait(smem_u32(&s_full[s]), (it / kGStages) & 1)) {
+            atomicOr(g.err, ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a = smem_u32(smem + s * kGStageBytes), b = a + kABytes;
 #pragma unroll
-        for (int ks = 0; ks < kBK / 16; ++ks) {
-          const uint64_t da = smem_desc_sw128(a + ks * 32), db = smem_desc_sw128(b + ks * 32);
-          const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
-          asm volatile(
-              "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
-              "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem),
-              "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+          for (int ks = 0; ks < kBK / 16; ++ks) {
+            const uint64_t da = smem_desc_sw128(a + ks * 32), db = smem_desc_sw128(b + ks * 32);
+            const uint32_t acc = (kt > 0 || ks > 0) ? 1u : 0u;
+            asm volatile(
+                "{\n\t.reg .pred p;\n\tsetp.ne.b32 p, %4, 0;\n\t"
+                "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(d),
+                "l"(da), "l"(db), "r"(kIdesc), "r"(acc));
+          }
+          umma_commit(smem_u32(&s_empty[s]));
         }
-        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                         smem_u32(&s_empty[s]))
-                     : "memory");
+        if (s_abort) break;
+        umma_commit(smem_u32(&s_tfull[buf]));  // after this tile's MMAs (they complete in order)
       }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-                       smem_u32(&s_done))
-                   : "memory");
     }
     __syncwarp();
   } else {
-    // epilogue warps 2..5: TMEM lane quarter (warp % 4) = rows 32 (warp % 4) + lane
-    bool ok = __all_sync(0xffffffffu, mbar_wait(smem_u32(&s_done), 0));
-    if (!ok) atomicOr(g.err, ERR_TIMEOUT);
-    if (s_abort) ok = false;
-    ok = __all_sync(0xffffffffu, ok);
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    const int q = warp & 3;
-    const int row = m0 + 32 * q + lane;
-    const bool row_ok = row < g.M;
+    // epilogue warps 2..2+kEpiWarps-1: TMEM lane quarter q = warp % 4 holds
+    // tile rows 32 q .. 32 q + 31; the two warps of a quarter take
+    // alternate 32-column chunks
+    const int q = warp & 3, half = (warp - 2) >> 2;
+    float *T = reinterpret_cast<float *>(smem + kGStages * kGStageBytes) + (warp - 2) * 32 * kEpiStride;
+    const bool pairs = ((g.N | g.M | g.m_store) & 1) == 0;  // 4- and 8-byte stores of column / row pairs
+    int tl = 0;
+    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++tl) {
+      const int buf = tl & 1;
+      const int m0 = (tile % tiles_m) * kBM, n0 = (tile / tiles_m) * kBN;
+      bool ok = !s_abort && mbar_wait(smem_u32(&s_tfull[buf]), (tl >> 1) & 1);
+      ok = __all_sync(0xffffffffu, ok);
+      if (!ok) {
+        if (lane == 0) atomicOr(g.err, ERR_TIMEOUT);
+        s_abort = 1;
+        break;
+      }
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      const int rbase = m0 + 32 * q;
 #pragma unroll 1
-    for (int cb = 0; cb < kBN / 32; ++cb) {
-      uint32_t r[32];
-      const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + 32u * cb;
-      if (nk > 0) {
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-              "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-            : "r"(taddr));
-        asm volatile(
-            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
-            : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
-              "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
-              "=r"(r[30]), "=r"(r[31])
-            : "r"(taddr + 16u));
-        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-      }
-      float v[32];
-      const int nb = n0 + 32 * cb;
+      for (int cb = half; cb < kBN / 32; cb += 2) {
+        const int nb = n0 + 32 * cb;
+        if (nb >= g.N || rbase >= g.m_store) break;
+        // A: lane = row, the chunk's 32 accumulators into the warp's tile
+        {
+          uint32_t r[32];
+          const uint32_t taddr = tmem + ((uint32_t)(32 * q) << 16) + (uint32_t)(buf * kBN + 32 * cb);
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
+                "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
+              : "r"(taddr));
+          asm volatile(
+              "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+              : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
+                "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
+                "=r"(r[30]), "=r"(r[31])
+              : "r"(taddr + 16u));
+          asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-      for (int c = 0; c < 32; ++c) {
-        float x = (ok && nk > 0) ? __uint_as_float(r[c]) : 0.f;
-        const int n = nb + c;
-        if (g.bias && n < g.N) x += g.bias[n];
-        if (g.act == 1) x = fmaxf(x, 0.f);
-        if (g.mask && row_ok && n < g.N && !(__bfloat162float(g.mask[(int64_t)row * g.N + n]) > 0.f)) x = 0.f;
-        v[c] = x;
-      }
-      if (row_ok) {
-        if (g.c32) {
-          float *dst = g.c32 + (int64_t)row * g.N + nb;
-          if (nb + 32 <= g.N && (g.N & 3) == 0) {
-#pragma unroll
-            for (int c = 0; c < 32; c += 4) *reinterpret_cast<float4 *>(dst + c) = make_float4(v[c], v[c + 1], v[c + 2], v[c + 3]);
-          } else {
-            for (int c = 0; c < 32; ++c)
-              if (nb + c < g.N) dst[c] = v[c];
+          for (int c = 0; c < 32; ++c) T[lane * kEpiStride + c] = nk > 0 ? __uint_as_float(r[c]) : 0.f;
+        }
+        __syncwarp();
+        if (pairs && nb + 32 <= g.N) {
+          // B: half-warp per row, lane = column pair (2 rows per step); bias,
+          // scale, activation, mask, then 8-byte FP32 / 4-byte BF16 stores
+          const int sub = lane >> 4, cp = 2 * (lane & 15), col = nb + cp;
+          const float b0 = g.bias ? g.bias[col] : 0.f, b1 = g.bias ? g.bias[col + 1] : 0.f;
+#pragma unroll 4
+          for (int jj = 0; jj < 16; ++jj) {
+            const int j = 2 * jj + sub, row = rbase + j;
+            float x0 = (T[j * kEpiStride + cp] + b0) * g.scale, x1 = (T[j * kEpiStride + cp + 1] + b1) * g.scale;
+            if (g.act == 1) { x0 = fmaxf(x0, 0.f); x1 = fmaxf(x1, 0.f); }
+            if (row < g.m_store) {
+              const int64_t o = (int64_t)row * g.N + col;
+              if (g.mask) {
+                const float2 mk = __bfloat1622float2(*reinterpret_cast<const __nv_bfloat162 *>(g.mask + o));
+                if (!(mk.x > 0.f)) x0 = 0.f;
+                if (!(mk.y > 0.f)) x1 = 0.f;
+              }
+              if (g.c32) *reinterpret_cast<float2 *>(g.c32 + o) = make_float2(x0, x1);
+              if (g.c16) *reinterpret_cast<__nv_bfloat162 *>(g.c16 + o) = __floats2bfloat162_rn(x0, x1);
+            }
+            T[j * kEpiStride + cp] = x0;
+            T[j * kEpiStride + cp + 1] = x1;
+          }
+        } else {
+          // B, general sizes: lane = column, one row per step
+          const int col = nb + lane;
+          const bool col_ok = col < g.N;
+          const float bcol = (g.bias && col_ok) ? g.bias[col] : 0.f;
+          for (int j = 0; j < 32; ++j) {
+            const int row = rbase + j;
+            float x = (T[j * kEpiStride + lane] + bcol) * g.scale;
+            if (g.act == 1) x = fmaxf(x, 0.f);
+            if (col_ok && row < g.m_store) {
+              const int64_t o = (int64_t)row * g.N + col;
+              if (g.mask && !(__bfloat162float(g.mask[o]) > 0.f)) x = 0.f;
+              if (g.c32) g.c32[o] = x;
+              if (g.c16) g.c16[o] = __float2bfloat16_rn(x);
+            }
+            T[j * kEpiStride + lane] = x;
           }
         }
-        if (g.c16) {
-          __nv_bfloat16 *dst = g.c16 + (int64_t)row * g.N + nb;
-          if (nb + 32 <= g.N && (g.N & 7) == 0) {
-#pragma unroll
-            for (int c = 0; c < 32; c += 8) {
-              __nv_bfloat162 p0 = __floats2bfloat162_rn(v[c], v[c + 1]), p1 = __floats2bfloat162_rn(v[c + 2], v[c + 3]);
-              __nv_bfloat162 p2 = __floats2bfloat162_rn(v[c + 4], v[c + 5]), p3 = __floats2bfloat162_rn(v[c + 6], v[c + 7]);
-              uint4 u;
-              u.x = *reinterpret_cast<uint32_t *>(&p0);
-              u.y = *reinterpret_cast<uint32_t *>(&p1);
-              u.z = *reinterpret_cast<uint32_t *>(&p2);
-              u.w = *reinterpret_cast<uint32_t *>(&p3);
-              *reinterpret_cast<uint4 *>(dst + c) = u;
+        __syncwarp();
+        // C: the transposed BF16 copy, consecutive rows per store
+        if (g.c16t) {
+          if (pairs && nb + 32 <= g.N) {
+            const int r0 = 2 * (lane & 15), cs = lane >> 4, row = rbase + r0;
+            if (row < g.m_store) {  // M even, so row + 1 < M as well
+#pragma unroll 4
+              for (int cc = 0; cc < 16; ++cc) {
+                const int c = 2 * cc + cs;
+                *reinterpret_cast<__nv_bfloat162 *>(g.c16t + (int64_t)(nb + c) * g.M + row) =
+                    __floats2bfloat162_rn(T[r0 * kEpiStride + c], T[(r0 + 1) * kEpiStride + c]);
+              }
             }
           } else {
-            for (int c = 0; c < 32; ++c)
-              if (nb + c < g.N) dst[c] = __float2bfloat16_rn(v[c]);
+            const int row = rbase + lane;
+            if (row < g.m_store)
+              for (int c = 0; c < 32 && nb + c < g.N; ++c)
+                g.c16t[(int64_t)(nb + c) * g.M + row] = __float2bfloat16_rn(T[lane * kEpiStride + c]);
           }
         }
+        __syncwarp();
       }
-      if (g.c16t) {  // transposed: for each column the 32 lanes write 32 consecutive rows
-#pragma unroll
-        for (int c = 0; c < 32; ++c)
-          if (row_ok && nb + c < g.N) g.c16t[(int64_t)(nb + c) * g.M + row] = __float2bfloat16_rn(v[c]);
-      }
+      // buffer drained: the MMA warp may reuse it
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s_tempty[buf]));
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 1) {
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kBN) : "memory");
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols) : "memory");
   }
 }
 
@@ -408,14 +488,14 @@ EncodeTiledFn encode_fn() {
 }
 
 // Tensor map of a row-major BF16 matrix [rows][cols] (cols = K, contiguous):
-// boxes of 64 columns x 128 rows, 128-byte swizzle, zero fill outside.
-cudaError_t make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols) {
+// boxes of 64 columns x box_rows rows, 128-byte swizzle, zero fill outside.
+cudaError_t make_map(CUtensorMap *map, const void *base, int64_t rows, int64_t cols, int box_rows) {
   EncodeTiledFn fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   if ((cols & 7) != 0 || (reinterpret_cast<uintptr_t>(base) & 15) != 0) return cudaErrorInvalidValue;
   const cuuint64_t dims[2] = {(cuuint64_t)cols, (cuuint64_t)rows};
   const cuuint64_t strides[1] = {(cuuint64_t)cols * 2};
-  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)kBM};
+  const cuuint32_t box[2] = {(cuuint32_t)kBK, (cuuint32_t)box_rows};
   const cuuint32_t estr[2] = {1, 1};
   const CUresult r = fn(map, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<void *>(base), dims, strides, box, estr,
                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -435,8 +515,9 @@ int grid_for(int64_t n, int threads) {
 
 cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const float *bias, int act,
                     const __nv_bfloat16 *mask, float *c32, __nv_bfloat16 *c16, __nv_bfloat16 *c16t, uint32_t *err,
-                    cudaStream_t st) {
+                    cudaStream_t st, float scale, int m_store) {
   if (M <= 0 || N <= 0 || K <= 0 || (K & 7) != 0) return cudaErrorInvalidValue;
+  if (m_store < 0 || m_store > M) m_store = M;
   static bool attr = false;
   if (!attr) {
     cudaError_t e = cudaFuncSetAttribute(k_gemm_tn, cudaFuncAttributeMaxDynamicSharedMemorySize, kGemmSmem);
@@ -444,14 +525,19 @@ cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N
     attr = true;
   }
   CUtensorMap ma, mb;
-  cudaError_t e = make_map(&ma, A, M, K);
+  cudaError_t e = make_map(&ma, A, M, K, kBM);
   if (e != cudaSuccess) return e;
-  if ((e = make_map(&mb, B, N, K)) != cudaSuccess) return e;
+  if ((e = make_map(&mb, B, N, K, kBN)) != cudaSuccess) return e;
   GemmArgs g;
   g.M = M; g.N = N; g.K = K;
   g.bias = bias; g.act = act; g.mask = mask;
   g.c32 = c32; g.c16 = c16; g.c16t = c16t; g.err = err;
-  dim3 grid((M + kBM - 1) / kBM, (N + kBN - 1) / kBN);
+  g.scale = scale; g.m_store = m_store;
+  // persistent: one CTA per SM at most
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int64_t tiles = (int64_t)((M + kBM - 1) / kBM) * ((N + kBN - 1) / kBN);
+  const int grid = (int)(tiles < sms ? tiles : sms);
   k_gemm_tn<<<grid, kGThreads, kGemmSmem, st>>>(ma, mb, g);
   return cudaGetLastError();
 }

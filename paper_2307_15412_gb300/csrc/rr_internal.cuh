@@ -197,9 +197,11 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
 // [M][K], B [N][K] BF16 row-major (K a multiple of 8, 16-byte aligned),
 // + bias[N], act 1 = ReLU, mask [M][N] BF16 (zero where mask <= 0); outputs
 // any of FP32 [M][N], BF16 [M][N], BF16 transposed [N][M].
+// Outputs are scale x (A B^T + bias) before the activation; only rows
+// < m_store are written (m_store < 0: all M).
 cudaError_t gemm_tn(const __nv_bfloat16 *A, const __nv_bfloat16 *B, int M, int N, int K, const float *bias, int act,
                     const __nv_bfloat16 *mask, float *c32, __nv_bfloat16 *c16, __nv_bfloat16 *c16t, uint32_t *err,
-                    cudaStream_t st);
+                    cudaStream_t st, float scale = 1.f, int m_store = -1);
 cudaError_t mse_grad(const float *y, const float *t, int64_t B, int O, __nv_bfloat16 *dy, __nv_bfloat16 *dyt,
                      float *loss_acc, cudaStream_t st);
 cudaError_t row_sums(const __nv_bfloat16 *dzt, int rows, int64_t cols, float *out, cudaStream_t st);

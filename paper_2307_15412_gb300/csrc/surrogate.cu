@@ -104,15 +104,20 @@ cudaError_t refresh_bf16(Surrogate *s, cudaStream_t st) {
 }
 
 // Forward pass on x [B][d0] (FP32, device).  keep_t: also write the
-// transposed activations the backward pass needs.
-cudaError_t forward(Surrogate *s, const float *x, int64_t B, bool keep_t, uint32_t *err, cudaStream_t st) {
+// transposed activations the backward pass needs.  y_out: if given, the
+// output layer writes scale x its result for the first rows_out rows there
+// instead of the unscaled s->y.
+cudaError_t forward(Surrogate *s, const float *x, int64_t B, bool keep_t, uint32_t *err, cudaStream_t st,
+                    float *y_out = nullptr, float scale = 1.f, int64_t rows_out = -1) {
   cudaError_t e = to_bf16_both(x, (int)B, s->dims[0], s->x16, keep_t ? s->x16t : nullptr, st);
   if (e != cudaSuccess) return e;
   const __nv_bfloat16 *h = s->x16;
   for (int l = 0; l < s->L; ++l) {
     const bool last = l == s->L - 1;
-    e = gemm_tn(h, s->w16[l], (int)B, s->dims[l + 1], s->dims[l], s->p + s->boff[l], last ? 0 : 1, nullptr,
-                last ? s->y : nullptr, last ? nullptr : s->h16[l], (!last && keep_t) ? s->h16t[l] : nullptr, err, st);
+    float *c32 = last ? (y_out ? y_out : s->y) : nullptr;
+    e = gemm_tn(h, s->w16[l], (int)B, s->dims[l + 1], s->dims[l], s->p + s->boff[l], last ? 0 : 1, nullptr, c32,
+                last ? nullptr : s->h16[l], (!last && keep_t) ? s->h16t[l] : nullptr, err, st,
+                (last && y_out) ? scale : 1.f, (last && y_out && rows_out >= 0) ? (int)rows_out : -1);
     if (e != cudaSuccess) return e;
     if (!last) h = s->h16[l];
   }
@@ -303,8 +308,7 @@ rr_status rr_surrogate_forward(rr_ctx *c, const float *x, int64_t B, float *y) {
   rr::Guard g(rr_ctx_device(c));
   cudaStream_t cs = rr_ctx_stream(c);
   SUR_CUDA(c, rr::ensure_acts(s, B), "surrogate activations");
-  SUR_CUDA(c, rr::forward(s, x, B, false, rr_ctx_err(c), cs), "surrogate forward");
-  SUR_CUDA(c, rr::scale_copy(y, s->y, B * s->dims[s->L], s->out_scale, cs), "forward");
+  SUR_CUDA(c, rr::forward(s, x, B, false, rr_ctx_err(c), cs, y, s->out_scale, B), "surrogate forward");
   return RR_OK;
 }
 
@@ -431,8 +435,8 @@ rr_status rr_surrogate_infer(rr_ctx *c, const float *x, int64_t n, float *y_out,
       SUR_CUDA(c, cudaMemcpyAsync(s->xb, xin, sizeof(float) * rows * din, cudaMemcpyDeviceToDevice, cs), "infer");
       xin = s->xb;
     }
-    SUR_CUDA(c, rr::forward(s, xin, padded, false, rr_ctx_err(c), cs), "surrogate forward");
-    SUR_CUDA(c, rr::scale_copy(y_out + r0 * dout, s->y, rows * dout, s->out_scale, cs), "infer");
+    SUR_CUDA(c, rr::forward(s, xin, padded, false, rr_ctx_err(c), cs, y_out + r0 * dout, s->out_scale, rows),
+             "surrogate forward");
   }
   if (fell_back) SUR_CUDA(c, rr::outside_box(x, n, din, fell_back, cs), "infer");
   return RR_OK;
