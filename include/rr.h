@@ -115,6 +115,29 @@ const char *rr_version(void);
 rr_status rr_scene_upload(rr_ctx *ctx, int scene, const float *verts, int64_t nv,
                           const int32_t *tris, int64_t nt, const float *vel, int ptr_is_device);
 
+/* One mesh of rr_scene_upload_many: the arguments of rr_scene_upload. */
+typedef struct {
+  int32_t scene;
+  int32_t reserved;        /* 0 */
+  const float *verts;      /* [nv][3] */
+  int64_t nv;
+  const int32_t *tris;     /* [nt][3] */
+  int64_t nt;
+  float vel[3];            /* rigid translation velocity (m/s) */
+  float pad;
+} rr_mesh;
+
+#define RR_UPLOAD_ASYNC 1  /* host arrays: no synchronisation; see rr_scene_upload_many */
+
+/* rr_scene_upload for n_meshes meshes (distinct slots) in one call, all host
+ * or all device pointers.  With host pointers the copies are issued
+ * asynchronously and the call synchronises the stream once at its end, or
+ * not at all with flags & RR_UPLOAD_ASYNC: then the host arrays must stay
+ * valid and unchanged until rr_sync returns (pinned host memory makes the
+ * copies truly asynchronous).  Errors as for rr_scene_upload; meshes before
+ * a rejected one stay uploaded. */
+rr_status rr_scene_upload_many(rr_ctx *ctx, const rr_mesh *meshes, int n_meshes, int ptr_is_device, int flags);
+
 /* Builds the linear BVH of a scene: triangle bounds, 30-bit Morton codes of
  * the bounding-box centres, radix sort, binary radix tree (Karras 2012)
  * with bottom-up bounding boxes.  Must follow every rr_scene_upload. */

@@ -336,8 +336,9 @@ rr_status rr_sync(rr_ctx *c) {
   return st;
 }
 
-rr_status rr_scene_upload(rr_ctx *c, int scene, const float *verts, int64_t nv, const int32_t *tris,
-                          int64_t nt, const float *vel, int ptr_is_device) {
+// Copies one mesh into its slot on the context stream (no synchronisation).
+static rr_status upload_mesh(rr_ctx *c, int scene, const float *verts, int64_t nv, const int32_t *tris, int64_t nt,
+                      const float *vel, int ptr_is_device) {
   if (!c) return RR_EINVAL;
   if (scene < 0 || scene >= RR_MAX_SCENES) return fail(c, RR_EINVAL, "scene %d out of [0,%d)", scene, RR_MAX_SCENES);
   if (nv < 0 || nt < 0) return fail(c, RR_EINVAL, "negative sizes");
@@ -381,12 +382,31 @@ rr_status rr_scene_upload(rr_ctx *c, int scene, const float *verts, int64_t nv, 
     RR_CUDA(c, cudaMemcpyAsync(s->V, verts, sizeof(float) * 3 * (size_t)nv, kind, c->stream), "upload vertices");
     RR_CUDA(c, cudaMemcpyAsync(s->F, tris, sizeof(int32_t) * 3 * (size_t)nt, kind, c->stream), "upload faces");
   }
-  if (!ptr_is_device) RR_CUDA(c, cudaStreamSynchronize(c->stream), "upload");  // caller may reuse host arrays
   s->nv = nv;
   s->nt = nt;
   for (int i = 0; i < 3; ++i) s->vel[i] = vel ? vel[i] : 0.f;
   s->built = false;
   s->traced = false;
+  return RR_OK;
+}
+
+rr_status rr_scene_upload(rr_ctx *c, int scene, const float *verts, int64_t nv, const int32_t *tris,
+                          int64_t nt, const float *vel, int ptr_is_device) {
+  rr_status st = upload_mesh(c, scene, verts, nv, tris, nt, vel, ptr_is_device);
+  if (st != RR_OK) return st;
+  if (!ptr_is_device) RR_CUDA(c, cudaStreamSynchronize(c->stream), "upload");  // caller may reuse host arrays
+  return RR_OK;
+}
+
+rr_status rr_scene_upload_many(rr_ctx *c, const rr_mesh *meshes, int n_meshes, int ptr_is_device, int flags) {
+  if (!c) return RR_EINVAL;
+  if (n_meshes < 0 || (n_meshes > 0 && !meshes)) return fail(c, RR_EINVAL, "mesh array");
+  for (int i = 0; i < n_meshes; ++i) {
+    const rr_mesh &m = meshes[i];
+    rr_status st = upload_mesh(c, m.scene, m.verts, m.nv, m.tris, m.nt, m.vel, ptr_is_device);
+    if (st != RR_OK) return st;
+  }
+  if (!ptr_is_device && !(flags & RR_UPLOAD_ASYNC)) RR_CUDA(c, cudaStreamSynchronize(c->stream), "upload");
   return RR_OK;
 }
 

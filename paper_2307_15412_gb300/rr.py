@@ -49,6 +49,15 @@ class rr_job(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("grid", rr_raygrid)]
 
 
+class rr_mesh(ctypes.Structure):
+    _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("verts", ctypes.c_void_p),
+                ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p), ("nt", ctypes.c_int64),
+                ("vel", ctypes.c_float * 3), ("pad", ctypes.c_float)]
+
+
+RR_UPLOAD_ASYNC = 1
+
+
 class rr_adamw(ctypes.Structure):
     _fields_ = [("lr", ctypes.c_float), ("beta1", ctypes.c_float), ("beta2", ctypes.c_float),
                 ("eps", ctypes.c_float), ("weight_decay", ctypes.c_float)]
@@ -70,6 +79,7 @@ SIGNATURES = {
     "rr_last_error": (ctypes.c_char_p, [_P]),
     "rr_version": (ctypes.c_char_p, []),
     "rr_scene_upload": (_I, [_P, _I, _P, _I64, _P, _I64, _P, _I]),
+    "rr_scene_upload_many": (_I, [_P, _P, _I, _I, _I]),
     "rr_build_bvh": (_I, [_P, _I]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
@@ -231,6 +241,30 @@ class Context:
             velp = self._vel.ctypes.data
         self._check(self.lib.rr_scene_upload(self.h, scene, _ptr(V), int(V.shape[0]), _ptr(F), int(F.shape[0]),
                                              velp, 1 if on_dev else 0))
+
+    @staticmethod
+    def meshes(items):
+        """ctypes rr_mesh array for scene_upload_many from (scene, V, F, vel)
+        items (V float32 [nv,3], F int32 [nt,3], contiguous numpy arrays or
+        torch tensors, all on the host or all on the device; vel or None).
+        The arrays must outlive every upload that uses the result."""
+        arr = (rr_mesh * len(items))()
+        for i, (sc, V, F, vel) in enumerate(items):
+            arr[i].scene = int(sc)
+            arr[i].verts = _ptr(V)
+            arr[i].nv = int(V.shape[0])
+            arr[i].tris = _ptr(F)
+            arr[i].nt = int(F.shape[0])
+            if vel is not None:
+                for k in range(3):
+                    arr[i].vel[k] = float(vel[k])
+        return arr
+
+    def scene_upload_many(self, meshes, on_device: bool, asynchronous: bool = False):
+        """Uploads a prepared rr_mesh array (see meshes()).  asynchronous:
+        host arrays stay untouched until the next sync() (pinned memory)."""
+        self._check(self.lib.rr_scene_upload_many(self.h, meshes, len(meshes), 1 if on_device else 0,
+                                                  RR_UPLOAD_ASYNC if asynchronous else 0))
 
     def build_bvh(self, scene: int):
         self._check(self.lib.rr_build_bvh(self.h, scene))

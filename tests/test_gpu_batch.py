@@ -232,3 +232,29 @@ def test_batch_of_sixteen_full_frames_in_one_wave(ctx):
     for k in (0, 15):
         si, _ = _single(ctx, 720 + k, radar, grid)
         assert rel_l2(got[k], si) <= 1e-5
+
+
+@pytest.mark.parametrize("on_device,asynchronous", [(False, True), (False, False), (True, False)])
+def test_scene_upload_many_matches_single_uploads(ctx, on_device, asynchronous):
+    """Several meshes in one rr_scene_upload_many call (pinned host memory
+    without synchronisation, host memory with one synchronisation, device
+    memory) give the frames of one rr_scene_upload per mesh."""
+    radar = I.Radar(n_samples=64, n_chirps=8, rx=I.rx_l_array())
+    grid = I.RayGrid(96, 96, math.radians(40), math.radians(40))
+    scenes = [I.hand_scene(500 + k, 3000 + 1000 * k, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+              for k in range(4)]
+    if on_device:
+        arrays = [(torch.from_numpy(s.V).cuda(), torch.from_numpy(s.F).cuda()) for s in scenes]
+    else:
+        arrays = [(torch.from_numpy(s.V).pin_memory(), torch.from_numpy(s.F).pin_memory()) for s in scenes]
+    meshes = ctx.meshes([(800 + k, arrays[k][0], arrays[k][1], s.vel) for k, s in enumerate(scenes)])
+    ctx.scene_upload_many(meshes, on_device=on_device, asynchronous=asynchronous)
+    out = _cube(4, radar)
+    ctx.batch_run([(800 + k, grid) for k in range(4)], radar, if_out=out)
+    ctx.sync()
+    got = to_complex(out)
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(810 + k, s.V, s.F, s.vel)
+        si, _ = _single(ctx, 810 + k, radar, grid)
+        assert np.linalg.norm(si) > 0
+        assert rel_l2(got[k], si) <= 1e-5
