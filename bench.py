@@ -42,10 +42,6 @@ FRAMES_PER_STEP = 16
 N_SCENES = FRAMES_PER_STEP
 FLUSH_BYTES = 256 << 20
 FP32_LANES_PER_SM = 128
-# kernels per step (all frames together): LBVH build (one cluster launch),
-# tile numbering, traversal, hit prefix, echo, IF synthesis, split-K sum,
-# range FFT rows, Doppler FFT columns
-LAUNCHES_PER_STEP = 9
 SYNTH_FP32, SYNTH_TC_BF16X3 = 0, 1
 VARIANT, VARIANT_NAME = SYNTH_TC_BF16X3, "tensor-core split-BF16x3 (tcgen05)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_synth_tc launch on
@@ -280,6 +276,10 @@ def run_gpu(args):
     torch.cuda.synchronize()
     wall0 = time.perf_counter()
     step_ms = timed_steps(variant, K)
+    # kernels per step as the library planned them (build, tile numbering,
+    # traversal, hit prefix, echo, per-hit constants, synthesis, split-K sum
+    # when split, range and Doppler FFTs)
+    plan = ctx.batch_plan()
     torch.cuda.synchronize()
     wall = time.perf_counter() - wall0
     if ws > 1:
@@ -385,7 +385,8 @@ def run_gpu(args):
                                            "trace_frame": float(stages[:, 1].mean()),
                                            "synth_if": float(stages[:, 2].mean()),
                                            "range_doppler": float(stages[:, 3].mean())},
-                "gpu_launches": LAUNCHES_PER_STEP * K,
+                "gpu_launches": plan["kernel_launches"] * K,
+                "batch_plan": plan,
                 "clocks": clocks,
                 "wall_s_timed_region": wall}
         print(json.dumps(line))

@@ -256,6 +256,14 @@ typedef struct {
 rr_status rr_batch_run(rr_ctx *ctx, const rr_job *jobs, int n_jobs, const rr_radar *radar,
                        rr_synth_variant variant, int window, float *if_out, float *rd_out, int flags);
 
+/* The plan of the context's last rr_batch_run (after autotuning): the ray
+ * tile (2^ray_tile_log2 x 2^(5 - ray_tile_log2) rays per warp), the split-K
+ * factor of the synthesis, the CTAs per builder cluster for meshes of up to
+ * 8 x 3840 triangles (16 above, 0 if none was cluster-built), and the number
+ * of kernels one such batch enqueues (a graph replay runs the same ones).
+ * Any pointer may be NULL.  RR_ENOTREADY before the first batch. */
+rr_status rr_batch_plan(const rr_ctx *ctx, int *ray_tile_log2, int *split, int *cluster_ctas, int *kernel_launches);
+
 /* ---- learned surrogate --------------------------------------------------- */
 
 /* A multilayer perceptron that maps hand parameters to a range-Doppler cube,

@@ -63,6 +63,8 @@ struct rr_ctx {
     int tc_cst_rows = 0;
     double2 *dir = nullptr;                 // FP64 ray-direction tables (n_az + n_el per frame)
     int64_t dir_cap = 0;
+    // the plan of the last batch (rr_batch_plan)
+    int last_tw = 0, last_split = 0, last_c = 0, last_launches = 0;
     // CUDA graph of the last batch
     cudaGraphExec_t exec = nullptr;
     cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
@@ -532,6 +534,17 @@ rr_status rr_range_doppler(rr_ctx *c, const float *if_in, int n_rx, int n_chirps
   return RR_OK;
 }
 
+rr_status rr_batch_plan(const rr_ctx *c, int *ray_tile_log2, int *split, int *cluster_ctas, int *kernel_launches) {
+  if (!c) return RR_EINVAL;
+  const auto &b = c->batch;
+  if (b.last_launches == 0) return RR_ENOTREADY;
+  if (ray_tile_log2) *ray_tile_log2 = b.last_tw;
+  if (split) *split = b.last_split;
+  if (cluster_ctas) *cluster_ctas = b.last_c;
+  if (kernel_launches) *kernel_launches = b.last_launches;
+  return RR_OK;
+}
+
 rr_status rr_phase_reference(rr_ctx *c, const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out) {
   if (!c) return RR_EINVAL;
   if (!in || !out || n_frames < 0 || n_rx < 1 || n_rx > RR_MAX_RX || cells < 1)
@@ -934,6 +947,27 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.tuned[shape] = {tw, sp};
     P.tw = tw;
     P.split = sp;
+  }
+
+  // the plan as it will run: ray tiles, split-K factor, cluster size, and
+  // the kernels one batch enqueues (build, four for trace and echo, the
+  // synthesis with its per-hit constants and split-K sum, range-Doppler)
+  {
+    int launches = (P.n8 > 0 ? 1 : 0) + (P.n16 > 0 ? 1 : 0) + 4;
+    for (SceneDev *s : P.others) launches += s->nt == 0 ? 1 : 3;
+    int split;
+    if (variant == RR_SYNTH_FP32) {
+      split = rr::synth_fp32_batch_split(P.rd, P.kmax, n_jobs, P.split);
+      launches += 2;
+    } else {
+      split = rr::synth_tc_split(P.rd, P.kmax, n_jobs, P.split);
+      launches += split > 1 ? 3 : 2;
+    }
+    if (rd_out) launches += radar->n_chirps > 1 ? 2 : 1;
+    b.last_tw = P.tw;
+    b.last_split = split;
+    b.last_c = P.n8 ? P.c_small : (P.n16 ? 16 : 0);
+    b.last_launches = launches;
   }
 
   // the graph key: everything the enqueued work depends on

@@ -370,6 +370,11 @@ int batch_split(const Plan &pl, const RadarDev &r, int64_t kmax, int n_jobs, int
 }
 }  // namespace
 
+int synth_fp32_batch_split(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  const Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
+  return batch_split(pl, r, kmax < 1 ? 1 : kmax, n_jobs, split);
+}
+
 int64_t synth_batch_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
   const Plan pl = make_plan(r, kmax < 1 ? 1 : kmax);
   const int S = batch_split(pl, r, kmax < 1 ? 1 : kmax, n_jobs, split);

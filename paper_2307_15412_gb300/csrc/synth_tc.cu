@@ -662,6 +662,10 @@ cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
 
 }  // namespace
 
+int synth_tc_split(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+  return tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split).S;
+}
+
 bool synth_tc_supported(const RadarDev &r) {
   return r.N >= 16 && r.N <= 2048 && (r.N & (r.N - 1)) == 0 && r.M >= 1;
 }
@@ -689,7 +693,8 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
   p.kb = r.slope * r.dt / kC;
   p.c1k = (float)(r.f0 * r.t_rep / kC);
   p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
-  p.partials = partials;
+  // with one split the CTAs' partial cubes are the output: no reduction pass
+  p.partials = pl.S == 1 ? out : partials;
   p.jobs = jobs;
   p.order = order;
   p.err = err;
@@ -711,6 +716,7 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = (total * n_jobs + threads - 1) / threads;
+  if (pl.S == 1) return cudaSuccess;
   k_tc_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total, n_jobs,
                                                     reinterpret_cast<float2 *>(out));
   return cudaGetLastError();

@@ -80,6 +80,7 @@ SIGNATURES = {
     "rr_version": (ctypes.c_char_p, []),
     "rr_scene_upload": (_I, [_P, _I, _P, _I64, _P, _I64, _P, _I]),
     "rr_scene_upload_many": (_I, [_P, _P, _I, _I, _I]),
+    "rr_batch_plan": (_I, [_P, _P, _P, _P, _P]),
     "rr_build_bvh": (_I, [_P, _I]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
@@ -322,6 +323,12 @@ class Context:
         flags = (RR_BATCH_GRAPH if graph else 0) | (RR_BATCH_AUTOTUNE if autotune else 0)
         self._check(self.lib.rr_batch_run(self.h, arr, len(arr), ctypes.byref(rs), int(variant), int(window),
                                           _ptr(if_out), _ptr(rd_out), flags))
+
+    def batch_plan(self):
+        """Plan of the last batch_run: ray_tile_log2, split, cluster_ctas, kernel_launches."""
+        v = [ctypes.c_int(0) for _ in range(4)]
+        self._check(self.lib.rr_batch_plan(self.h, *[ctypes.byref(x) for x in v]))
+        return dict(zip(("ray_tile_log2", "split", "cluster_ctas", "kernel_launches"), (x.value for x in v)))
 
     # ---- learned surrogate (argument marshalling only; see include/rr.h)
 
