@@ -385,7 +385,15 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
     __syncthreads();
   }
 
-  for (int e = tid; e < mine; e += kThreads) {
+  // Each thread climbs from a run of consecutive leaves: neighbours in key
+  // order are mostly siblings, so a thread's second leaf usually meets its
+  // first at their parent and goes on up the thread's own small subtree,
+  // instead of waiting behind climbs from leaves 1024 positions apart (the
+  // longest chain of dependent steps drops from about 66 to 30 on a
+  // 22k-triangle hand on 6 CTAs).
+  const int per = (mine + kThreads - 1) / kThreads;
+  const int e_end = min((tid + 1) * per, mine);
+  for (int e = tid * per; e < e_end; ++e) {
     const int i = first + e;
     const int t = P.idA[e];
     const int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
