@@ -385,15 +385,12 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
     __syncthreads();
   }
 
-  // Each thread climbs from a run of consecutive leaves: neighbours in key
-  // order are mostly siblings, so a thread's second leaf usually meets its
-  // first at their parent and goes on up the thread's own small subtree,
-  // instead of waiting behind climbs from leaves 1024 positions apart (the
-  // longest chain of dependent steps drops from about 66 to 30 on a
-  // 22k-triangle hand on 6 CTAs).
-  const int per = (mine + kThreads - 1) / kThreads;
-  const int e_end = min((tid + 1) * per, mine);
-  for (int e = tid * per; e < e_end; ++e) {
+  // Leaf pre-pass (threads strided over the leaves, so the triangles' loads
+  // are all in flight together): the sorted triangle copy, the leaf's half
+  // of its parent node and the leaf box in the parent's box slot.  The
+  // climbs below then start at the exchange, with no global load or store
+  // of their own before it.
+  for (int e = tid; e < mine; e += kThreads) {
     const int i = first + e;
     const int t = P.idA[e];
     const int a = F[3 * t], b = F[3 * t + 1], c = F[3 * t + 2];
@@ -403,8 +400,39 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
     tris[3 * i + 0] = make_float4(v0.x, v0.y, v0.z, __int_as_float(t));
     tris[3 * i + 1] = make_float4(v1.x, v1.y, v1.z, 0.f);
     tris[3 * i + 2] = make_float4(v2.x, v2.y, v2.z, 0.f);
-    float bl[3] = {fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z))};
-    float bh[3] = {fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z))};
+    const float bl[3] = {fminf(v0.x, fminf(v1.x, v2.x)), fminf(v0.y, fminf(v1.y, v2.y)), fminf(v0.z, fminf(v1.z, v2.z))};
+    const float bh[3] = {fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z))};
+    const bool as_left = i == 0 ? true : (i == n - 1 ? false : hb_at(i) < hb_at(i - 1));
+    const int p = as_left ? i : i - 1;
+    BvhNode *np = nodes + p;
+    if (as_left) {
+      np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+      reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
+      np->kids.x = ~i;
+    } else {
+      np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+      reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
+      np->kids.y = ~i;
+    }
+    const int owner = p / cap, slot = p - owner * cap, side = as_left ? 0 : 1;
+    float *nb = owner == crank ? P.nbox : cluster.map_shared_rank(P.nbox, owner);
+#pragma unroll
+    for (int x = 0; x < 3; ++x) {
+      nb[(side * 6 + x) * cap + slot] = bl[x];
+      nb[(side * 6 + 3 + x) * cap + slot] = bh[x];
+    }
+  }
+  cluster.sync();  // every leaf box is in its slot
+
+  // Each thread climbs from a run of consecutive leaves: neighbours in key
+  // order are mostly siblings, so a thread's second leaf usually meets its
+  // first at their parent and goes on up the thread's own small subtree,
+  // instead of waiting behind climbs from leaves 1024 positions apart.
+  const int per = (mine + kThreads - 1) / kThreads;
+  const int e_end = min((tid + 1) * per, mine);
+  for (int e = tid * per; e < e_end; ++e) {
+    const int i = first + e;
+    float bl[3], bh[3];
     int cur = ~i, l = i, r = i;
     for (int guard = 0; guard < 2 * n + 64; ++guard) {
       bool as_left;
@@ -412,35 +440,44 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
       else if (r == n - 1) as_left = false;
       else as_left = hb_at(r) < hb_at(l - 1);
       const int p = as_left ? r : l - 1;
-      // final node fields straight to global memory
-      BvhNode *np = nodes + p;
-      if (as_left) {
-        np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-        reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
-        np->kids.x = cur;
-      } else {
-        np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-        reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
-        np->kids.y = cur;
-      }
-      // this child's box for the sibling, in the parent's owner CTA; a
-      // parent inside this CTA's block synchronises at CTA scope
       const int owner = p / cap, slot = p - owner * cap;
       const int side = as_left ? 0 : 1;
+      // a parent inside this CTA's block synchronises at CTA scope
       bool local = false;
       if (owner == crank) {
         const uint32_t hp = (uint32_t)P.hb[slot] + 1u;
         local = P.pref[slot] > hp && P.suf[slot] > hp;
       }
       float *nb = local ? P.nbox : cluster.map_shared_rank(P.nbox, owner);
+      if (guard > 0) {  // the leaf level was written by the pre-pass
+        // final node fields straight to global memory
+        BvhNode *np = nodes + p;
+        if (as_left) {
+          np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+          reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
+          np->kids.x = cur;
+        } else {
+          np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
+          reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
+          np->kids.y = cur;
+        }
+        // this child's box for the sibling, in the parent's owner CTA
 #pragma unroll
-      for (int x = 0; x < 3; ++x) {
-        nb[(side * 6 + x) * cap + slot] = bl[x];
-        nb[(side * 6 + 3 + x) * cap + slot] = bh[x];
+        for (int x = 0; x < 3; ++x) {
+          nb[(side * 6 + x) * cap + slot] = bl[x];
+          nb[(side * 6 + 3 + x) * cap + slot] = bh[x];
+        }
       }
       const int other = local ? exch_acq_rel_cta(&P.nflag[slot], as_left ? l : r)
                               : exch_acq_rel_cluster(cluster.map_shared_rank(&P.nflag[slot], owner), as_left ? l : r);
       if (other < 0) break;  // first to arrive: the sibling's thread goes on
+      if (guard == 0) {  // the leaf's own box, from its slot
+#pragma unroll
+        for (int x = 0; x < 3; ++x) {
+          bl[x] = nb[(side * 6 + x) * cap + slot];
+          bh[x] = nb[(side * 6 + 3 + x) * cap + slot];
+        }
+      }
 #pragma unroll
       for (int x = 0; x < 3; ++x) {
         bl[x] = fminf(bl[x], nb[((1 - side) * 6 + x) * cap + slot]);
