@@ -404,16 +404,8 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
     const float bh[3] = {fmaxf(v0.x, fmaxf(v1.x, v2.x)), fmaxf(v0.y, fmaxf(v1.y, v2.y)), fmaxf(v0.z, fmaxf(v1.z, v2.z))};
     const bool as_left = i == 0 ? true : (i == n - 1 ? false : hb_at(i) < hb_at(i - 1));
     const int p = as_left ? i : i - 1;
-    BvhNode *np = nodes + p;
-    if (as_left) {
-      np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-      reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
-      np->kids.x = ~i;
-    } else {
-      np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-      reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
-      np->kids.y = ~i;
-    }
+    if (as_left) nodes[p].kids.x = ~i;
+    else nodes[p].kids.y = ~i;
     const int owner = p / cap, slot = p - owner * cap, side = as_left ? 0 : 1;
     float *nb = owner == crank ? P.nbox : cluster.map_shared_rank(P.nbox, owner);
 #pragma unroll
@@ -450,17 +442,9 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
       }
       float *nb = local ? P.nbox : cluster.map_shared_rank(P.nbox, owner);
       if (guard > 0) {  // the leaf level was written by the pre-pass
-        // final node fields straight to global memory
-        BvhNode *np = nodes + p;
-        if (as_left) {
-          np->lxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-          reinterpret_cast<float2 *>(&np->lrz)[0] = make_float2(bl[2], bh[2]);
-          np->kids.x = cur;
-        } else {
-          np->rxy = make_float4(bl[0], bh[0], bl[1], bh[1]);
-          reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(bl[2], bh[2]);
-          np->kids.y = cur;
-        }
+        // the child index to global memory (the boxes follow from the slots at the end)
+        if (as_left) nodes[p].kids.x = cur;
+        else nodes[p].kids.y = cur;
         // this child's box for the sibling, in the parent's owner CTA
 #pragma unroll
         for (int x = 0; x < 3; ++x) {
@@ -495,6 +479,16 @@ k_build_cluster(const BuildJob one, const BuildJob *__restrict__ table) {
   }
   // no CTA may leave while others still touch its shared memory
   cluster.sync();
+  // both child boxes of every node this CTA owns are in its slots now
+  for (int e = tid; e < mine; e += kThreads) {
+    const int p = first + e;
+    if (p >= n - 1) break;
+    const float *nb = P.nbox;
+    BvhNode *np = nodes + p;
+    np->lxy = make_float4(nb[0 * cap + e], nb[3 * cap + e], nb[1 * cap + e], nb[4 * cap + e]);
+    np->rxy = make_float4(nb[6 * cap + e], nb[9 * cap + e], nb[7 * cap + e], nb[10 * cap + e]);
+    np->lrz = make_float4(nb[2 * cap + e], nb[5 * cap + e], nb[8 * cap + e], nb[11 * cap + e]);
+  }
 }
 
 int g_cluster_ok[64] = {0};  // per device: 0 unknown, 1 usable, -1 not usable
