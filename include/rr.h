@@ -258,10 +258,14 @@ rr_status rr_batch_run(rr_ctx *ctx, const rr_job *jobs, int n_jobs, const rr_rad
 
 /* The plan of the context's last rr_batch_run (after autotuning): the ray
  * tile (2^ray_tile_log2 x 2^(5 - ray_tile_log2) rays per warp), the split-K
- * factor of the synthesis, the CTAs per builder cluster for meshes of up to
- * 8 x 3840 triangles (16 above, 0 if none was cluster-built), and the number
- * of kernels one such batch enqueues (a graph replay runs the same ones).
- * Any pointer may be NULL.  RR_ENOTREADY before the first batch. */
+ * factor of the synthesis, the largest builder cluster used for meshes of up
+ * to 8 x 3840 triangles (16 for larger ones alone, 0 if none was
+ * cluster-built), and the number of kernels one such batch enqueues (a
+ * graph replay runs the same ones).  Meshes are built by clusters of 1 to 16
+ * CTAs: all meshes of up to 8 x 3840 triangles on one size when they fit on
+ * the GPU at once, else grouped by size (1, 2, 4 or 8 CTAs), one build
+ * launch per group.  Any pointer may be NULL.  RR_ENOTREADY before the first
+ * batch. */
 rr_status rr_batch_plan(const rr_ctx *ctx, int *ray_tile_log2, int *split, int *cluster_ctas, int *kernel_launches);
 
 /* ---- learned surrogate --------------------------------------------------- */

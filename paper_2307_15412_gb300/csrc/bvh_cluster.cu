@@ -583,18 +583,20 @@ int cluster_max_active(int C) {
 
 // Cluster size for the n_jobs meshes of a batch that need at least cmin
 // CTAs each (cmin <= 8): the largest size whose resident clusters hold all
-// of them at once (one wave, each mesh on as many CTAs as possible), else 8.
+// of them at once (one wave, each mesh on as many CTAs as possible), or 0
+// when no size does (the batch then groups its meshes by size).
 int batch_cluster_size(int n_jobs, int cmin) {
   for (int C = 8; C >= cmin && C >= 1; --C)
     if (n_jobs <= cluster_max_active(C)) return C;
-  return 8;
+  return 0;
 }
 
 bool cluster_build_usable() { return cluster_usable(); }
 
 // One frame: 8 CTAs up to 16384 triangles, else 16 (the shorter sort
-// passes win).  Batches: 8 CTAs as long as they fit (twice as many meshes
-// build at once on the 152 SMs, which matters more than each one's time).
+// passes win; a lone small mesh is faster on 8 CTAs than on one).
+// Batches: the group of meshes up to 8 kMaxCap triangles (8) or above
+// (16); the batch planner sizes the first group's clusters.
 int cluster_size_for(int n, bool batch) {
   if (batch) return n <= 8 * kMaxCap ? 8 : 16;
   return n <= 8 * 2048 ? 8 : 16;

@@ -665,9 +665,13 @@ uint64_t fnv(uint64_t h, const void *p, size_t n) {
 // Everything a batch enqueues, decided on the host before any work is issued.
 struct BatchPlan {
   int n_jobs = 0;
-  int n8 = 0, n16 = 0;              // cluster-built frames (table order: group of <= 8 CTAs, 16-CTA group)
-  int c_small = 8;                  // cluster size of the first group
-  int max_cap8 = 0, max_cap16 = 0;
+  // cluster-built frames in groups of one cluster size each (table order:
+  // group 0, 1, ...): 1, 2, 4, 8 CTAs by mesh size, or all meshes of up to
+  // 8 x 3840 triangles in group 3 with the one-wave size; 16 CTAs above
+  int gC[5] = {1, 2, 4, 8, 16};
+  int gn[5] = {0, 0, 0, 0, 0};
+  int gcap[5] = {0, 0, 0, 0, 0};
+  int n_cluster() const { return gn[0] + gn[1] + gn[2] + gn[3] + gn[4]; }
   std::vector<SceneDev *> others;   // frames built by the per-scene path (fewer than 2 or very many triangles)
   int64_t kmax = 0;                 // largest hit segment
   rr::RadarDev rd;
@@ -701,12 +705,13 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b.ftab, b.h_ftab, sizeof(rr::FrameJob) * P.n_jobs, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-  if (P.n8 + P.n16 > 0 &&
-      (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  if (P.n_cluster() > 0 &&
+      (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * P.n_cluster(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) return e;
-  if (P.n8 && (e = rr::launch_build_bvh_cluster_table(b.btab, P.n8, P.c_small, P.max_cap8, st)) != cudaSuccess) return e;
-  if (P.n16 && (e = rr::launch_build_bvh_cluster_table(b.btab + P.n8, P.n16, 16, P.max_cap16, st)) != cudaSuccess) return e;
+  for (int g = 0, off = 0; g < 5; off += P.gn[g], ++g)
+    if (P.gn[g] && (e = rr::launch_build_bvh_cluster_table(b.btab + off, P.gn[g], P.gC[g], P.gcap[g], st)) != cudaSuccess)
+      return e;
   for (SceneDev *s : P.others)
     if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
@@ -800,7 +805,9 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   BatchPlan P;
   P.n_jobs = n_jobs;
   const int kpc = rr::cluster_keys_per_cta();
-  int cmin = 1;  // CTAs the largest mesh of the first group needs
+  int cmin = 1;       // CTAs the largest mesh of up to 8 x kpc triangles needs
+  int n_small = 0;    // cluster-built meshes of up to 8 x kpc triangles
+  std::vector<char> cl_job(n_jobs, 0);
   for (int j = 0; j < n_jobs; ++j) {
     if ((st = get_scene(c, jobs[j].scene, &sc[j])) != RR_OK) return st;
     if (seen[jobs[j].scene]) return fail(c, RR_EINVAL, "scene %d appears twice in the batch", jobs[j].scene);
@@ -815,15 +822,28 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
     const int n = (int)sc[j]->nt;
     const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
-    if (cl && rr::cluster_size_for(n, true) == 8) {
-      ++P.n8;
-      cmin = std::max(cmin, (n + kpc - 1) / kpc);
-    } else if (cl) {
-      ++P.n16;
+    if (cl) {
+      cl_job[j] = 1;
+      if (rr::cluster_size_for(n, true) == 8) {
+        ++n_small;
+        cmin = std::max(cmin, (n + kpc - 1) / kpc);
+      }
+    } else {
+      P.others.push_back(sc[j]);
     }
-    else P.others.push_back(sc[j]);
   }
-  if (P.n8) P.c_small = rr::batch_cluster_size(P.n8, cmin);
+  // all small meshes in one wave if some cluster size allows it, else
+  // groups of 1, 2, 4 or 8 CTAs by mesh size (fewest SMs per mesh)
+  const int one_c = n_small ? rr::batch_cluster_size(n_small, cmin) : 0;
+  if (one_c > 0) P.gC[3] = one_c;
+  auto group_of = [&](int n) -> int {
+    if (rr::cluster_size_for(n, true) != 8) return 4;
+    if (one_c > 0) return 3;
+    const int need = (n + kpc - 1) / kpc;
+    return need <= 1 ? 0 : (need <= 2 ? 1 : (need <= 4 ? 2 : 3));
+  };
+  for (int j = 0; j < n_jobs; ++j)
+    if (cl_job[j]) ++P.gn[group_of((int)sc[j]->nt)];
   const int64_t total = seg[n_jobs];
   const int n_rx = radar->n_rx;
   P.rd = to_dev(radar);
@@ -911,7 +931,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
 
   // device tables, staged in pinned memory (wait until the last copy out of it is done)
   RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
-  int i8 = 0, i16 = P.n8;
+  int gfill[5];
+  for (int g = 0, off = 0; g < 5; off += P.gn[g], ++g) gfill[g] = off;
   for (int j = 0; j < n_jobs; ++j) {
     SceneDev *s = sc[j];
     rr::FrameJob f = rr::frame_job_for(*s, to_dev(&jobs[j].grid), seg[j + 1] - seg[j]);
@@ -928,16 +949,10 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.h_ftab[j] = f;
     const int n = (int)s->nt;
     if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
-      const bool small = rr::cluster_size_for(n, true) == 8;
-      const int C = small ? P.c_small : 16;
-      const rr::BuildJob bj = rr::build_job_for(*s, C);
-      if (small) {
-        b.h_btab[i8++] = bj;
-        P.max_cap8 = std::max(P.max_cap8, bj.cap);
-      } else {
-        b.h_btab[i16++] = bj;
-        P.max_cap16 = std::max(P.max_cap16, bj.cap);
-      }
+      const int g = group_of(n);
+      const rr::BuildJob bj = rr::build_job_for(*s, P.gC[g]);
+      b.h_btab[gfill[g]++] = bj;
+      P.gcap[g] = std::max(P.gcap[g], bj.cap);
     }
   }
 
@@ -953,7 +968,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   // the kernels one batch enqueues (build, four for trace and echo, the
   // synthesis with its per-hit constants and split-K sum, range-Doppler)
   {
-    int launches = (P.n8 > 0 ? 1 : 0) + (P.n16 > 0 ? 1 : 0) + 4;
+    int launches = 4;
+    for (int g = 0; g < 5; ++g) launches += P.gn[g] > 0 ? 1 : 0;
     for (SceneDev *s : P.others) launches += s->nt == 0 ? 1 : 3;
     int split;
     if (variant == RR_SYNTH_FP32) {
@@ -966,7 +982,10 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     if (rd_out) launches += radar->n_chirps > 1 ? 2 : 1;
     b.last_tw = P.tw;
     b.last_split = split;
-    b.last_c = P.n8 ? P.c_small : (P.n16 ? 16 : 0);
+    b.last_c = 0;
+    for (int g = 0; g < 4; ++g)
+      if (P.gn[g]) b.last_c = P.gC[g];
+    if (!b.last_c && P.gn[4]) b.last_c = 16;
     b.last_launches = launches;
   }
 
@@ -981,7 +1000,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   key = fnv(key, &P.tw, sizeof(P.tw));
   key = fnv(key, &P.split, sizeof(P.split));
   key = fnv(key, b.h_ftab, sizeof(rr::FrameJob) * n_jobs);
-  key = fnv(key, b.h_btab, sizeof(rr::BuildJob) * (P.n8 + P.n16));
+  key = fnv(key, b.h_btab, sizeof(rr::BuildJob) * P.n_cluster());
   for (SceneDev *s : P.others) {
     key = fnv(key, &s, sizeof(s));
     key = fnv(key, &s->nt, sizeof(s->nt));

@@ -279,3 +279,28 @@ def test_batch_plan_reports_the_enqueued_kernels(ctx):
     plan = ctx.batch_plan()
     assert plan["kernel_launches"] == 1 + 4 + (3 if plan["split"] > 1 else 2) + 2
     ctx.sync()
+
+
+def test_batch_grouped_by_mesh_size_is_exact(ctx):
+    """A batch with more meshes than one wave of clusters holds is built in
+    groups of 1, 2, 4 and 8 CTAs by mesh size (one launch each): the trees
+    must still be the oracle's and the frames those of single-frame runs."""
+    radar = I.Radar(n_samples=64, n_chirps=8, rx=I.rx_l_array())
+    grid = I.RayGrid(64, 64, math.radians(40), math.radians(40))
+    sizes = [1500, 5000, 12000, 25000]
+    scenes = [I.hand_scene(900 + k, sizes[k % 4], range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+              for k in range(40)]
+    for k, s in enumerate(scenes):
+        ctx.scene_upload(1500 + k, s.V, s.F, s.vel)
+    out = _cube(40, radar)
+    ctx.batch_run([(1500 + k, grid) for k in range(40)], radar, if_out=out)
+    ctx.sync()
+    plan = ctx.batch_plan()
+    assert plan["kernel_launches"] == 4 + 4 + 2  # four build groups, trace and echo, FP32 synthesis
+    assert plan["cluster_ctas"] == 8
+    for k in range(4):
+        _check_tree(ctx, 1500 + k, scenes[k], scenes[k].F.shape[0] <= 5000)
+    got = to_complex(out)
+    for k in range(4):
+        si, _ = _single(ctx, 1500 + k, radar, grid)
+        assert rel_l2(got[k], si) <= 1e-5
