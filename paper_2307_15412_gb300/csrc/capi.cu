@@ -215,7 +215,7 @@ rr_status run_synth(rr_ctx *c, const rr_radar *r, rr_synth_variant v, const uint
             "synth_if launch");
     return RR_OK;
   }
-  const int64_t need = rr::synth_tc_partial_floats(rd, kmax, 1, 0);
+  const int64_t need = rr::synth_tc_partial_floats(rd, v == RR_SYNTH_TC_TF32, kmax, 1, 0);
   RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
   RR_CUDA(c, grow(c->tc_cst, c->tc_cst_cap, (int64_t)r->n_rx * (ld > 0 ? ld : 1)), "synth constants");
   RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, nullptr, 0, c->partials,
@@ -683,7 +683,7 @@ struct BatchPlan {
 
 int64_t batch_partials_need(const BatchPlan &P, int split) {
   if (P.variant == RR_SYNTH_FP32) return rr::synth_batch_partial_floats(P.rd, P.kmax, P.n_jobs, split);
-  return rr::synth_tc_partial_floats(P.rd, P.kmax, P.n_jobs, split);
+  return rr::synth_tc_partial_floats(P.rd, P.variant == RR_SYNTH_TC_TF32, P.kmax, P.n_jobs, split);
 }
 
 // The frames of a batch by decreasing hit count (written by the trace
@@ -976,7 +976,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
       split = rr::synth_fp32_batch_split(P.rd, P.kmax, n_jobs, P.split);
       launches += 2;
     } else {
-      split = rr::synth_tc_split(P.rd, P.kmax, n_jobs, P.split);
+      split = rr::synth_tc_split(P.rd, variant == RR_SYNTH_TC_TF32, P.kmax, n_jobs, P.split);
       launches += split > 1 ? 3 : 2;
     }
     if (rd_out) launches += radar->n_chirps > 1 ? 2 : 1;

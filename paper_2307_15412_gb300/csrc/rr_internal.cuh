@@ -184,12 +184,12 @@ cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int
 // (jobs == nullptr: d/a/dd/ld/count/kmax) or a FrameJob table of n_jobs
 // frames; tf32 selects kind::tf32, else split-BF16x3.
 bool synth_tc_supported(const RadarDev &r);
-int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+int64_t synth_tc_partial_floats(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split);
 // cst: float4 scratch laid out like the hit arrays (at least n_rx * ld
 // entries past d_base: d_base = d for one frame, the base of the batch hit
 // arrays for a batch) for the per-hit constants.
 // The split-K factor the launchers use for a batch (split <= 0: their own choice).
-int synth_tc_split(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+int synth_tc_split(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split);
 int synth_fp32_batch_split(const RadarDev &r, int64_t kmax, int n_jobs, int split);
 // order (may be null): device int[n_jobs], the frames in launch order.
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,

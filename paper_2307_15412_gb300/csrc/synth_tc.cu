@@ -59,19 +59,16 @@ namespace rr {
 namespace {
 
 constexpr int kTcThreads = 544;  // 16 producer warps + 1 MMA warp
-constexpr int kLO = 16;
 constexpr int kHitsPerBlock = 32;
 constexpr int kTerms = 4;                         // terms of the coupling expansion
-constexpr float kLC = 0.5f * (float)(kLO - 1);    // centre l_c of the fast-time offsets
-constexpr int kStages = 3;
+constexpr int kStages = 3;                        // at most (fewer when the B operand is large)
 // Long accumulation chains in tensor memory lose precision (2.4e-4 rel-L2
 // for 37k hits in one accumulator against 1.3e-5 for 1.7k, split-BF16x3), so
 // every kMaxChain blocks the accumulator is folded into an FP32 row buffer
 // in shared memory and the chain restarts.
 constexpr int kMaxChain = 64;                      // blocks (of 32 hits) per accumulation chain
-constexpr int kStageBytes = 64 * 1024;           // A region 32 KB + B region 32 KB
-constexpr int kABytes = 32 * 1024;
-constexpr int kTmemCols = 256;  // accumulator: 32 T columns (TF32) or 64 T (BF16x3, hi and lo products)
+constexpr int kRingBytes = 3 * 64 * 1024;        // the stage ring
+constexpr int kABytes = 32 * 1024;               // A region of a stage (hi and lo, or TF32)
 constexpr unsigned long long kWaitNs = 2000000000ull;  // 2 s bound on any wait
 
 struct SynthTcParams {
@@ -252,58 +249,76 @@ __device__ __forceinline__ int expansion_terms(float x) {
 // and empty (one tcgen05.commit: the tensor core has read it); `done`
 // receives a commit after the last block.
 constexpr int kProducers = 512;
-constexpr int kFoldStride = 33;  // floats per row of the fold buffer (padded against bank conflicts)
-constexpr int kFoldBytes = 128 * kFoldStride * 4;
+// floats per row of the fold buffer: 2 LO accumulators, padded against bank conflicts
+template <int LO>
+constexpr int fold_stride() { return 2 * LO + 1; }
+template <int LO>
+constexpr int smem_bytes_tc() { return kRingBytes + 128 * fold_stride<LO>() * 4; }
 
-// Loads 32 accumulator columns of this thread's row (TMEM lane 32 w + lane).
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, uint32_t *r) {
+// Loads 16 accumulator columns at ca and 16 at cb of this thread's row
+// (TMEM lane 32 w + lane) into r[0..15] and r[16..31].
+__device__ __forceinline__ void tmem_ld16x2(uint32_t ca, uint32_t cb, uint32_t *r) {
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
         "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
-      : "r"(taddr));
+      : "r"(ca));
   asm volatile(
       "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
       : "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]),
         "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]),
         "=r"(r[30]), "=r"(r[31])
-      : "r"(taddr + 16u));
+      : "r"(cb));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 }
 
 // Adds sum_{t < nt} kappa_t D_t of this thread's accumulator row (TMEM
-// lane 32 w + lane, w = warp % 4) into acc[0..15] (Re) and acc[16..31] (Im);
-// kappa = (1, -j sg, k2, j k3), k2 = -sg^2 / 2, k3 = sg^3 / 6.  D_t sits in
-// columns 32 t; with `second` (BF16x3) the hi x lo product of term t sits in
-// columns 32 (nt + t) and is added to it.
+// lane 32 w + lane, w = warp % 4) into acc[0..LO) (Re) and acc[LO..2 LO)
+// (Im); kappa = (1, -j sg, k2, j k3), k2 = -sg^2 / 2, k3 = sg^3 / 6.  D_t
+// sits in columns 2 LO t (Re half, then Im half); with `second` (BF16x3)
+// the hi x lo product of term t sits NT = 2 LO nt columns further and is
+// added to it.
+template <int LO>
 __device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
                                          float *acc) {
   const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
+  const uint32_t NT = 2u * LO * (uint32_t)nt;
 #pragma unroll
   for (int t = 0; t < kTerms; ++t) {
     if (t >= nt) break;
-    uint32_t r[32];
-    tmem_ld32(tbase + 32u * t, r);
-    if (second) {
-      uint32_t r2[32];
-      tmem_ld32(tbase + 32u * (nt + t), r2);
 #pragma unroll
-      for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
-    }
+    for (int c = 0; c < LO / 16; ++c) {
+      uint32_t r[32];
+      const uint32_t cre = 2u * LO * t + 16u * c, cim = cre + LO;
+      tmem_ld16x2(tbase + cre, tbase + cim, r);
+      if (second) {
+        uint32_t r2[32];
+        tmem_ld16x2(tbase + NT + cre, tbase + NT + cim, r2);
 #pragma unroll
-    for (int q = 0; q < kLO; ++q) {
-      const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[kLO + q]);
-      if (t == 0) { acc[q] += dr; acc[kLO + q] += di; }
-      else if (t == 1) { acc[q] += sg * di; acc[kLO + q] -= sg * dr; }   // (-j sg)(dr + j di)
-      else if (t == 2) { acc[q] += k2 * dr; acc[kLO + q] += k2 * di; }
-      else { acc[q] -= k3 * di; acc[kLO + q] += k3 * dr; }               // (j k3)(dr + j di)
+        for (int q = 0; q < 32; ++q) r[q] = __float_as_uint(__uint_as_float(r[q]) + __uint_as_float(r2[q]));
+      }
+#pragma unroll
+      for (int q = 0; q < 16; ++q) {
+        const float dr = __uint_as_float(r[q]), di = __uint_as_float(r[16 + q]);
+        float &ar = acc[16 * c + q], &ai = acc[LO + 16 * c + q];
+        if (t == 0) { ar += dr; ai += di; }
+        else if (t == 1) { ar += sg * di; ai -= sg * dr; }   // (-j sg)(dr + j di)
+        else if (t == 2) { ar += k2 * dr; ai += k2 * di; }
+        else { ar -= k3 * di; ai += k3 * dr; }               // (j k3)(dr + j di)
+      }
     }
   }
 }
 
-template <bool TF32>
+// LO: fast-time offsets per row (16, or 32 for BF16x3 chirps of >= 256
+// samples: twice the samples per A row, the B operand and the accumulator
+// twice as wide).
+template <bool TF32, int LO>
 __global__ void __launch_bounds__(kTcThreads, 1)
 k_synth_tc(const SynthTcParams p) {
+  constexpr float LC = 0.5f * (float)(LO - 1);        // centre l_c of the fast-time offsets
+  constexpr int kTmemCols = LO == 16 ? 256 : 512;     // hi x hi (+ lo x hi) and hi x lo products
+  constexpr int FS = fold_stride<LO>();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done, s_fold, s_folded;
   __shared__ uint32_t s_tmem;
@@ -371,19 +386,25 @@ k_synth_tc(const SynthTcParams p) {
     if (lane == 0 && bm > 0.f) atomicMax(&s_bmax, __float_as_uint(bm));  // non-negative: bits order as values
   }
   __syncthreads();
-  const int nterms = expansion_terms<TF32>(6.2831853f * __uint_as_float(s_bmax) * mu_max * kLC);
-  // lo halves (BF16x3): A_lo 16 KB after A_hi; B_lo right after the 32 T
-  // rows of B_hi, so that one MMA of N = 64 T reads [B_hi | B_lo]
-  const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : 4096u * (uint32_t)nterms;
+  const int nterms = expansion_terms<TF32>(6.2831853f * __uint_as_float(s_bmax) * mu_max * LC);
+  // B columns: 2 LO per term (Re half, Im half); lo halves (BF16x3): A_lo
+  // 16 KB after A_hi, B_lo right after the NT rows of B_hi, so that one MMA
+  // of N = 2 NT reads [B_hi | B_lo] while 2 NT <= 256
+  const uint32_t NT = 2u * LO * (uint32_t)nterms;
+  const uint32_t lo_a = TF32 ? 0u : 16384u, lo_b = TF32 ? 0u : NT * 128u;
+  // stage ring laid out for this CTA's B operand: 3 stages of 64 KB, or 2
+  // when a wide B (LO = 32, T >= 3) needs more
+  const uint32_t stage_bytes = LO == 16 ? 65536u : ((uint32_t)kABytes + NT * 256u + 1023u) & ~1023u;
+  const int nst = (int)min((uint32_t)kStages, (uint32_t)kRingBytes / stage_bytes);
   // accumulator rows of warps 0-3: row 32 w + lane = (chirp, h); fold buffer
-  float *fold = reinterpret_cast<float *>(smem + kStages * kStageBytes);
+  float *fold = reinterpret_cast<float *>(smem + kRingBytes);
   const int my_row = 32 * (warp & 3) + lane;
   const int HEr = p.HI < 8 ? 8 : p.HI;
   const int my_mi = my_row / HEr, my_h = my_row - my_mi * HEr;
   const float my_sg = 6.2831853f * ((float)(m0 + my_mi) - mcen);
   const float my_k2 = -0.5f * my_sg * my_sg, my_k3 = my_sg * my_sg * my_sg * (1.f / 6.f);
   if (warp < 4)
-    for (int q = 0; q < 2 * kLO; ++q) fold[my_row * kFoldStride + q] = 0.f;
+    for (int q = 0; q < 2 * LO; ++q) fold[my_row * FS + q] = 0.f;
 
   if (warp < 16) {
     // ---- producers: lane = block-local hit; warp w writes the A rows
@@ -395,7 +416,6 @@ k_synth_tc(const SynthTcParams p) {
     const int nseg = HE / 8;                         // 8-row units per chirp (16 per tile)
     const int mi = warp / nseg, seg = warp - mi * nseg;
     const int hbase = 8 * seg;
-    const int l = warp;
     // the constants of block b + 1 are loaded while block b is generated
     float4 cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
     float a_next = 0.f;
@@ -416,14 +436,14 @@ k_synth_tc(const SynthTcParams p) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        fold_row(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * kFoldStride);
+        fold_row<LO>(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * FS);
         asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
         asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
       }
-      const int stg = b % kStages;
-      unsigned char *A = smem + stg * kStageBytes;
+      const int stg = b % nst;
+      unsigned char *A = smem + stg * stage_bytes;
       unsigned char *B = A + kABytes;
-      if (b >= kStages && !mbar_wait(smem_u32(&s_empty[stg]), ((b - kStages) / kStages) & 1)) {
+      if (b >= nst && !mbar_wait(smem_u32(&s_empty[stg]), ((b - nst) / nst) & 1)) {
         atomicOr(p.err, ERR_TIMEOUT);
         s_abort = 1;
         break;
@@ -446,9 +466,9 @@ k_synth_tc(const SynthTcParams p) {
         if (mi < mvalid) {
           const float fm = (float)(m0 + mi);
           const float beta = fmaf(fm, b1, b0);
-          const float cyc = fmaf(fm, c1, c0) + b1 * ((fm - mcen) * kLC);
-          W = expm2pi(beta * (float)kLO);
-          P = expm2pi(fmaf(beta * (float)kLO, (float)hbase, cyc));
+          const float cyc = fmaf(fm, c1, c0) + b1 * ((fm - mcen) * LC);
+          W = expm2pi(beta * (float)LO);
+          P = expm2pi(fmaf(beta * (float)LO, (float)hbase, cyc));
           P.x *= a;
           P.y *= a;
         }
@@ -475,19 +495,24 @@ k_synth_tc(const SynthTcParams p) {
           }
         }
       }
-      // B: terms t = 0..3, halves Re / Im of offset l: column 32 t + 16 half + l
+      // B: terms t < T, halves Re / Im of offsets l = (LO / 16) w + dl:
+      // column 2 LO t + LO half + l
       {
         const float beta_c = fmaf(mcen, b1, b0);
-        const float2 B0 = expm2pi(beta_c * (float)l);
-        const float bl = b1 * ((float)l - kLC);
-        float w = 1.f;  // (b1 (l - l_c))^t
 #pragma unroll
-        for (int t = 0; t < kTerms; ++t) {
-          if (t >= nterms) break;  // columns 32 t .. of unused terms are not read
-          const float re = w * B0.x, im = w * B0.y;
-          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + l, lane), re, -im);        // Re half
-          put2<TF32>(B, B + lo_b, op_off<TF32>(32 * t + kLO + l, lane), im, re);   // Im half
-          w *= bl;
+        for (int dl = 0; dl < LO / 16; ++dl) {
+          const int l = (LO / 16) * warp + dl;
+          const float2 B0 = expm2pi(beta_c * (float)l);
+          const float bl = b1 * ((float)l - LC);
+          float w = 1.f;  // (b1 (l - l_c))^t
+#pragma unroll
+          for (int t = 0; t < kTerms; ++t) {
+            if (t >= nterms) break;  // columns of unused terms are not read
+            const float re = w * B0.x, im = w * B0.y;
+            put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + l, lane), re, -im);        // Re half
+            put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + LO + l, lane), im, re);    // Im half
+            w *= bl;
+          }
         }
       }
       // generic-proxy smem writes -> visible to the tensor core, then arrive
@@ -497,14 +522,16 @@ k_synth_tc(const SynthTcParams p) {
   } else {
     // ---- MMA issuer (warp 16, one lane)
     if (lane == 0) {
-      // N = 32 columns per term; BF16x3: A_hi [B_hi | B_lo] with N = 64 T,
-      // then A_lo B_hi into the first 32 T columns
-      const uint32_t id = idesc(TF32 ? 2u : 1u, 32u * (uint32_t)nterms);
-      const uint32_t id2 = idesc(1u, 64u * (uint32_t)nterms);
+      // N = NT columns; BF16x3: A_hi [B_hi | B_lo] with N = 2 NT when that
+      // is <= 256, else A_hi B_hi and A_hi B_lo apart; then A_lo B_hi into
+      // the first NT columns
+      const uint32_t id = idesc(TF32 ? 2u : 1u, NT);
+      const bool packed = 2u * NT <= 256u;
+      const uint32_t id2 = idesc(1u, packed ? 2u * NT : NT);
       for (int b = 0; b < nb; ++b) {
         if (s_abort) break;
-        const int stg = b % kStages;
-        if (!mbar_wait(smem_u32(&s_full[stg]), (b / kStages) & 1)) {
+        const int stg = b % nst;
+        if (!mbar_wait(smem_u32(&s_full[stg]), (b / nst) & 1)) {
           atomicOr(p.err, ERR_TIMEOUT);
           s_abort = 1;
           break;
@@ -516,7 +543,7 @@ k_synth_tc(const SynthTcParams p) {
           break;
         }
         asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(smem + stg * kStageBytes), bb0 = a0 + kABytes;
+        const uint32_t a0 = smem_u32(smem + stg * stage_bytes), bb0 = a0 + kABytes;
         if (TF32) {
 #pragma unroll 1
           for (int ks = 0; ks < kHitsPerBlock / 4; ++ks) {
@@ -529,8 +556,14 @@ k_synth_tc(const SynthTcParams p) {
             const uint32_t ko = (uint32_t)ks * 32u;
             const uint64_t ahi = smem_desc_sw128(a0 + ko), alo = smem_desc_sw128(a0 + lo_a + ko);
             const uint64_t bhi = smem_desc_sw128(bb0 + ko);
-            mma<false>(tmem, ahi, bhi, id2, (!fresh || ks > 0) ? 1u : 0u);  // [hi x hi | hi x lo]
-            mma<false>(tmem, alo, bhi, id, 1u);                               // += lo x hi
+            const uint32_t acc = (!fresh || ks > 0) ? 1u : 0u;
+            if (packed) {
+              mma<false>(tmem, ahi, bhi, id2, acc);  // [hi x hi | hi x lo]
+            } else {
+              mma<false>(tmem, ahi, bhi, id, acc);                                       // hi x hi
+              mma<false>(tmem + NT, ahi, smem_desc_sw128(bb0 + lo_b + ko), id, acc);    // hi x lo
+            }
+            mma<false>(tmem, alo, bhi, id, 1u);  // += lo x hi
           }
         }
         mma_commit(smem_u32(&s_empty[stg]));
@@ -554,15 +587,15 @@ k_synth_tc(const SynthTcParams p) {
     if (s_abort) have = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     have = __all_sync(0xffffffffu, have);
-    float *acc = fold + my_row * kFoldStride;
-    if (have) fold_row(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, acc);
+    float *acc = fold + my_row * FS;
+    if (have) fold_row<LO>(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, acc);
     const int m = m0 + my_mi;
     if (my_mi < mvalid && my_h < p.HI) {
       float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
-                                                                    (int64_t)p.N + (int64_t)my_h * kLO));
+                                                                    (int64_t)p.N + (int64_t)my_h * LO));
 #pragma unroll
-      for (int q = 0; q < 8; ++q)
-        o[q] = have ? make_float4(acc[2 * q], acc[kLO + 2 * q], acc[2 * q + 1], acc[kLO + 2 * q + 1])
+      for (int q = 0; q < LO / 2; ++q)
+        o[q] = have ? make_float4(acc[2 * q], acc[LO + 2 * q], acc[2 * q + 1], acc[LO + 2 * q + 1])
                     : make_float4(0.f, 0.f, 0.f, 0.f);
     }
   }
@@ -578,7 +611,7 @@ k_synth_tc(const SynthTcParams p) {
 // tiles: c0 = frac(f0 d / c) (the FP64 carrier reduction), c1 = f0 d-dot
 // T_rep / c, b0 = S dt d / c, b1 = S dt d-dot T_rep / c; and the check of
 // the coupling expansion's bound for the widest tile.
-__global__ void k_tc_consts(const SynthTcParams p, float mu_max) {
+__global__ void k_tc_consts(const SynthTcParams p, float mu_max, float lc) {
   const int job = blockIdx.z, j = blockIdx.y;
   const float *dbase = p.d, *ddbase = p.dd;
   int64_t ld = p.ld;
@@ -598,7 +631,7 @@ __global__ void k_tc_consts(const SynthTcParams p, float mu_max) {
     const double x = p.f0_c * (double)d;
     const float b1 = p.b1k * dd;
     cj[k] = make_float4((float)(x - floor(x)), p.c1k * dd, (float)(p.kb * (double)d), b1);
-    if (6.2831853f * fabsf(b1) * mu_max * kLC > 0.157f) bad = true;
+    if (6.2831853f * fabsf(b1) * mu_max * lc > 0.157f) bad = true;
   }
   if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_TC_BOUND);
 }
@@ -622,9 +655,13 @@ struct TcPlan {
   int HI, mc, n_tiles, S;
 };
 
-TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
+// Fast-time offsets per row: 32 for BF16x3 chirps of >= 256 samples (8 or
+// more rows per chirp, no padding), else 16.
+int tc_lo(const RadarDev &r, bool tf32) { return (!tf32 && r.N >= 256) ? 32 : 16; }
+
+TcPlan tc_plan(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
   TcPlan pl;
-  pl.HI = r.N / kLO;
+  pl.HI = r.N / tc_lo(r, tf32);
   pl.mc = 128 / (pl.HI < 8 ? 8 : pl.HI);
   pl.n_tiles = (r.M + pl.mc - 1) / pl.mc;
   int sms = 152, dev = 0;
@@ -646,32 +683,32 @@ TcPlan tc_plan(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
   return pl;
 }
 
-template <bool TF32>
+template <bool TF32, int LO>
 cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
   static bool attr_set = false;
-  const int smem = kStages * kStageBytes + kFoldBytes;
+  constexpr int smem = smem_bytes_tc<LO>();
   if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_synth_tc<TF32>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    cudaError_t e = cudaFuncSetAttribute(k_synth_tc<TF32, LO>, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
   dim3 grid(p.n_tiles * p.n_rx, p.S, n_jobs);
-  k_synth_tc<TF32><<<grid, kTcThreads, smem, st>>>(p);
+  k_synth_tc<TF32, LO><<<grid, kTcThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int synth_tc_split(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
-  return tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split).S;
+int synth_tc_split(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
+  return tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split).S;
 }
 
 bool synth_tc_supported(const RadarDev &r) {
   return r.N >= 16 && r.N <= 2048 && (r.N & (r.N - 1)) == 0 && r.M >= 1;
 }
 
-int64_t synth_tc_partial_floats(const RadarDev &r, int64_t kmax, int n_jobs, int split) {
-  const TcPlan pl = tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split);
+int64_t synth_tc_partial_floats(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
+  const TcPlan pl = tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split);
   return (int64_t)n_jobs * pl.S * r.n_rx * r.M * r.N * 2;
 }
 
@@ -681,7 +718,8 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
                             float4 *cst, const float *d_base, cudaStream_t st) {
   if (!cst) return cudaErrorInvalidValue;  // d_base may be null with no hits
   if (!synth_tc_supported(r) || n_jobs < 1) return cudaErrorInvalidValue;
-  const TcPlan pl = tc_plan(r, kmax < 1 ? 1 : kmax, n_jobs, split);
+  const int LO = tc_lo(r, tf32);
+  const TcPlan pl = tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split);
   const int64_t total = (int64_t)r.n_rx * r.M * r.N;
   if ((int64_t)n_jobs * pl.S * total * 2 > partial_cap_floats) return cudaErrorInvalidValue;
   SynthTcParams p;
@@ -708,11 +746,12 @@ cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count,
     const int cap = (4 * sms + r.n_rx * n_jobs - 1) / (r.n_rx * n_jobs);
     if (bx > cap) bx = cap < 1 ? 1 : cap;
     const float mu_max = 0.5f * (float)((pl.mc < r.M ? pl.mc : r.M) - 1);
-    k_tc_consts<<<dim3(bx, r.n_rx, n_jobs), 256, 0, st>>>(p, mu_max);
+    k_tc_consts<<<dim3(bx, r.n_rx, n_jobs), 256, 0, st>>>(p, mu_max, 0.5f * (float)(LO - 1));
     const cudaError_t ec = cudaGetLastError();
     if (ec != cudaSuccess) return ec;
   }
-  cudaError_t e = tf32 ? launch_tc<true>(p, n_jobs, st) : launch_tc<false>(p, n_jobs, st);
+  cudaError_t e = tf32 ? launch_tc<true, 16>(p, n_jobs, st)
+                       : (LO == 32 ? launch_tc<false, 32>(p, n_jobs, st) : launch_tc<false, 16>(p, n_jobs, st));
   if (e != cudaSuccess) return e;
   const int threads = 256;
   const int64_t blocks = (total * n_jobs + threads - 1) / threads;
