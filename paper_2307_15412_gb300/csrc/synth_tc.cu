@@ -6,11 +6,11 @@
 //   phi = c0 + c1 m + (b0 + b1 m) n      (cycles),
 //   c0 = f0 d / c (reduced modulo 1 in FP64), c1 = f0 ddot T_rep / c,
 //   b0 = S dt d / c, b1 = S dt ddot T_rep / c.
-// Time is split as t_n = t_hi + t_lo with n = LO h + l (LO = 16): the rows
-// of the GEMM are (chirp m, h) pairs, its columns the fast-time offsets l,
-// its reduction index the hits.  A tile of 128 rows holds mc chirps of
-// HE = max(HI, 8) rows each (HI = N / 16; rows h >= HI are zero padding, so
-// mc = 128 / HE <= 16).  Around the tile's centre chirp m_c, m = m_c + mu:
+// Time is split as t_n = t_hi + t_lo with n = LO h + l (LO = 16, or 32 for
+// split-BF16x3 chirps of >= 256 samples): the rows of the GEMM are (chirp
+// m, h) pairs, its columns the fast-time offsets l, its reduction index the
+// hits.  A tile of 128 rows holds mc chirps of HE = max(HI, 8) rows each
+// (HI = N / LO; rows h >= HI are zero padding, so mc = 128 / HE <= 16).  Around the tile's centre chirp m_c, m = m_c + mu:
 //   phi = [c0 + c1 m + beta_m LO h + b1 mu l_c] + beta_c l + b1 mu (l - l_c),
 //   beta_m = b0 + b1 m, beta_c = b0 + b1 m_c, l_c = (LO - 1) / 2.
 // The coupling exp(-j 2 pi b1 mu (l - l_c)) is expanded to third order,
@@ -19,8 +19,9 @@
 // x^4 / 24, x <= 2 pi |b1| max|mu| (LO - 1) / 2 (centring l halves x); every
 // hit checks x <= 0.157 (remainder <= 2.6e-5 relative, a quarter of the
 // split-BF16x3 tolerance) and latches ERR_TC_BOUND otherwise.  For the
-// full-frame radar (N = 256, 8 chirps per tile) at |d-dot| = 2 m/s,
-// x = 1.1e-3; for N = 128 (16 chirps), 4.7e-3.
+// full-frame radar at |d-dot| = 2 m/s, x = 1.1e-3 with LO = 16 (N = 256,
+// 8 chirps per tile) and 4.9e-3 with LO = 32 (16 chirps per tile); for
+// N = 128 (LO = 16, 16 chirps), 4.7e-3.
 //
 // The b1 factor of each term belongs to the hit and mu to the row, so the
 // terms are carried in the GEMM's N dimension:
@@ -30,8 +31,8 @@
 // with kappa applied per row in the epilogue.  Each CTA uses the T <= 4
 // terms its hits need (x^T / T! below the variant's rounding; T = 1 for a
 // static scene or a one-chirp tile).  Complex values are made real by
-// doubling the columns: D = [t][Re | Im][l] is 128 x 32 T (M = 128,
-// N = 32 T); the reduction runs over (hit, re/im), 2 entries per hit, with
+// doubling the columns: D = [t][Re | Im][l] is 128 x 2 LO T (M = 128,
+// N = 2 LO T); the reduction runs over (hit, re/im), 2 entries per hit, with
 // B = [[Re B_t, Im B_t], [-Im B_t, Re B_t]].  Variants: BF16x3
 // (x = x_hi + x_lo in bfloat16, products lo*hi + hi*lo + hi*hi, kind::f16)
 // and TF32 (inputs rounded to TF32 in the producer, kind::tf32); FP32
@@ -39,10 +40,10 @@
 //
 // Per CTA: one (frame, channel, 128-row tile) and an interleaved share of
 // its hits (split-K).  Sixteen producer warps generate blocks of 32 hits
-// (lane = hit) into a ring of three 64 KB shared-memory stages in the
+// (lane = hit) into a ring of up to three shared-memory stages in the
 // 128-byte swizzled K-major layout (one warp store fills one 128-byte row,
 // free of bank conflicts); warp w writes the 8 A rows of its (chirp,
-// h-segment) unit and the B columns of offset l = w.  One lane of warp 16
+// h-segment) unit and the B columns of offsets l = (LO / 16) w + dl.  One lane of warp 16
 // issues the MMAs of a full stage and commits them to the stage's empty
 // barrier.  Every 64 blocks warps 0-3 fold the accumulator into an FP32
 // row buffer (long chains in tensor memory lose precision).  All waits are
@@ -577,7 +578,7 @@ k_synth_tc(const SynthTcParams p) {
   }
 
   // ---- epilogue: warps 0-3 fold the last chain into their rows and write
-  // them (row 32 w + lane = (chirp, h): 16 complex samples n = 16 h + l)
+  // them (row 32 w + lane = (chirp, h): LO complex samples n = LO h + l)
   if (warp < 4) {
     bool have = nb > 0;
     if (!mbar_wait(smem_u32(&s_done), 0)) {
