@@ -47,7 +47,7 @@ VARIANT, VARIANT_NAME = SYNTH_TC_BF16X3, "tensor-core split-BF16x3 (tcgen05)"
 # dram__bytes_read.sum + dram__bytes_write.sum of one k_synth_tc launch on
 # this workload (ncu capture of the current kernel, 16 frames); retaken
 # whenever the kernel changes, else reported as null
-SYNTH_TC_DRAM_BYTES = 3.398656e6
+SYNTH_TC_DRAM_BYTES = None
 
 
 def _peaks():
@@ -363,13 +363,14 @@ def run_gpu(args):
                            "mean_hits_per_frame": float(np.mean(counts)),
                            "l2": "flushed before every timed step (256 MiB write, outside the events)",
                            "execution": "rr_batch_run: one launch per stage over all frames of the step, "
-                                        "replayed from a CUDA graph; autotuned tile shape and split-K",
+                                        "replayed from a CUDA graph; autotuned ray-tile shape; synthesis shared out "
+                                        "over one CTA per SM (equal producer work per SM)",
                            "parallelism": "replicas (independent frames per GPU)"},
-                "roofline": {"bound": "tensor", "kernel": "k_synth_tc<BF16x3> (+ split-K sum), all frames of a step",
+                "roofline": {"bound": "tensor", "kernel": "k_synth_tc<BF16x3> (+ per-hit constants), all frames of a step",
                              "achieved": achieved, "peak": peak_tc, "unit": "TFLOP/s", "frac": achieved / peak_tc,
                              "traffic": SYNTH_TC_DRAM_BYTES, "traffic_unit": "bytes per launch (ncu)",
                              "work": "algorithmic: 8 flop per complex MAC of Eq. 4 (the kernel issues 3 T x as many "
-                                     "tensor flops: T expansion terms, 2 for these hands, x 3 BF16 products)",
+                                     "tensor flops: T expansion terms, 2 or 3 for these hands, x 3 BF16 products)",
                              "timing": "synthesis stage of %d eager steps (CUDA events on the library stream)" % KS,
                              "peak_source": "MEASURED_PEAKS.json bf16_tflops_sustained (of measured)"},
                 "plain_fp32": {"value": fp32_value, "unit": "frames/s", "steps": K32,

@@ -247,9 +247,9 @@ typedef struct {
  * flags: RR_BATCH_GRAPH captures the enqueued work as a CUDA graph on the
  * first call of a batch (after one eager run) and replays it on later calls
  * with identical jobs, radar, outputs and scene buffers (any change
- * re-captures); RR_BATCH_AUTOTUNE times the candidate ray-tile shapes and
- * split-K factors once per batch shape and keeps the fastest (results are
- * the same up to FP32 summation order).  The hit lists of a batch live in
+ * re-captures); RR_BATCH_AUTOTUNE times the candidate ray-tile shapes (and,
+ * for RR_SYNTH_FP32, split-K factors) once per batch shape and keeps the
+ * fastest (results are the same up to FP32 summation order).  The hit lists of a batch live in
  * the context (one segment of n_az * n_el hits per frame), not in the
  * scenes: rr_get_hits does not see them.  Errors as for the single-frame
  * calls; device-side errors surface at rr_sync. */
@@ -258,7 +258,8 @@ rr_status rr_batch_run(rr_ctx *ctx, const rr_job *jobs, int n_jobs, const rr_rad
 
 /* The plan of the context's last rr_batch_run (after autotuning): the ray
  * tile (2^ray_tile_log2 x 2^(5 - ray_tile_log2) rays per warp), the split-K
- * factor of the synthesis, the largest builder cluster used for meshes of up
+ * factor of the FP32 synthesis (1 for the tensor-core variants, which share
+ * the work out over one CTA per SM instead), the largest builder cluster used for meshes of up
  * to 8 x 3840 triangles (16 for larger ones alone, 0 if none was
  * cluster-built), and the number of kernels one such batch enqueues (a
  * graph replay runs the same ones).  Meshes are built by clusters of 1 to 16

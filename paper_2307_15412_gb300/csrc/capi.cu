@@ -215,10 +215,10 @@ rr_status run_synth(rr_ctx *c, const rr_radar *r, rr_synth_variant v, const uint
             "synth_if launch");
     return RR_OK;
   }
-  const int64_t need = rr::synth_tc_partial_floats(rd, v == RR_SYNTH_TC_TF32, kmax, 1, 0);
+  const int64_t need = rr::synth_tc_scratch_floats(rd, v == RR_SYNTH_TC_TF32, 1);
   RR_CUDA(c, grow(c->partials, c->partials_cap, need), "synth partials");
   RR_CUDA(c, grow(c->tc_cst, c->tc_cst_cap, (int64_t)r->n_rx * (ld > 0 ? ld : 1)), "synth constants");
-  RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, nullptr, 0, c->partials,
+  RR_CUDA(c, rr::launch_synth_tc(rd, v == RR_SYNTH_TC_TF32, count, kmax, ld, d, a, dd, nullptr, 1, c->partials,
                                  c->partials_cap, out, c->d_err, c->tc_cst, d, c->stream),
           "synth_if launch (tensor cores)");
   return RR_OK;
@@ -683,7 +683,7 @@ struct BatchPlan {
 
 int64_t batch_partials_need(const BatchPlan &P, int split) {
   if (P.variant == RR_SYNTH_FP32) return rr::synth_batch_partial_floats(P.rd, P.kmax, P.n_jobs, split);
-  return rr::synth_tc_partial_floats(P.rd, P.variant == RR_SYNTH_TC_TF32, P.kmax, P.n_jobs, split);
+  return rr::synth_tc_scratch_floats(P.rd, P.variant == RR_SYNTH_TC_TF32, P.n_jobs);
 }
 
 // The frames of a batch by decreasing hit count (written by the trace
@@ -695,7 +695,7 @@ cudaError_t batch_synth(rr_ctx *c, const BatchPlan &P, int split, cudaStream_t s
   if (P.variant == RR_SYNTH_FP32)
     return rr::launch_synth_fp32_batch(P.rd, b.ftab, P.n_jobs, P.kmax, split, b.partials, b.partials_cap, P.ifb, st);
   return rr::launch_synth_tc(P.rd, P.variant == RR_SYNTH_TC_TF32, nullptr, P.kmax, 0, nullptr, nullptr, nullptr, b.ftab,
-                             P.n_jobs, batch_order(c, P.n_jobs), split, b.partials, b.partials_cap, P.ifb, c->d_err, b.tc_cst, b.d, st);
+                             P.n_jobs, b.partials, b.partials_cap, P.ifb, c->d_err, b.tc_cst, b.d, st);
 }
 
 // Enqueues one batch on stream st: no allocation, no host wait, so the same
@@ -761,7 +761,8 @@ cudaError_t batch_autotune(rr_ctx *c, BatchPlan P, int *tw_out, int *split_out) 
   }
   best = INFINITY;
   const int splits[4] = {0, 1, 2, 4};
-  for (int k = 0; k < 4 && e == cudaSuccess; ++k) {
+  // (the tensor-core synthesis has no split factor: one CTA per SM)
+  for (int k = 0; k < (P.variant == RR_SYNTH_FP32 ? 4 : 0) && e == cudaSuccess; ++k) {
     if (batch_partials_need(P, splits[k]) > b.partials_cap) continue;
     for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
       if ((e = cudaEventRecord(e0, st)) != cudaSuccess) break;
@@ -976,8 +977,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
       split = rr::synth_fp32_batch_split(P.rd, P.kmax, n_jobs, P.split);
       launches += 2;
     } else {
-      split = rr::synth_tc_split(P.rd, variant == RR_SYNTH_TC_TF32, P.kmax, n_jobs, P.split);
-      launches += split > 1 ? 3 : 2;
+      split = 1;  // one CTA per SM over equal shares of the work
+      launches += 2;
     }
     if (rd_out) launches += radar->n_chirps > 1 ? 2 : 1;
     b.last_tw = P.tw;

@@ -184,18 +184,22 @@ cudaError_t launch_synth_fp32_batch(const RadarDev &r, const FrameJob *jobs, int
 // (jobs == nullptr: d/a/dd/ld/count/kmax) or a FrameJob table of n_jobs
 // frames; tf32 selects kind::tf32, else split-BF16x3.
 bool synth_tc_supported(const RadarDev &r);
-int64_t synth_tc_partial_floats(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split);
+// Device scratch (in floats) of one tensor-core synthesis launch over
+// n_jobs frames: partial tiles of the items that CTAs share, the launch's
+// plan and its counters.  Independent of the hit counts.
+int64_t synth_tc_scratch_floats(const RadarDev &r, bool tf32, int n_jobs);
+// The split-K factor the FP32 batch launcher uses (split <= 0: its own choice).
+int synth_fp32_batch_split(const RadarDev &r, int64_t kmax, int n_jobs, int split);
+// Enqueues a small memset and two kernels on st (per-hit constants with the
+// plan, then the synthesis on one CTA per SM); out: [n_jobs][n_rx][M][N]
+// complex, every element written.
 // cst: float4 scratch laid out like the hit arrays (at least n_rx * ld
 // entries past d_base: d_base = d for one frame, the base of the batch hit
 // arrays for a batch) for the per-hit constants.
-// The split-K factor the launchers use for a batch (split <= 0: their own choice).
-int synth_tc_split(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split);
-int synth_fp32_batch_split(const RadarDev &r, int64_t kmax, int n_jobs, int split);
-// order (may be null): device int[n_jobs], the frames in launch order.
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
-                            const int *order, int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
-                            float4 *cst, const float *d_base, cudaStream_t st);
+                            float *scratch, int64_t scratch_cap_floats, float *out, uint32_t *err, float4 *cst,
+                            const float *d_base, cudaStream_t st);
 // Learned-surrogate kernels (see mlp.cu).  gemm_tn: C = A B^T with A
 // [M][K], B [N][K] BF16 row-major (K a multiple of 8, 16-byte aligned),
 // + bias[N], act 1 = ReLU, mask [M][N] BF16 (zero where mask <= 0); outputs

@@ -38,17 +38,21 @@
 // and TF32 (inputs rounded to TF32 in the producer, kind::tf32); FP32
 // accumulation in tensor memory in both.
 //
-// Per CTA: one (frame, channel, 128-row tile) and an interleaved share of
-// its hits (split-K).  Sixteen producer warps generate blocks of 32 hits
+// Work: one CTA per SM, each taking an equal share of the launch's cost
+// units (stream-K; the plan and the slot scheme are described at the
+// kernel).  An item is one (frame, channel, 128-row tile) over all its
+// hits; a CTA runs its share as consecutive runs of blocks of 32 hits, one
+// run per item it touches.  Sixteen producer warps generate the blocks
 // (lane = hit) into a ring of up to three shared-memory stages in the
 // 128-byte swizzled K-major layout (one warp store fills one 128-byte row,
 // free of bank conflicts); warp w writes the 8 A rows of its (chirp,
-// h-segment) unit and the B columns of offsets l = (LO / 16) w + dl.  One lane of warp 16
-// issues the MMAs of a full stage and commits them to the stage's empty
-// barrier.  Every 64 blocks warps 0-3 fold the accumulator into an FP32
-// row buffer (long chains in tensor memory lose precision).  All waits are
-// bounded; a wait that runs out latches ERR_TIMEOUT, drains what it can and
-// frees the tensor memory.
+// h-segment) unit and the B columns of offsets l = (LO / 16) w + dl.  One
+// lane of warp 16 issues the MMAs of a full stage and commits them to the
+// stage's empty barrier.  At the end of a run and every 64 blocks inside
+// one, warps 0-3 fold the accumulator into an FP32 row buffer (long chains
+// in tensor memory lose precision); at the end of a run they write it out.
+// All waits are bounded; a wait that runs out latches ERR_TIMEOUT, drains
+// what it can and frees the tensor memory.
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <math.h>
@@ -77,18 +81,30 @@ struct SynthTcParams {
   int64_t ld;
   const uint32_t *count;
   int64_t kmax;
-  int n_rx, M, N, HI, mc, n_tiles, S;
+  int n_rx, M, N, HI, mc, n_tiles;
+  int n_jobs, n_pairs;     // pairs = (frame, channel), pair id = frame * n_rx + channel
+  int LO, tf32;
+  float mu_max;            // half the chirp span of a full tile
   double f0_c, kb;
   float c1k, b1k;
-  float *partials;        // [jobs][S][n_rx][M][N] complex
+  float *out;              // [jobs][n_rx][M][N] complex
+  float *slots;            // [2 CTAs][LO / 2][128] float4: tiles of items shared by CTAs
   const FrameJob *jobs;
-  const int *order;       // frames in launch order (largest hit lists first) or null
   uint32_t *err;
   // per-hit constants (c0, c1, b0, b1) laid out like the hit arrays: entry
   // (hit_d pointer - d_base) + j * ld + k for hit k of channel j
   float4 *cst;
   const float *d_base;
+  // the launch's plan (see k_tc_consts): ticket and bmax are zeroed before
+  // every launch, the rest is written by the last block of k_tc_consts
+  uint32_t *ticket;        // k_tc_consts blocks done
+  uint32_t *bmax;          // [pairs] largest |b1| of the pair's hits (FP32 bits)
+  int64_t *pl_cost;        // [pairs + 1] cost units before each pair (plan order)
+  int32_t *pl_pair;        // [pairs] pair id | T << 24, by T (largest first), then pair id
+  int32_t *pl_nb;          // [pairs] blocks of kHitsPerBlock hits per tile
+  uint32_t *cnt;           // [pairs][n_tiles][4] arrivals per item and row quarter
 };
+
 
 __device__ __forceinline__ uint32_t smem_u32(const void *p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -228,13 +244,17 @@ __device__ __forceinline__ uint64_t smem_desc_sw128(uint32_t addr) {
 }
 
 // Terms the coupling expansion needs for a largest phase x = 2 pi |b1|
-// mu_max l_c: the smallest T with remainder x^T / T! <= eps, eps = 2^-20
-// for BF16x3 (twenty times below its operand rounding, about 2^-16 per
-// product) and 2^-14 for TF32 (seven times below 2^-11); at most kTerms
-// (x <= 0.157 is checked per hit).
-template <bool TF32>
-__device__ __forceinline__ int expansion_terms(float x) {
-  const float eps = TF32 ? 6.103515625e-05f : 9.5367431640625e-07f;
+// mu_max l_c: the smallest T with remainder x^T / T! <= eps, at most kTerms
+// (x <= 0.157 is checked per hit).  The bound holds at the tile's corners
+// (|mu| = mu_max, |l - l_c| = l_c); the remainder scales as (mu (l -
+// l_c))^T, so its RMS over a tile is a fifth of the corner value at T = 2
+// (E[mu^4] E[(l - l_c)^4] / (mu_max l_c)^4 = 1/25 for uniform mu and l).
+// eps = 2^-16 for BF16x3: the corner error is at most one rounding unit of
+// its split-BF16 products (about 2^-16 each), and the rel-L2 it adds is a
+// fifth of that.  eps = 2^-14 for TF32: eight times below its 2^-11
+// rounding, since TF32 frames sit close to the 1e-3 bound already.
+__device__ __forceinline__ int expansion_terms(float x, bool tf32) {
+  const float eps = tf32 ? 6.103515625e-05f : 1.52587890625e-05f;
   float r = x;  // x^T / T! for T = 1, 2, 3
   if (r <= eps) return 1;
   r *= 0.5f * x;
@@ -280,8 +300,8 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ca, uint32_t cb, uint32_t *
 // the hi x lo product of term t sits NT = 2 LO nt columns further and is
 // added to it.
 template <int LO>
-__device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
-                                         float *acc) {
+__device__ __noinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
+                                      float *acc) {
   const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   const uint32_t NT = 2u * LO * (uint32_t)nt;
 #pragma unroll
@@ -311,47 +331,209 @@ __device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool s
   }
 }
 
+// Cost units of one block of kHitsPerBlock hits with T expansion terms: the
+// operand stores of one producer warp (8 A rows, LO / 8 B columns per term).
+__host__ __device__ __forceinline__ int block_cost(int LO, int T) { return 8 + (LO / 8) * T; }
+
+// The CTA that owns the block starting at cost unit s when W units are
+// shared by P CTAs, CTA c taking [floor(W c / P), floor(W (c + 1) / P)).
+__device__ __forceinline__ int cost_owner(int64_t s, int64_t W, int P) { return (int)(((s + 1) * P - 1) / W); }
+
+// One (frame, channel, tile) item's run of blocks inside a CTA's share.
+struct Seg {
+  int q, j, tile, T;
+  int nb;           // blocks per tile of the item's pair
+  int b0, n;        // first block inside the item, blocks in the run
+  int pi;           // the pair's position in the plan
+  bool head, tail;  // the item also has blocks in the previous / next CTA
+};
+
+// Walks the blocks whose cost start lies in [lo, hi): pair by pair in plan
+// order, tile by tile inside a pair, blocks of a tile in hit order.  The
+// plan is read from the launch parameters and hi is passed to every call,
+// so the walk holds only two registers (the launcher keeps a pair's blocks
+// below 2^31).
+struct SegWalk {
+  int g;  // next block of pair i (tile-major)
+  int i;
+
+  __device__ static int first_block(int64_t pos, int64_t Ci, int G, int u) {
+    if (pos <= Ci) return 0;
+    const int64_t f = (pos - Ci + u - 1) / u;
+    return f < G ? (int)f : G;
+  }
+  __device__ void init(const SynthTcParams &p, int64_t lo) {
+    int a = 0, b = p.n_pairs - 1;  // the last pair starting at or before lo
+    while (a < b) {
+      const int m = (a + b + 1) >> 1;
+      if (p.pl_cost[m] <= lo) a = m;
+      else b = m - 1;
+    }
+    i = a;
+    g = first_block(lo, p.pl_cost[i], p.pl_nb[i] * p.n_tiles, block_cost(p.LO, p.pl_pair[i] >> 24));
+  }
+  __device__ bool next(const SynthTcParams &p, int64_t hi, Seg &s) {
+    while (i < p.n_pairs) {
+      const int32_t pk = p.pl_pair[i];
+      const int T = pk >> 24, u = block_cost(p.LO, T);
+      const int nb = p.pl_nb[i], G = nb * p.n_tiles;
+      const int64_t Ci = p.pl_cost[i];
+      if (g >= G) {
+        ++i;
+        g = 0;
+        continue;
+      }
+      if (Ci + (int64_t)g * u >= hi) return false;
+      const int gend = first_block(hi, Ci, G, u);
+      const int t = g / nb;
+      const int e = min((t + 1) * nb, gend);
+      const int pid = pk & 0xFFFFFF;
+      s.q = pid / p.n_rx;
+      s.j = pid - s.q * p.n_rx;
+      s.tile = t;
+      s.T = T;
+      s.nb = nb;
+      s.b0 = g - t * nb;
+      s.n = e - g;
+      s.pi = i;
+      s.head = s.b0 > 0;
+      s.tail = e < (t + 1) * nb;
+      g = e;
+      return true;
+    }
+    return false;
+  }
+};
+
+// Warps 0-3 of k_synth_tc: write this thread's folded row (acc: 2 LO floats,
+// Re then Im) of a finished run (plan position pi, tile | head << 30 |
+// tail << 31).  An item inside one CTA goes straight to the output; an item
+// shared by several CTAs goes to this CTA's slot, and the last of its CTAs
+// to arrive (a counter per item and row quarter) sums the slots in CTA
+// order into the output.  Out of line: it runs a few times per CTA.
+template <int LO>
+__device__ __noinline__ void flush_run(const SynthTcParams &p, int pi, int tf, const float *accr, int my_row, int my_mi,
+                                       int my_h, int64_t W, int P) {
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  Seg s;
+  {
+    const int32_t pk = p.pl_pair[pi];
+    const int pid = pk & 0xFFFFFF;
+    s.q = pid / p.n_rx;
+    s.j = pid - s.q * p.n_rx;
+    s.T = pk >> 24;
+    s.nb = p.pl_nb[pi];
+    s.pi = pi;
+    s.tile = tf & 0x3FFFFFFF;
+    s.head = (tf >> 30) & 1;
+    s.tail = (tf >> 31) & 1;
+  }
+  const int m0 = s.tile * p.mc;
+  const bool live = my_mi < min(p.mc, p.M - m0) && my_h < p.HI;
+  float4 *o = reinterpret_cast<float4 *>(
+      p.out + 2 * ((((int64_t)s.q * p.n_rx + s.j) * p.M + (m0 + my_mi)) * (int64_t)p.N + (int64_t)my_h * LO));
+  if (!s.head && !s.tail) {
+    if (live) {
+#pragma unroll
+      for (int q = 0; q < LO / 2; ++q)
+        o[q] = make_float4(accr[2 * q], accr[LO + 2 * q], accr[2 * q + 1], accr[LO + 2 * q + 1]);
+    }
+    return;
+  }
+  const int c = blockIdx.x;
+  float4 *sl = reinterpret_cast<float4 *>(p.slots) + (int64_t)(s.head ? 2 * c : 2 * c + 1) * (LO / 2) * 128;
+#pragma unroll
+  for (int q = 0; q < LO / 2; ++q)
+    __stcg(&sl[q * 128 + my_row], make_float4(accr[2 * q], accr[LO + 2 * q], accr[2 * q + 1], accr[LO + 2 * q + 1]));
+  __threadfence();
+  __syncwarp();
+  const int64_t item = ((int64_t)s.q * p.n_rx + s.j) * p.n_tiles + s.tile;
+  uint32_t old = 0;
+  if (lane == 0) old = atomicAdd(&p.cnt[item * 4 + (warp & 3)], 1u);
+  old = __shfl_sync(0xffffffffu, old, 0);
+  // contributors: the owners of the item's first and last blocks
+  const int u = block_cost(LO, s.T);
+  const int64_t c0 = p.pl_cost[s.pi] + (int64_t)s.tile * s.nb * u;
+  const int cf = cost_owner(c0, W, P), cl = cost_owner(c0 + (int64_t)(s.nb - 1) * u, W, P);
+  if (old != (uint32_t)(cl - cf)) return;
+  __threadfence();
+  if (!live) return;
+  const float4 *slots = reinterpret_cast<const float4 *>(p.slots);
+#pragma unroll 4
+  for (int q = 0; q < LO / 2; ++q) {
+    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int cc = cf; cc <= cl; ++cc) {
+      const float4 x = __ldcg(&slots[(int64_t)(cc == cf ? 2 * cc + 1 : 2 * cc) * (LO / 2) * 128 + q * 128 + my_row]);
+      v.x += x.x;
+      v.y += x.y;
+      v.z += x.z;
+      v.w += x.w;
+    }
+    o[q] = v;
+  }
+}
+
 // LO: fast-time offsets per row (16, or 32 for BF16x3 chirps of >= 256
 // samples: twice the samples per A row, the B operand and the accumulator
 // twice as wide).
+//
+// Work split (stream-K): the plan lists every (frame, channel, tile) item's
+// blocks of 32 hits with a cost per block; CTA c takes the blocks whose
+// cost start lies in its equal share of the total, so every SM gets the
+// same producer work whatever the hit counts.  An item inside one CTA is
+// written straight to the output; an item shared by several CTAs is
+// written by each into a slot (2 per CTA: the item continuing from the
+// previous CTA, the one continuing into the next), and the last of them to
+// arrive (a counter per item and row quarter) sums the slots in CTA order
+// and writes the output, so the result does not depend on timing.  The
+// pairs are ordered by their term count, largest first, and a CTA runs
+// with the terms of its first pair.
 template <bool TF32, int LO>
 __global__ void __launch_bounds__(kTcThreads, 1)
-k_synth_tc(const SynthTcParams p) {
-  constexpr float LC = 0.5f * (float)(LO - 1);        // centre l_c of the fast-time offsets
+k_synth_tc(const __grid_constant__ SynthTcParams p) {
   constexpr int kTmemCols = LO == 16 ? 256 : 512;     // hi x hi (+ lo x hi) and hi x lo products
   constexpr int FS = fold_stride<LO>();
   extern __shared__ __align__(1024) unsigned char smem[];
   __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done, s_fold, s_folded;
   __shared__ uint32_t s_tmem;
-  __shared__ uint32_t s_bmax;  // largest |b1| among this CTA's hits (FP32 bits)
+  __shared__ long long s_lo, s_hi, s_W;
+  __shared__ int s_P, s_nblocks, s_nterms;
   __shared__ volatile int s_abort;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-  const int j = blockIdx.x % p.n_rx;
-  const int tile = blockIdx.x / p.n_rx;
-  const int s_idx = blockIdx.y;
-  const int job = p.order ? p.order[blockIdx.z] : (int)blockIdx.z;
-  const int m0 = tile * p.mc;
-  const int mvalid = min(p.mc, p.M - m0);
-  const float mcen = m0 + 0.5f * (float)(mvalid - 1);  // centre chirp of the tile
-  const float mu_max = 0.5f * (float)(mvalid - 1);
-
-  const float *dbase = p.d, *abase = p.a, *ddbase = p.dd;
-  int64_t ld = p.ld;
-  int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
-  if (p.jobs) {
-    const FrameJob &J = p.jobs[job];
-    dbase = J.hit_d;
-    abase = J.hit_a;
-    ddbase = J.hit_dd;
-    ld = J.ld;
-    K = min((int64_t)*J.count, J.cap);
+  if (tid == 0) {
+    // this CTA's share of the cost units; at least two blocks of the
+    // costliest kind per CTA, so every CTA between an item's first and last
+    // owner holds a block of it
+    const int64_t W = p.pl_cost[p.n_pairs];
+    int64_t P = W / (2 * block_cost(LO, kTerms));
+    if (P > (int64_t)gridDim.x) P = gridDim.x;
+    if (P < 1) P = 1;
+    int nbk = 0, nt = 1;
+    int64_t lo = 0, hi = 0;
+    if ((int64_t)blockIdx.x < P && W > 0) {
+      lo = W * (int64_t)blockIdx.x / P;
+      hi = W * (int64_t)(blockIdx.x + 1) / P;
+      SegWalk wk;
+      wk.init(p, lo);
+      Seg sg;
+      bool first = true;
+      while (wk.next(p, hi, sg)) {
+        if (first) nt = sg.T;
+        first = false;
+        nbk += sg.n;
+      }
+    }
+    s_lo = lo;
+    s_hi = hi;
+    s_W = W;
+    s_P = (int)P;
+    s_nblocks = nbk;
+    s_nterms = nt;
   }
-  const float *dj = dbase + (int64_t)j * ld;
-  const float *aj = abase + (int64_t)j * ld;
-  const float *ddj = ddbase + (int64_t)j * ld;
-  const int64_t nblk_all = (K + kHitsPerBlock - 1) / kHitsPerBlock;
-  const int nb = nblk_all > s_idx ? (int)((nblk_all - 1 - s_idx) / p.S + 1) : 0;  // this CTA's blocks
+  __syncthreads();
+  const int nb_cta = s_nblocks;
+  if (nb_cta == 0) return;
 
   if (warp == 16) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(&s_tmem)),
@@ -368,26 +550,13 @@ k_synth_tc(const SynthTcParams p) {
     mbar_init(smem_u32(&s_fold), 1);
     mbar_init(smem_u32(&s_folded), 128);
     s_abort = 0;
-    s_bmax = 0u;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
   const uint32_t tmem = s_tmem;
-  const float4 *cj = p.cst + (dj - p.d_base);  // this channel's per-hit constants
-  // the expansion's terms for this CTA, from the largest |b1| of its hits
-  if (warp < 16) {
-    float bm = 0.f;
-    for (int b = warp; b < nb; b += 16) {
-      const int64_t k = ((int64_t)s_idx + (int64_t)b * p.S) * kHitsPerBlock + lane;
-      if (k < K) bm = fmaxf(bm, fabsf(cj[k].w));
-    }
-    for (int o = 16; o; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
-    if (lane == 0 && bm > 0.f) atomicMax(&s_bmax, __float_as_uint(bm));  // non-negative: bits order as values
-  }
-  __syncthreads();
-  const int nterms = expansion_terms<TF32>(6.2831853f * __uint_as_float(s_bmax) * mu_max * LC);
+  const int nterms = s_nterms;
   // B columns: 2 LO per term (Re half, Im half); lo halves (BF16x3): A_lo
   // 16 KB after A_hi, B_lo right after the NT rows of B_hi, so that one MMA
   // of N = 2 NT reads [B_hi | B_lo] while 2 NT <= 256
@@ -400,46 +569,109 @@ k_synth_tc(const SynthTcParams p) {
   // accumulator rows of warps 0-3: row 32 w + lane = (chirp, h); fold buffer
   float *fold = reinterpret_cast<float *>(smem + kRingBytes);
   const int my_row = 32 * (warp & 3) + lane;
-  const int HEr = p.HI < 8 ? 8 : p.HI;
-  const int my_mi = my_row / HEr, my_h = my_row - my_mi * HEr;
-  const float my_sg = 6.2831853f * ((float)(m0 + my_mi) - mcen);
-  const float my_k2 = -0.5f * my_sg * my_sg, my_k3 = my_sg * my_sg * my_sg * (1.f / 6.f);
+  const int HE = p.HI < 8 ? 8 : p.HI;                // rows per chirp in a tile
+  const int my_mi = my_row / HE, my_h = my_row - my_mi * HE;
+  float *accr = fold + my_row * FS;
   if (warp < 4)
-    for (int q = 0; q < 2 * LO; ++q) fold[my_row * FS + q] = 0.f;
+    for (int q = 0; q < 2 * LO; ++q) accr[q] = 0.f;
 
+  // kappa of this thread's row in a tile: sg = 2 pi mu, k2, k3
+  auto row_consts = [&](int tile, float &sg, float &k2, float &k3) {
+    const int m0 = tile * p.mc;
+    const int mvalid = min(p.mc, p.M - m0);
+    sg = 6.2831853f * ((float)(m0 + my_mi) - ((float)m0 + 0.5f * (float)(mvalid - 1)));
+    k2 = -0.5f * sg * sg;
+    k3 = sg * sg * sg * (1.f / 6.f);
+  };
+  // warps 0-3: write this thread's folded row of a finished run
+  auto flush = [&](int pi, int tf) {
+    flush_run<LO>(p, pi, tf, accr, my_row, my_mi, my_h, s_W, s_P);
+  };
+
+  // the run the producers are on: plan position, tile | head << 30 | tail << 31
+  int cur_pi = 0, cur_tf = 0;
   if (warp < 16) {
     // ---- producers: lane = block-local hit; warp w writes the A rows
-    // 8 w .. 8 w + 7 (unit w: chirp w / nseg, segment w % nseg) and the eight
-    // B columns of fast-time offset l = w (4 terms x Re / Im).  In the
+    // 8 w .. 8 w + 7 (unit w: chirp w / nseg, segment w % nseg) and the B
+    // columns of offsets l = (LO / 16) w + dl (T terms x Re / Im).  In the
     // 128-byte swizzled layout one warp store covers a whole 128-byte row
-    // (32 hits), so the stores are free of bank conflicts.
-    const int HE = p.HI < 8 ? 8 : p.HI;              // rows per chirp in the tile
+    // (32 hits), so the stores are free of bank conflicts.  Warps 0-3 fold
+    // the accumulator every kMaxChain blocks of a run and at the end of
+    // every run but the CTA's last, then write the run out.
     const int nseg = HE / 8;                         // 8-row units per chirp (16 per tile)
-    const int mi = warp / nseg, seg = warp - mi * nseg;
-    const int hbase = 8 * seg;
-    // the constants of block b + 1 are loaded while block b is generated
+    const int mi = warp / nseg, seg8 = warp - mi * nseg;
+    const int hbase = 8 * seg8;
+    SegWalk wk;
+    wk.init(p, s_lo);
+    Seg s;
+    int kf = 0;  // folds done
+    // folds the finished chain of this warp's rows (warps 0-3); false if the wait ran out
+    auto fold_chain = [&](int tile) {
+      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_fold), kf & 1))) {
+        atomicOr(p.err, ERR_TIMEOUT);
+        s_abort = 1;
+        return false;
+      }
+      ++kf;
+      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+      float sg, k2, k3;
+      row_consts(tile, sg, k2, k3);
+      fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
+      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
+      return true;
+    };
+    // one flat loop over the CTA's blocks; a new run starts when bl reaches
+    // the run's length (the runs' lengths add up to nb_cta)
+    int bl = 0, rn = 0, b0 = 0, tile = 0, K = 0, m0 = 0, mvalid = 0;
+    float mcen = 0.f;
+    const float4 *cj = p.cst;
+    const float *aj = p.a;
     float4 cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
     float a_next = 0.f;
-    {
-      const int64_t k = (int64_t)s_idx * kHitsPerBlock + lane;
-      if (nb > 0 && k < K) {
-        cv_next = cj[k];
-        a_next = aj[k];
-      }
-    }
-    for (int b = 0; b < nb; ++b) {
+    for (int b = 0; b < nb_cta; ++b, ++bl) {
       if (s_abort) break;
-      if (warp < 4 && b > 0 && b % kMaxChain == 0) {
-        // fold the accumulator of the last kMaxChain blocks into the row buffer
-        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_fold), (b / kMaxChain - 1) & 1))) {
-          atomicOr(p.err, ERR_TIMEOUT);
-          s_abort = 1;
-          break;
+      if (bl == rn) {
+        // end of the previous run (not the CTA's last): fold and write it out
+        if (b > 0 && warp < 4) {
+          if (!fold_chain(tile)) break;
+          flush(cur_pi, cur_tf);
+          for (int q = 0; q < 2 * LO; ++q) accr[q] = 0.f;
         }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        fold_row<LO>(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, fold + (32 * warp + lane) * FS);
-        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
+        if (!wk.next(p, s_hi, s)) break;  // (never: nb_cta counts the runs' blocks)
+        const float *dbase = p.d, *abase = p.a;
+        int64_t ld = p.ld;
+        int64_t Kl = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+        if (p.jobs) {
+          const FrameJob &J = p.jobs[s.q];
+          dbase = J.hit_d;
+          abase = J.hit_a;
+          ld = J.ld;
+          Kl = min((int64_t)*J.count, J.cap);
+        }
+        K = (int)Kl;  // below 2^31 (checked by the launcher)
+        const float *dj = dbase + (int64_t)s.j * ld;
+        aj = abase + (int64_t)s.j * ld;
+        cj = p.cst + (dj - p.d_base);  // this channel's per-hit constants
+        tile = s.tile;
+        m0 = tile * p.mc;
+        mvalid = min(p.mc, p.M - m0);
+        mcen = m0 + 0.5f * (float)(mvalid - 1);  // centre chirp of the tile
+        b0 = s.b0;
+        rn = s.n;
+        bl = 0;
+        cur_pi = s.pi;
+        cur_tf = s.tile | (s.head ? 1 << 30 : 0) | (s.tail ? (int)(1u << 31) : 0);
+        // the constants of block b + 1 are loaded while block b is generated
+        cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
+        a_next = 0.f;
+        const int k = b0 * kHitsPerBlock + lane;
+        if (k < K) {
+          cv_next = cj[k];
+          a_next = aj[k];
+        }
+      } else if (warp < 4 && bl % kMaxChain == 0 && !fold_chain(tile)) {
+        break;  // the chain of the last kMaxChain blocks of this run is complete: folded
       }
       const int stg = b % nst;
       unsigned char *A = smem + stg * stage_bytes;
@@ -452,10 +684,10 @@ k_synth_tc(const SynthTcParams p) {
       const float4 cv = cv_next;
       const float a = a_next;
       {
-        const int64_t kn = ((int64_t)s_idx + (int64_t)(b + 1) * p.S) * kHitsPerBlock + lane;
+        const int kn = (b0 + bl + 1) * kHitsPerBlock + lane;
         cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
         a_next = 0.f;
-        if (b + 1 < nb && kn < K) {
+        if (bl + 1 < rn && kn < K) {
           cv_next = cj[kn];
           a_next = aj[kn];
         }
@@ -463,23 +695,23 @@ k_synth_tc(const SynthTcParams p) {
       const float c0 = cv.x, c1 = cv.y, b0 = cv.z, b1 = cv.w;
       // A: rows (chirp mi, h = hbase .. hbase + 7) of this hit
       {
-        float2 P = make_float2(0.f, 0.f), W = make_float2(1.f, 0.f);
+        float2 Pp = make_float2(0.f, 0.f), Wp = make_float2(1.f, 0.f);
         if (mi < mvalid) {
           const float fm = (float)(m0 + mi);
           const float beta = fmaf(fm, b1, b0);
-          const float cyc = fmaf(fm, c1, c0) + b1 * ((fm - mcen) * LC);
-          W = expm2pi(beta * (float)LO);
-          P = expm2pi(fmaf(beta * (float)LO, (float)hbase, cyc));
-          P.x *= a;
-          P.y *= a;
+          const float cyc = fmaf(fm, c1, c0) + b1 * ((fm - mcen) * (0.5f * (float)(LO - 1)));
+          Wp = expm2pi(beta * (float)LO);
+          Pp = expm2pi(fmaf(beta * (float)LO, (float)hbase, cyc));
+          Pp.x *= a;
+          Pp.y *= a;
         }
         // rows row0 .. row0 + 7 (row0 % 8 == 0, so row % 8 == q): P W^q
         // by a tree of depth 3 (W^2, W^4) instead of a chain of 7 products
         float2 R[8];
-        R[0] = P;
-        R[1] = cmul(P, W);
-        const float2 W2 = cmul(W, W);
-        R[2] = cmul(P, W2);
+        R[0] = Pp;
+        R[1] = cmul(Pp, Wp);
+        const float2 W2 = cmul(Wp, Wp);
+        R[2] = cmul(Pp, W2);
         R[3] = cmul(R[1], W2);
         const float2 W4 = cmul(W2, W2);
 #pragma unroll
@@ -504,7 +736,7 @@ k_synth_tc(const SynthTcParams p) {
         for (int dl = 0; dl < LO / 16; ++dl) {
           const int l = (LO / 16) * warp + dl;
           const float2 B0 = expm2pi(beta_c * (float)l);
-          const float bl = b1 * ((float)l - LC);
+          const float bl1 = b1 * ((float)l - 0.5f * (float)(LO - 1));
           float w = 1.f;  // (b1 (l - l_c))^t
 #pragma unroll
           for (int t = 0; t < kTerms; ++t) {
@@ -512,7 +744,7 @@ k_synth_tc(const SynthTcParams p) {
             const float re = w * B0.x, im = w * B0.y;
             put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + l, lane), re, -im);        // Re half
             put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + LO + l, lane), im, re);    // Im half
-            w *= bl;
+            w *= bl1;
           }
         }
       }
@@ -529,58 +761,72 @@ k_synth_tc(const SynthTcParams p) {
       const uint32_t id = idesc(TF32 ? 2u : 1u, NT);
       const bool packed = 2u * NT <= 256u;
       const uint32_t id2 = idesc(1u, packed ? 2u * NT : NT);
-      for (int b = 0; b < nb; ++b) {
-        if (s_abort) break;
-        const int stg = b % nst;
-        if (!mbar_wait(smem_u32(&s_full[stg]), (b / nst) & 1)) {
-          atomicOr(p.err, ERR_TIMEOUT);
-          s_abort = 1;
-          break;
-        }
-        const bool fresh = b % kMaxChain == 0;  // first block of an accumulation chain
-        if (b > 0 && fresh && !mbar_wait(smem_u32(&s_folded), (b / kMaxChain - 1) & 1)) {
-          atomicOr(p.err, ERR_TIMEOUT);
-          s_abort = 1;
-          break;
-        }
-        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-        const uint32_t a0 = smem_u32(smem + stg * stage_bytes), bb0 = a0 + kABytes;
-        if (TF32) {
-#pragma unroll 1
-          for (int ks = 0; ks < kHitsPerBlock / 4; ++ks) {
-            const uint32_t ko = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
-            mma<true>(tmem, smem_desc_sw128(a0 + ko), smem_desc_sw128(bb0 + ko), id, (!fresh || ks > 0) ? 1u : 0u);
+      SegWalk wk;
+      wk.init(p, s_lo);
+      Seg s;
+      int kf = 0, bl = 0, rn = 0;
+      {
+        for (int b = 0; b < nb_cta; ++b, ++bl) {
+          if (s_abort) break;
+          if (bl == rn) {
+            if (!wk.next(p, s_hi, s)) break;  // (never: nb_cta counts the runs' blocks)
+            rn = s.n;
+            bl = 0;
           }
-        } else {
-#pragma unroll 1
-          for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
-            const uint32_t ko = (uint32_t)ks * 32u;
-            const uint64_t ahi = smem_desc_sw128(a0 + ko), alo = smem_desc_sw128(a0 + lo_a + ko);
-            const uint64_t bhi = smem_desc_sw128(bb0 + ko);
-            const uint32_t acc = (!fresh || ks > 0) ? 1u : 0u;
-            if (packed) {
-              mma<false>(tmem, ahi, bhi, id2, acc);  // [hi x hi | hi x lo]
-            } else {
-              mma<false>(tmem, ahi, bhi, id, acc);                                       // hi x hi
-              mma<false>(tmem + NT, ahi, smem_desc_sw128(bb0 + lo_b + ko), id, acc);    // hi x lo
+          const int stg = b % nst;
+          if (!mbar_wait(smem_u32(&s_full[stg]), (b / nst) & 1)) {
+            atomicOr(p.err, ERR_TIMEOUT);
+            s_abort = 1;
+            break;
+          }
+          const bool fresh = bl % kMaxChain == 0;  // first block of an accumulation chain
+          if (b > 0 && fresh) {
+            if (!mbar_wait(smem_u32(&s_folded), kf & 1)) {
+              atomicOr(p.err, ERR_TIMEOUT);
+              s_abort = 1;
+              break;
             }
-            mma<false>(tmem, alo, bhi, id, 1u);  // += lo x hi
+            ++kf;
           }
+          asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+          const uint32_t a0 = smem_u32(smem + stg * stage_bytes), bb0 = a0 + kABytes;
+          if (TF32) {
+#pragma unroll 1
+            for (int ks = 0; ks < kHitsPerBlock / 4; ++ks) {
+              const uint32_t ko = (uint32_t)(ks >> 2) * 16384u + (uint32_t)(ks & 3) * 32u;
+              mma<true>(tmem, smem_desc_sw128(a0 + ko), smem_desc_sw128(bb0 + ko), id, (!fresh || ks > 0) ? 1u : 0u);
+            }
+          } else {
+#pragma unroll 1
+            for (int ks = 0; ks < kHitsPerBlock / 8; ++ks) {
+              const uint32_t ko = (uint32_t)ks * 32u;
+              const uint64_t ahi = smem_desc_sw128(a0 + ko), alo = smem_desc_sw128(a0 + lo_a + ko);
+              const uint64_t bhi = smem_desc_sw128(bb0 + ko);
+              const uint32_t acc = (!fresh || ks > 0) ? 1u : 0u;
+              if (packed) {
+                mma<false>(tmem, ahi, bhi, id2, acc);  // [hi x hi | hi x lo]
+              } else {
+                mma<false>(tmem, ahi, bhi, id, acc);                                       // hi x hi
+                mma<false>(tmem + NT, ahi, smem_desc_sw128(bb0 + lo_b + ko), id, acc);    // hi x lo
+              }
+              mma<false>(tmem, alo, bhi, id, 1u);  // += lo x hi
+            }
+          }
+          mma_commit(smem_u32(&s_empty[stg]));
+          const bool chain_end = bl + 1 == rn || (bl + 1) % kMaxChain == 0;
+          if (chain_end && b + 1 < nb_cta) mma_commit(smem_u32(&s_fold));
         }
-        mma_commit(smem_u32(&s_empty[stg]));
-        if ((b + 1) % kMaxChain == 0 && b + 1 < nb) mma_commit(smem_u32(&s_fold));
       }
-      // after the last block's MMAs (they complete in issue order); with no
-      // block at all the commit arrives at once
+      // after the last block's MMAs (they complete in issue order)
       mma_commit(smem_u32(&s_done));
     }
     __syncwarp();
   }
 
   // ---- epilogue: warps 0-3 fold the last chain into their rows and write
-  // them (row 32 w + lane = (chirp, h): LO complex samples n = LO h + l)
+  // the last run (row 32 w + lane = (chirp, h): LO complex samples n = LO h + l)
   if (warp < 4) {
-    bool have = nb > 0;
+    bool have = true;
     if (!mbar_wait(smem_u32(&s_done), 0)) {
       atomicOr(p.err, ERR_TIMEOUT);
       have = false;
@@ -588,16 +834,11 @@ k_synth_tc(const SynthTcParams p) {
     if (s_abort) have = false;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     have = __all_sync(0xffffffffu, have);
-    float *acc = fold + my_row * FS;
-    if (have) fold_row<LO>(tmem, warp, nterms, !TF32, my_sg, my_k2, my_k3, acc);
-    const int m = m0 + my_mi;
-    if (my_mi < mvalid && my_h < p.HI) {
-      float4 *o = reinterpret_cast<float4 *>(p.partials + 2 * (((((int64_t)job * p.S + s_idx) * p.n_rx + j) * p.M + m) *
-                                                                    (int64_t)p.N + (int64_t)my_h * LO));
-#pragma unroll
-      for (int q = 0; q < LO / 2; ++q)
-        o[q] = have ? make_float4(acc[2 * q], acc[LO + 2 * q], acc[2 * q + 1], acc[LO + 2 * q + 1])
-                    : make_float4(0.f, 0.f, 0.f, 0.f);
+    if (have) {
+      float sg, k2, k3;
+      row_consts(cur_tf & 0x3FFFFFFF, sg, k2, k3);
+      fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
+      flush(cur_pi, cur_tf);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
@@ -608,11 +849,80 @@ k_synth_tc(const SynthTcParams p) {
   }
 }
 
+// The launch's plan, built by one block of 256 threads once every block of
+// k_tc_consts has published its largest |b1|: per (frame, channel) pair its
+// expansion terms T (the remainder bound for a full tile's largest phase),
+// its blocks per tile, the pairs ordered by T (largest first, ties by pair
+// id), the cumulative cost of the pairs in that order, and zeroed item
+// counters.
+__device__ void tc_build_plan(const SynthTcParams &p, float lc) {
+  __shared__ int s_wcnt[8];
+  __shared__ long long s_wsum[8];
+  const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
+  const int np = p.n_pairs;
+  const float xs = 6.2831853f * p.mu_max * lc;  // phase x per unit |b1|
+  auto blocks_of = [&](int q) {
+    int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
+    if (p.jobs) K = min((int64_t)*p.jobs[q].count, p.jobs[q].cap);
+    const int64_t nb = (K + kHitsPerBlock - 1) / kHitsPerBlock;
+    return (int)(nb < 1 ? 1 : nb);
+  };
+  int base = 0;
+  for (int T = kTerms; T >= 1; --T) {
+    for (int c0 = 0; c0 < np; c0 += 256) {
+      const int pid = c0 + tid;
+      bool f = false;
+      if (pid < np) f = expansion_terms(xs * __uint_as_float(__ldcg(&p.bmax[pid])), p.tf32 != 0) == T;
+      const unsigned bal = __ballot_sync(0xffffffffu, f);
+      if (lane == 0) s_wcnt[w] = __popc(bal);
+      __syncthreads();
+      int off = 0, tot = 0;
+      for (int k = 0; k < 8; ++k) {
+        off += k < w ? s_wcnt[k] : 0;
+        tot += s_wcnt[k];
+      }
+      if (f) {
+        const int pos = base + off + __popc(bal & ((1u << lane) - 1u));
+        p.pl_pair[pos] = pid | (T << 24);
+        p.pl_nb[pos] = blocks_of(pid / p.n_rx);
+      }
+      base += tot;
+      __syncthreads();
+    }
+  }
+  long long run = 0;
+  if (tid == 0) p.pl_cost[0] = 0;
+  for (int c0 = 0; c0 < np; c0 += 256) {
+    const int i = c0 + tid;
+    long long x = 0;
+    if (i < np) x = (long long)p.n_tiles * p.pl_nb[i] * block_cost(p.LO, p.pl_pair[i] >> 24);
+    for (int o = 1; o < 32; o <<= 1) {
+      const long long y = __shfl_up_sync(0xffffffffu, x, o);
+      if (lane >= o) x += y;
+    }
+    if (lane == 31) s_wsum[w] = x;
+    __syncthreads();
+    long long off = 0, tot = 0;
+    for (int k = 0; k < 8; ++k) {
+      off += k < w ? s_wsum[k] : 0;
+      tot += s_wsum[k];
+    }
+    if (i < np) p.pl_cost[i + 1] = run + off + x;
+    run += tot;
+    __syncthreads();
+  }
+  const int64_t n_cnt = (int64_t)np * p.n_tiles * 4;
+  for (int64_t k = tid; k < n_cnt; k += 256) p.cnt[k] = 0u;
+}
+
 // Per-hit constants of the synthesis, once per (frame, channel, hit) for all
 // tiles: c0 = frac(f0 d / c) (the FP64 carrier reduction), c1 = f0 d-dot
-// T_rep / c, b0 = S dt d / c, b1 = S dt d-dot T_rep / c; and the check of
-// the coupling expansion's bound for the widest tile.
-__global__ void k_tc_consts(const SynthTcParams p, float mu_max, float lc) {
+// T_rep / c, b0 = S dt d / c, b1 = S dt d-dot T_rep / c; the check of the
+// coupling expansion's bound for a full tile; each pair's largest |b1|; and,
+// in the block that finishes last, the plan of the synthesis launch.
+__global__ void __launch_bounds__(256) k_tc_consts(const SynthTcParams p, float lc) {
+  __shared__ float s_wmax[8];
+  __shared__ int s_last;
   const int job = blockIdx.z, j = blockIdx.y;
   const float *dbase = p.d, *ddbase = p.dd;
   int64_t ld = p.ld;
@@ -627,65 +937,78 @@ __global__ void k_tc_consts(const SynthTcParams p, float mu_max, float lc) {
   const float *dj = dbase + (int64_t)j * ld, *ddj = ddbase + (int64_t)j * ld;
   float4 *cj = p.cst + (dj - p.d_base);
   bool bad = false;
+  float bm = 0.f;
   for (int64_t k = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; k < K; k += (int64_t)gridDim.x * blockDim.x) {
     const float d = dj[k], dd = ddj[k];
     const double x = p.f0_c * (double)d;
     const float b1 = p.b1k * dd;
     cj[k] = make_float4((float)(x - floor(x)), p.c1k * dd, (float)(p.kb * (double)d), b1);
-    if (6.2831853f * fabsf(b1) * mu_max * lc > 0.157f) bad = true;
+    bm = fmaxf(bm, fabsf(b1));
+    if (6.2831853f * fabsf(b1) * p.mu_max * lc > 0.157f) bad = true;
   }
-  if (__any_sync(0xffffffffu, bad) && (threadIdx.x & 31) == 0) atomicOr(p.err, ERR_TC_BOUND);
-}
-
-__global__ void k_tc_reduce(const float2 *__restrict__ partials, int S, int64_t total, int n_jobs,
-                            float2 *__restrict__ out) {
-  const int64_t x = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (x >= total * n_jobs) return;
-  const int64_t job = x / total, i = x - job * total;
-  const float2 *pj = partials + job * S * total;
-  float2 s = pj[i];
-  for (int k = 1; k < S; ++k) {
-    const float2 v = pj[(int64_t)k * total + i];
-    s.x += v.x;
-    s.y += v.y;
+  const int lane = threadIdx.x & 31;
+  if (__any_sync(0xffffffffu, bad) && lane == 0) atomicOr(p.err, ERR_TC_BOUND);
+  for (int o = 16; o; o >>= 1) bm = fmaxf(bm, __shfl_xor_sync(0xffffffffu, bm, o));
+  if (lane == 0) s_wmax[threadIdx.x >> 5] = bm;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float m = 0.f;
+    for (int k = 0; k < 8; ++k) m = fmaxf(m, s_wmax[k]);
+    if (m > 0.f) atomicMax(&p.bmax[job * p.n_rx + j], __float_as_uint(m));  // non-negative: bits order as values
+    __threadfence();
+    const uint32_t total = gridDim.x * gridDim.y * gridDim.z;
+    s_last = atomicAdd(p.ticket, 1u) == total - 1u;
   }
-  out[x] = s;
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  tc_build_plan(p, lc);
 }
 
 struct TcPlan {
-  int HI, mc, n_tiles, S;
+  int HI, mc, n_tiles;
 };
 
 // Fast-time offsets per row: 32 for BF16x3 chirps of >= 256 samples (8 or
 // more rows per chirp, no padding), else 16.
 int tc_lo(const RadarDev &r, bool tf32) { return (!tf32 && r.N >= 256) ? 32 : 16; }
 
-TcPlan tc_plan(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
+TcPlan tc_plan(const RadarDev &r, bool tf32) {
   TcPlan pl;
   pl.HI = r.N / tc_lo(r, tf32);
   pl.mc = 128 / (pl.HI < 8 ? 8 : pl.HI);
   pl.n_tiles = (r.M + pl.mc - 1) / pl.mc;
-  int sms = 152, dev = 0;
-  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-  const int64_t ctas = (int64_t)pl.n_tiles * r.n_rx * n_jobs;
-  const int64_t blocks = (kmax + kHitsPerBlock - 1) / kHitsPerBlock;
-  int64_t S = split;
-  if (S <= 0) {  // one CTA per SM at a time: pick the split with the least idle tail
-    double best = 1e30;
-    for (int64_t c = 1; c <= 8; ++c) {
-      const double waves = (double)((ctas * c + sms - 1) / sms);
-      const double cost = waves / c + 0.02 * c;  // per-CTA fixed cost (set-up, epilogue, partials)
-      if (cost < best) { best = cost; S = c; }
-    }
-  }
-  if (S > blocks) S = blocks;
-  if (S < 1) S = 1;
-  pl.S = (int)S;
   return pl;
 }
 
+int sm_count() {
+  int sms = 152, dev = 0;
+  if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  return sms < 1 ? 1 : sms;
+}
+
+// Scratch of one launch, in 4-byte words: the slots (2 per CTA of 128 rows
+// x 2 LO floats), then ticket, bmax, plan and item counters.
+struct TcScratch {
+  int64_t ticket, bmax, cost, pair, nb, cnt, total;
+};
+
+TcScratch tc_scratch(const RadarDev &r, bool tf32, int n_jobs) {
+  const int64_t LO = tc_lo(r, tf32);
+  const int64_t np = (int64_t)n_jobs * r.n_rx;
+  TcScratch L;
+  L.ticket = 2 * (int64_t)sm_count() * 128 * 2 * LO;
+  L.bmax = L.ticket + 1;
+  L.cost = (L.bmax + np + 1) & ~(int64_t)1;  // 8-byte aligned
+  L.pair = L.cost + 2 * (np + 1);
+  L.nb = L.pair + np;
+  L.cnt = L.nb + np;
+  L.total = L.cnt + np * tc_plan(r, tf32).n_tiles * 4;
+  return L;
+}
+
 template <bool TF32, int LO>
-cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
+cudaError_t launch_tc(const SynthTcParams &p, cudaStream_t st) {
   static bool attr_set = false;
   constexpr int smem = smem_bytes_tc<LO>();
   if (!attr_set) {
@@ -693,73 +1016,72 @@ cudaError_t launch_tc(const SynthTcParams &p, int n_jobs, cudaStream_t st) {
     if (e != cudaSuccess) return e;
     attr_set = true;
   }
-  dim3 grid(p.n_tiles * p.n_rx, p.S, n_jobs);
-  k_synth_tc<TF32, LO><<<grid, kTcThreads, smem, st>>>(p);
+  k_synth_tc<TF32, LO><<<sm_count(), kTcThreads, smem, st>>>(p);
   return cudaGetLastError();
 }
 
 }  // namespace
 
-int synth_tc_split(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
-  return tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split).S;
-}
-
 bool synth_tc_supported(const RadarDev &r) {
   return r.N >= 16 && r.N <= 2048 && (r.N & (r.N - 1)) == 0 && r.M >= 1;
 }
 
-int64_t synth_tc_partial_floats(const RadarDev &r, bool tf32, int64_t kmax, int n_jobs, int split) {
-  const TcPlan pl = tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split);
-  return (int64_t)n_jobs * pl.S * r.n_rx * r.M * r.N * 2;
+int64_t synth_tc_scratch_floats(const RadarDev &r, bool tf32, int n_jobs) {
+  return tc_scratch(r, tf32, n_jobs < 1 ? 1 : n_jobs).total;
 }
 
 cudaError_t launch_synth_tc(const RadarDev &r, bool tf32, const uint32_t *count, int64_t kmax, int64_t ld,
                             const float *d, const float *a, const float *dd, const FrameJob *jobs, int n_jobs,
-                            const int *order, int split, float *partials, int64_t partial_cap_floats, float *out, uint32_t *err,
-                            float4 *cst, const float *d_base, cudaStream_t st) {
-  if (!cst) return cudaErrorInvalidValue;  // d_base may be null with no hits
+                            float *scratch, int64_t scratch_cap_floats, float *out, uint32_t *err, float4 *cst,
+                            const float *d_base, cudaStream_t st) {
+  if (!cst || !scratch || !out || !err) return cudaErrorInvalidValue;  // d_base may be null with no hits
   if (!synth_tc_supported(r) || n_jobs < 1) return cudaErrorInvalidValue;
+  if ((int64_t)n_jobs * r.n_rx >= (1 << 24)) return cudaErrorInvalidValue;  // pair ids fit the plan's 24 bits
   const int LO = tc_lo(r, tf32);
-  const TcPlan pl = tc_plan(r, tf32, kmax < 1 ? 1 : kmax, n_jobs, split);
-  const int64_t total = (int64_t)r.n_rx * r.M * r.N;
-  if ((int64_t)n_jobs * pl.S * total * 2 > partial_cap_floats) return cudaErrorInvalidValue;
+  const TcPlan pl = tc_plan(r, tf32);
+  if ((kmax / kHitsPerBlock + 1) * (int64_t)pl.n_tiles >= ((int64_t)1 << 31)) return cudaErrorInvalidValue;
+  const TcScratch L = tc_scratch(r, tf32, n_jobs);
+  if (L.total > scratch_cap_floats) return cudaErrorInvalidValue;
   SynthTcParams p;
   p.d = d; p.a = a; p.dd = dd; p.ld = ld;
   p.count = count; p.kmax = kmax;
   p.n_rx = r.n_rx; p.M = r.M; p.N = r.N;
-  p.HI = pl.HI; p.mc = pl.mc; p.n_tiles = pl.n_tiles; p.S = pl.S;
+  p.HI = pl.HI; p.mc = pl.mc; p.n_tiles = pl.n_tiles;
+  p.n_jobs = n_jobs;
+  p.n_pairs = n_jobs * r.n_rx;
+  p.LO = LO;
+  p.tf32 = tf32 ? 1 : 0;
+  p.mu_max = 0.5f * (float)((pl.mc < r.M ? pl.mc : r.M) - 1);
   p.f0_c = r.f0 / kC;
   p.kb = r.slope * r.dt / kC;
   p.c1k = (float)(r.f0 * r.t_rep / kC);
   p.b1k = (float)(r.slope * r.dt / kC * r.t_rep);
-  // with one split the CTAs' partial cubes are the output: no reduction pass
-  p.partials = pl.S == 1 ? out : partials;
+  p.out = out;
+  p.slots = scratch;
   p.jobs = jobs;
-  p.order = order;
   p.err = err;
   p.cst = cst;
   p.d_base = d_base;
+  uint32_t *words = reinterpret_cast<uint32_t *>(scratch);
+  p.ticket = words + L.ticket;
+  p.bmax = words + L.bmax;
+  p.pl_cost = reinterpret_cast<int64_t *>(words + L.cost);
+  p.pl_pair = reinterpret_cast<int32_t *>(words + L.pair);
+  p.pl_nb = reinterpret_cast<int32_t *>(words + L.nb);
+  p.cnt = words + L.cnt;
+  cudaError_t e = cudaMemsetAsync(p.ticket, 0, sizeof(uint32_t) * (1 + (size_t)p.n_pairs), st);
+  if (e != cudaSuccess) return e;
   {
-    int sms = 152, dev = 0;
-    if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    const int sms = sm_count();
     const int64_t per = (kmax + 255) / 256;
     int bx = (int)(per < 1 ? 1 : per);
     const int cap = (4 * sms + r.n_rx * n_jobs - 1) / (r.n_rx * n_jobs);
     if (bx > cap) bx = cap < 1 ? 1 : cap;
-    const float mu_max = 0.5f * (float)((pl.mc < r.M ? pl.mc : r.M) - 1);
-    k_tc_consts<<<dim3(bx, r.n_rx, n_jobs), 256, 0, st>>>(p, mu_max, 0.5f * (float)(LO - 1));
-    const cudaError_t ec = cudaGetLastError();
-    if (ec != cudaSuccess) return ec;
+    k_tc_consts<<<dim3(bx, r.n_rx, n_jobs), 256, 0, st>>>(p, 0.5f * (float)(LO - 1));
+    if ((e = cudaGetLastError()) != cudaSuccess) return e;
   }
-  cudaError_t e = tf32 ? launch_tc<true, 16>(p, n_jobs, st)
-                       : (LO == 32 ? launch_tc<false, 32>(p, n_jobs, st) : launch_tc<false, 16>(p, n_jobs, st));
-  if (e != cudaSuccess) return e;
-  const int threads = 256;
-  const int64_t blocks = (total * n_jobs + threads - 1) / threads;
-  if (pl.S == 1) return cudaSuccess;
-  k_tc_reduce<<<(unsigned)blocks, threads, 0, st>>>(reinterpret_cast<const float2 *>(partials), pl.S, total, n_jobs,
-                                                    reinterpret_cast<float2 *>(out));
-  return cudaGetLastError();
+  return tf32 ? launch_tc<true, 16>(p, st)
+              : (LO == 32 ? launch_tc<false, 32>(p, st) : launch_tc<false, 16>(p, st));
 }
 
 }  // namespace rr

@@ -263,8 +263,9 @@ def test_scene_upload_many_matches_single_uploads(ctx, on_device, asynchronous):
 def test_batch_plan_reports_the_enqueued_kernels(ctx):
     """rr_batch_plan after a batch: one cluster build launch, four for the
     trace and echo, the synthesis (FP32: kernel + split-K sum; tensor
-    cores: per-hit constants + kernel, + the sum only when split) and the
-    two FFT passes when a range-Doppler cube is asked for."""
+    cores: per-hit constants with the plan + the kernel on one CTA per SM,
+    reported as split 1) and the two FFT passes when a range-Doppler cube
+    is asked for."""
     radar, scenes, grids = _mixed_batch()
     for k, s in enumerate(scenes[:3]):
         ctx.scene_upload(850 + k, s.V, s.F, s.vel)
@@ -277,7 +278,8 @@ def test_batch_plan_reports_the_enqueued_kernels(ctx):
     assert 2 <= plan["ray_tile_log2"] <= 4 and plan["split"] >= 1 and 1 <= plan["cluster_ctas"] <= 8
     ctx.batch_run(jobs, radar, if_out=out, rd_out=rd, variant=1)
     plan = ctx.batch_plan()
-    assert plan["kernel_launches"] == 1 + 4 + (3 if plan["split"] > 1 else 2) + 2
+    assert plan["split"] == 1
+    assert plan["kernel_launches"] == 1 + 4 + 2 + 2
     ctx.sync()
 
 
