@@ -346,6 +346,7 @@ struct Seg {
   int b0, n;        // first block inside the item, blocks in the run
   int pi;           // the pair's position in the plan
   bool head, tail;  // the item also has blocks in the previous / next CTA
+  int64_t c0;       // cost start of the item's first block
 };
 
 // Walks the blocks whose cost start lies in [lo, hi): pair by pair in plan
@@ -398,6 +399,7 @@ struct SegWalk {
       s.pi = i;
       s.head = s.b0 > 0;
       s.tail = e < (t + 1) * nb;
+      s.c0 = Ci + (int64_t)t * nb * u;
       g = e;
       return true;
     }
@@ -405,34 +407,28 @@ struct SegWalk {
   }
 };
 
+// What the write-out of a run needs, fixed when the run starts.
+struct RunOut {
+  float *tile;     // output of the item's tile: chirp m0, sample 0 of its (frame, channel)
+  int item;        // (pair id) * n_tiles + tile: counter index
+  int cf, cl;      // CTAs that own the item's first and last blocks
+  int mvalid;      // chirps in the tile
+  int flags;       // 1: the item has blocks in the previous CTA, 2: in the next
+};
+
 // Warps 0-3 of k_synth_tc: write this thread's folded row (acc: 2 LO floats,
-// Re then Im) of a finished run (plan position pi, tile | head << 30 |
-// tail << 31).  An item inside one CTA goes straight to the output; an item
-// shared by several CTAs goes to this CTA's slot, and the last of its CTAs
-// to arrive (a counter per item and row quarter) sums the slots in CTA
-// order into the output.  Out of line: it runs a few times per CTA.
+// Re then Im) of a finished run.  An item inside one CTA goes straight to
+// the output; an item shared by several CTAs goes to this CTA's slot, and
+// the last of its CTAs to arrive (a counter per item and row quarter) sums
+// the slots in CTA order into the output.  Out of line: it runs a few times
+// per CTA.
 template <int LO>
-__device__ __noinline__ void flush_run(const SynthTcParams &p, int pi, int tf, const float *accr, int my_row, int my_mi,
-                                       int my_h, int64_t W, int P) {
+__device__ __noinline__ void flush_run(const SynthTcParams &p, const RunOut &r, const float *accr, int my_row,
+                                       int my_mi, int my_h) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  Seg s;
-  {
-    const int32_t pk = p.pl_pair[pi];
-    const int pid = pk & 0xFFFFFF;
-    s.q = pid / p.n_rx;
-    s.j = pid - s.q * p.n_rx;
-    s.T = pk >> 24;
-    s.nb = p.pl_nb[pi];
-    s.pi = pi;
-    s.tile = tf & 0x3FFFFFFF;
-    s.head = (tf >> 30) & 1;
-    s.tail = (tf >> 31) & 1;
-  }
-  const int m0 = s.tile * p.mc;
-  const bool live = my_mi < min(p.mc, p.M - m0) && my_h < p.HI;
-  float4 *o = reinterpret_cast<float4 *>(
-      p.out + 2 * ((((int64_t)s.q * p.n_rx + s.j) * p.M + (m0 + my_mi)) * (int64_t)p.N + (int64_t)my_h * LO));
-  if (!s.head && !s.tail) {
+  const bool live = my_mi < r.mvalid && my_h < p.HI;
+  float4 *o = reinterpret_cast<float4 *>(r.tile + 2 * ((int64_t)my_mi * p.N + (int64_t)my_h * LO));
+  if (r.flags == 0) {
     if (live) {
 #pragma unroll
       for (int q = 0; q < LO / 2; ++q)
@@ -441,35 +437,40 @@ __device__ __noinline__ void flush_run(const SynthTcParams &p, int pi, int tf, c
     return;
   }
   const int c = blockIdx.x;
-  float4 *sl = reinterpret_cast<float4 *>(p.slots) + (int64_t)(s.head ? 2 * c : 2 * c + 1) * (LO / 2) * 128;
+  float4 *sl = reinterpret_cast<float4 *>(p.slots) + (int64_t)((r.flags & 1) ? 2 * c : 2 * c + 1) * (LO / 2) * 128;
 #pragma unroll
   for (int q = 0; q < LO / 2; ++q)
     __stcg(&sl[q * 128 + my_row], make_float4(accr[2 * q], accr[LO + 2 * q], accr[2 * q + 1], accr[LO + 2 * q + 1]));
   __threadfence();
   __syncwarp();
-  const int64_t item = ((int64_t)s.q * p.n_rx + s.j) * p.n_tiles + s.tile;
   uint32_t old = 0;
-  if (lane == 0) old = atomicAdd(&p.cnt[item * 4 + (warp & 3)], 1u);
+  if (lane == 0) old = atomicAdd(&p.cnt[(int64_t)r.item * 4 + (warp & 3)], 1u);
   old = __shfl_sync(0xffffffffu, old, 0);
-  // contributors: the owners of the item's first and last blocks
-  const int u = block_cost(LO, s.T);
-  const int64_t c0 = p.pl_cost[s.pi] + (int64_t)s.tile * s.nb * u;
-  const int cf = cost_owner(c0, W, P), cl = cost_owner(c0 + (int64_t)(s.nb - 1) * u, W, P);
-  if (old != (uint32_t)(cl - cf)) return;
+  if (old != (uint32_t)(r.cl - r.cf)) return;
   __threadfence();
   if (!live) return;
-  const float4 *slots = reinterpret_cast<const float4 *>(p.slots);
-#pragma unroll 4
-  for (int q = 0; q < LO / 2; ++q) {
-    float4 v = make_float4(0.f, 0.f, 0.f, 0.f);
-    for (int cc = cf; cc <= cl; ++cc) {
-      const float4 x = __ldcg(&slots[(int64_t)(cc == cf ? 2 * cc + 1 : 2 * cc) * (LO / 2) * 128 + q * 128 + my_row]);
-      v.x += x.x;
-      v.y += x.y;
-      v.z += x.z;
-      v.w += x.w;
+  // the sum over the contributors' slots in CTA order, eight float4 at a time
+  const float4 *slots = reinterpret_cast<const float4 *>(p.slots) + my_row;
+#pragma unroll
+  for (int h = 0; h < LO / 2; h += 8) {
+    float4 v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) v[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+    for (int cc = r.cf; cc <= r.cl; ++cc) {
+      const float4 *sc = slots + (int64_t)(cc == r.cf ? 2 * cc + 1 : 2 * cc) * (LO / 2) * 128;
+      float4 x[8];
+#pragma unroll
+      for (int q = 0; q < 8; ++q) x[q] = __ldcg(&sc[(h + q) * 128]);
+#pragma unroll
+      for (int q = 0; q < 8; ++q) {
+        v[q].x += x[q].x;
+        v[q].y += x[q].y;
+        v[q].z += x[q].z;
+        v[q].w += x[q].w;
+      }
     }
-    o[q] = v;
+#pragma unroll
+    for (int q = 0; q < 8; ++q) o[h + q] = v[q];
   }
 }
 
@@ -583,13 +584,11 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
     k2 = -0.5f * sg * sg;
     k3 = sg * sg * sg * (1.f / 6.f);
   };
-  // warps 0-3: write this thread's folded row of a finished run
-  auto flush = [&](int pi, int tf) {
-    flush_run<LO>(p, pi, tf, accr, my_row, my_mi, my_h, s_W, s_P);
-  };
 
-  // the run the producers are on: plan position, tile | head << 30 | tail << 31
-  int cur_pi = 0, cur_tf = 0;
+  // the run the producers are on: its tile, and (warps 0-3, one copy per
+  // warp in shared memory, so that it holds no registers) its write-out
+  __shared__ RunOut s_run[4];
+  int tile = 0;
   if (warp < 16) {
     // ---- producers: lane = block-local hit; warp w writes the A rows
     // 8 w .. 8 w + 7 (unit w: chirp w / nseg, segment w % nseg) and the B
@@ -623,7 +622,7 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
     };
     // one flat loop over the CTA's blocks; a new run starts when bl reaches
     // the run's length (the runs' lengths add up to nb_cta)
-    int bl = 0, rn = 0, b0 = 0, tile = 0, K = 0, m0 = 0, mvalid = 0;
+    int bl = 0, rn = 0, b0 = 0, K = 0, m0 = 0, mvalid = 0;
     float mcen = 0.f;
     const float4 *cj = p.cst;
     const float *aj = p.a;
@@ -635,7 +634,7 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
         // end of the previous run (not the CTA's last): fold and write it out
         if (b > 0 && warp < 4) {
           if (!fold_chain(tile)) break;
-          flush(cur_pi, cur_tf);
+          flush_run<LO>(p, s_run[warp & 3], accr, my_row, my_mi, my_h);
           for (int q = 0; q < 2 * LO; ++q) accr[q] = 0.f;
         }
         if (!wk.next(p, s_hi, s)) break;  // (never: nb_cta counts the runs' blocks)
@@ -660,8 +659,19 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
         b0 = s.b0;
         rn = s.n;
         bl = 0;
-        cur_pi = s.pi;
-        cur_tf = s.tile | (s.head ? 1 << 30 : 0) | (s.tail ? (int)(1u << 31) : 0);
+        if (warp < 4) {
+          __syncwarp();  // the lanes are done with the previous run's copy
+          if (lane == 0) {
+            RunOut &r = s_run[warp];
+            r.tile = p.out + 2 * ((((int64_t)s.q * p.n_rx + s.j) * p.M + m0) * (int64_t)p.N);
+            r.item = (s.q * p.n_rx + s.j) * p.n_tiles + s.tile;
+            r.cf = cost_owner(s.c0, s_W, s_P);
+            r.cl = cost_owner(s.c0 + (int64_t)(s.nb - 1) * block_cost(LO, s.T), s_W, s_P);
+            r.mvalid = mvalid;
+            r.flags = (s.head ? 1 : 0) | (s.tail ? 2 : 0);
+          }
+          __syncwarp();
+        }
         // the constants of block b + 1 are loaded while block b is generated
         cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
         a_next = 0.f;
@@ -836,9 +846,9 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
     have = __all_sync(0xffffffffu, have);
     if (have) {
       float sg, k2, k3;
-      row_consts(cur_tf & 0x3FFFFFFF, sg, k2, k3);
+      row_consts(tile, sg, k2, k3);
       fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
-      flush(cur_pi, cur_tf);
+      flush_run<LO>(p, s_run[warp & 3], accr, my_row, my_mi, my_h);
     }
   }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
