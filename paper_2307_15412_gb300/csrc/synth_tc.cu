@@ -864,41 +864,65 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
 // expansion terms T (the remainder bound for a full tile's largest phase),
 // its blocks per tile, the pairs ordered by T (largest first, ties by pair
 // id), the cumulative cost of the pairs in that order, and zeroed item
-// counters.
+// counters.  Each pair's T and block count are read and computed once and
+// parked in the counter array (at least 4 words per pair), which is zeroed
+// last.
 __device__ void tc_build_plan(const SynthTcParams &p, float lc) {
-  __shared__ int s_wcnt[8];
+  __shared__ int s_tot[kTerms + 1];
+  __shared__ int s_wc[kTerms + 1][8];
   __shared__ long long s_wsum[8];
   const int tid = threadIdx.x, lane = tid & 31, w = tid >> 5;
   const int np = p.n_pairs;
   const float xs = 6.2831853f * p.mu_max * lc;  // phase x per unit |b1|
-  auto blocks_of = [&](int q) {
+  uint32_t *park = p.cnt;                        // nb << 3 | T per pair
+  if (tid <= kTerms) s_tot[tid] = 0;
+  __syncthreads();
+  for (int pid = tid; pid < np; pid += 256) {
+    const int T = expansion_terms(xs * __uint_as_float(__ldcg(&p.bmax[pid])), p.tf32 != 0);
+    const int q = pid / p.n_rx;
     int64_t K = p.count ? min((int64_t)*p.count, p.kmax) : p.kmax;
     if (p.jobs) K = min((int64_t)*p.jobs[q].count, p.jobs[q].cap);
-    const int64_t nb = (K + kHitsPerBlock - 1) / kHitsPerBlock;
-    return (int)(nb < 1 ? 1 : nb);
-  };
-  int base = 0;
-  for (int T = kTerms; T >= 1; --T) {
-    for (int c0 = 0; c0 < np; c0 += 256) {
-      const int pid = c0 + tid;
-      bool f = false;
-      if (pid < np) f = expansion_terms(xs * __uint_as_float(__ldcg(&p.bmax[pid])), p.tf32 != 0) == T;
-      const unsigned bal = __ballot_sync(0xffffffffu, f);
-      if (lane == 0) s_wcnt[w] = __popc(bal);
-      __syncthreads();
-      int off = 0, tot = 0;
-      for (int k = 0; k < 8; ++k) {
-        off += k < w ? s_wcnt[k] : 0;
-        tot += s_wcnt[k];
-      }
-      if (f) {
-        const int pos = base + off + __popc(bal & ((1u << lane) - 1u));
-        p.pl_pair[pos] = pid | (T << 24);
-        p.pl_nb[pos] = blocks_of(pid / p.n_rx);
-      }
-      base += tot;
-      __syncthreads();
+    int64_t nb = (K + kHitsPerBlock - 1) / kHitsPerBlock;
+    if (nb < 1) nb = 1;
+    park[pid] = (uint32_t)nb << 3 | (uint32_t)T;
+    atomicAdd(&s_tot[T], 1);
+  }
+  __syncthreads();
+  // bucket bases: T = kTerms first
+  int base[kTerms + 1];
+  {
+    int acc = 0;
+#pragma unroll
+    for (int T = kTerms; T >= 1; --T) {
+      base[T] = acc;
+      acc += s_tot[T];
     }
+  }
+  for (int c0 = 0; c0 < np; c0 += 256) {
+    const int pid = c0 + tid;
+    const uint32_t v = pid < np ? park[pid] : 0u;
+    const int T = (int)(v & 7u);
+    unsigned bal[kTerms + 1];
+#pragma unroll
+    for (int t = 1; t <= kTerms; ++t) {
+      bal[t] = __ballot_sync(0xffffffffu, pid < np && T == t);
+      if (lane == 0) s_wc[t][w] = __popc(bal[t]);
+    }
+    __syncthreads();
+    if (pid < np) {
+      int off = 0;
+      for (int k = 0; k < w; ++k) off += s_wc[T][k];
+      const int pos = base[T] + off + __popc(bal[T] & ((1u << lane) - 1u));
+      p.pl_pair[pos] = pid | (T << 24);
+      p.pl_nb[pos] = (int)(v >> 3);
+    }
+#pragma unroll
+    for (int t = 1; t <= kTerms; ++t) {
+      int tot = 0;
+      for (int k = 0; k < 8; ++k) tot += s_wc[t][k];
+      base[t] += tot;
+    }
+    __syncthreads();
   }
   long long run = 0;
   if (tid == 0) p.pl_cost[0] = 0;
