@@ -300,7 +300,7 @@ __device__ __forceinline__ void tmem_ld16x2(uint32_t ca, uint32_t cb, uint32_t *
 // the hi x lo product of term t sits NT = 2 LO nt columns further and is
 // added to it.
 template <int LO>
-__device__ __noinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
+__device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool second, float sg, float k2, float k3,
                                       float *acc) {
   const uint32_t tbase = tmem + ((uint32_t)(32 * (warp & 3)) << 16);
   const uint32_t NT = 2u * LO * (uint32_t)nt;
@@ -420,10 +420,9 @@ struct RunOut {
 // Re then Im) of a finished run.  An item inside one CTA goes straight to
 // the output; an item shared by several CTAs goes to this CTA's slot, and
 // the last of its CTAs to arrive (a counter per item and row quarter) sums
-// the slots in CTA order into the output.  Out of line: it runs a few times
-// per CTA.
+// the slots in CTA order into the output.
 template <int LO>
-__device__ __noinline__ void flush_run(const SynthTcParams &p, const RunOut &r, const float *accr, int my_row,
+__device__ __forceinline__ void flush_run(const SynthTcParams &p, const RunOut &r, const float *accr, int my_row,
                                        int my_mi, int my_h) {
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const bool live = my_mi < r.mvalid && my_h < p.HI;
@@ -495,7 +494,7 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
   constexpr int kTmemCols = LO == 16 ? 256 : 512;     // hi x hi (+ lo x hi) and hi x lo products
   constexpr int FS = fold_stride<LO>();
   extern __shared__ __align__(1024) unsigned char smem[];
-  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_done, s_fold, s_folded;
+  __shared__ __align__(8) uint64_t s_full[kStages], s_empty[kStages], s_fold, s_folded;
   __shared__ uint32_t s_tmem;
   __shared__ long long s_lo, s_hi, s_W;
   __shared__ int s_P, s_nblocks, s_nterms;
@@ -547,7 +546,6 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
       mbar_init(smem_u32(&s_full[q]), kProducers);
       mbar_init(smem_u32(&s_empty[q]), 1);
     }
-    mbar_init(smem_u32(&s_done), 1);
     mbar_init(smem_u32(&s_fold), 1);
     mbar_init(smem_u32(&s_folded), 128);
     s_abort = 0;
@@ -604,22 +602,6 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
     wk.init(p, s_lo);
     Seg s;
     int kf = 0;  // folds done
-    // folds the finished chain of this warp's rows (warps 0-3); false if the wait ran out
-    auto fold_chain = [&](int tile) {
-      if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_fold), kf & 1))) {
-        atomicOr(p.err, ERR_TIMEOUT);
-        s_abort = 1;
-        return false;
-      }
-      ++kf;
-      asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-      float sg, k2, k3;
-      row_consts(tile, sg, k2, k3);
-      fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
-      asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
-      asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
-      return true;
-    };
     // one flat loop over the CTA's blocks; a new run starts when bl reaches
     // the run's length (the runs' lengths add up to nb_cta)
     int bl = 0, rn = 0, b0 = 0, K = 0, m0 = 0, mvalid = 0;
@@ -628,15 +610,33 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
     const float *aj = p.a;
     float4 cv_next = make_float4(0.f, 0.f, 0.f, 0.f);
     float a_next = 0.f;
-    for (int b = 0; b < nb_cta; ++b, ++bl) {
+    for (int b = 0;; ++b, ++bl) {
       if (s_abort) break;
-      if (bl == rn) {
-        // end of the previous run (not the CTA's last): fold and write it out
-        if (b > 0 && warp < 4) {
-          if (!fold_chain(tile)) break;
+      const bool run_end = bl == rn;  // also after the CTA's last block (b == nb_cta)
+      // warps 0-3: the chain that ended with the previous block is complete
+      // (at a run's end, every kMaxChain blocks inside a run, and after the
+      // CTA's last block): fold it, and at a run's end write the run out.
+      // One place for all folds keeps one inlined copy of the code.
+      if (warp < 4 && b > 0 && (run_end || bl % kMaxChain == 0)) {
+        if (!__all_sync(0xffffffffu, mbar_wait(smem_u32(&s_fold), kf & 1))) {
+          atomicOr(p.err, ERR_TIMEOUT);
+          s_abort = 1;
+          break;
+        }
+        ++kf;
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        float sg, k2, k3;
+        row_consts(tile, sg, k2, k3);
+        fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
+        asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+        asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&s_folded)) : "memory");
+        if (run_end) {
           flush_run<LO>(p, s_run[warp & 3], accr, my_row, my_mi, my_h);
           for (int q = 0; q < 2 * LO; ++q) accr[q] = 0.f;
         }
+      }
+      if (b == nb_cta) break;
+      if (run_end) {
         if (!wk.next(p, s_hi, s)) break;  // (never: nb_cta counts the runs' blocks)
         const float *dbase = p.d, *abase = p.a;
         int64_t ld = p.ld;
@@ -680,8 +680,6 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
           cv_next = cj[k];
           a_next = aj[k];
         }
-      } else if (warp < 4 && bl % kMaxChain == 0 && !fold_chain(tile)) {
-        break;  // the chain of the last kMaxChain blocks of this run is complete: folded
       }
       const int stg = b % nst;
       unsigned char *A = smem + stg * stage_bytes;
@@ -823,34 +821,13 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
             }
           }
           mma_commit(smem_u32(&s_empty[stg]));
-          const bool chain_end = bl + 1 == rn || (bl + 1) % kMaxChain == 0;
-          if (chain_end && b + 1 < nb_cta) mma_commit(smem_u32(&s_fold));
+          if (bl + 1 == rn || (bl + 1) % kMaxChain == 0) mma_commit(smem_u32(&s_fold));  // end of a chain
         }
       }
-      // after the last block's MMAs (they complete in issue order)
-      mma_commit(smem_u32(&s_done));
     }
     __syncwarp();
   }
 
-  // ---- epilogue: warps 0-3 fold the last chain into their rows and write
-  // the last run (row 32 w + lane = (chirp, h): LO complex samples n = LO h + l)
-  if (warp < 4) {
-    bool have = true;
-    if (!mbar_wait(smem_u32(&s_done), 0)) {
-      atomicOr(p.err, ERR_TIMEOUT);
-      have = false;
-    }
-    if (s_abort) have = false;
-    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    have = __all_sync(0xffffffffu, have);
-    if (have) {
-      float sg, k2, k3;
-      row_consts(tile, sg, k2, k3);
-      fold_row<LO>(tmem, warp, nterms, !TF32, sg, k2, k3, accr);
-      flush_run<LO>(p, s_run[warp & 3], accr, my_row, my_mi, my_h);
-    }
-  }
   asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
   __syncthreads();
   if (warp == 16) {
