@@ -143,6 +143,26 @@ rr_status rr_scene_upload_many(rr_ctx *ctx, const rr_mesh *meshes, int n_meshes,
  * with bottom-up bounding boxes.  Must follow every rr_scene_upload. */
 rr_status rr_build_bvh(rr_ctx *ctx, int scene);
 
+/* Replaces the vertex positions of an uploaded scene (same count, same
+ * faces: a new pose of an animated mesh) and its velocity (NULL: static).
+ * verts: float32 [nv][3], host or device as ptr_is_device says; nv must
+ * equal the uploaded count (RR_EINVAL otherwise).  The scene then needs
+ * rr_build_bvh or rr_refit_bvh before it is traced.  Host arrays may be
+ * reused when the call returns. */
+rr_status rr_scene_update_vertices(rr_ctx *ctx, int scene, const float *verts, int64_t nv, const float *vel,
+                                   int ptr_is_device);
+
+/* Refits the scene's LBVH to its current vertices: the tree of the last
+ * build (its topology, sorted Morton codes and triangle order) is kept and
+ * every bounding box is recomputed bottom up from the moved triangles, in
+ * one launch instead of the build's sort.  The paper traces each frame
+ * of a motion sequence against its own mesh; for small pose changes the
+ * old order stays a good tree, and the nearest hits are exact either way
+ * (only the traversal's cost depends on the tree).  Needs a build of the
+ * scene's current faces since its last rr_scene_upload (RR_ENOTREADY
+ * otherwise); unchanged vertices give the built boxes bit for bit. */
+rr_status rr_refit_bvh(rr_ctx *ctx, int scene);
+
 /* ---- tracing and echo (Sec. III-A, Eq. 1-3; Sec. III-B path lengths) ---- */
 
 /* Traces every ray of `grid` from radar->tx into the scene (nearest hit,
@@ -224,6 +244,7 @@ typedef struct {
 
 #define RR_BATCH_GRAPH 1     /* run the batch as a CUDA graph (captured on first use, replayed after) */
 #define RR_BATCH_AUTOTUNE 2  /* pick ray-tile shape and split-K factor by timing them on first use */
+#define RR_BATCH_REFIT 4     /* refit (rr_refit_bvh) the trees of frames that have one for their current faces */
 
 /* Runs the whole hot path -- build_bvh, trace_frame (ray generation,
  * traversal, echo of Sec. III-A, path lengths of Sec. III-B), synth_if
@@ -249,7 +270,10 @@ typedef struct {
  * with identical jobs, radar, outputs and scene buffers (any change
  * re-captures); RR_BATCH_AUTOTUNE times the candidate ray-tile shapes (and,
  * for RR_SYNTH_FP32, split-K factors) once per batch shape and keeps the
- * fastest (results are the same up to FP32 summation order).  The hit lists of a batch live in
+ * fastest (results are the same up to FP32 summation order);
+ * RR_BATCH_REFIT refits instead of rebuilding the trees of frames whose
+ * scene was built for its current faces (rr_scene_update_vertices between
+ * runs), in two launches for all of them.  The hit lists of a batch live in
  * the context (one segment of n_az * n_el hits per frame), not in the
  * scenes: rr_get_hits does not see them.  Errors as for the single-frame
  * calls; device-side errors surface at rr_sync. */

@@ -117,3 +117,30 @@ def _node_of(l: int, r: int, keys) -> int:
         if _clz64(keys[l] ^ keys[i]) > dlr:
             g = i
     return g
+
+
+def subtree_boxes(V: np.ndarray, F: np.ndarray, order: np.ndarray, left, right, rng_l, rng_r) -> np.ndarray:
+    """Child boxes of every internal node of the radix tree, in the node
+    layout of the CUDA builder: 12 float32 per node = left (lo.x, hi.x, lo.y,
+    hi.y), right (lo.x, hi.x, lo.y, hi.y), left (lo.z, hi.z), right (lo.z,
+    hi.z).  A child's box is the componentwise min / max over the vertices of
+    the triangles in its range of sorted positions (a leaf: its triangle) --
+    the definition of a bounding-volume hierarchy's boxes, whatever order
+    they are computed in, and exact in float32.  The tree (left, right,
+    rng_l, rng_r from ``radix_tree``) may have been built for other vertex
+    positions: this is the box set a refit of that tree must produce."""
+    tri = np.asarray(V, np.float32)[np.asarray(F)[np.asarray(order)]]  # [n, 3 vertices, 3]
+    tlo, thi = tri.min(axis=1), tri.max(axis=1)
+    m = len(left)
+    out = np.empty((m, 12), np.float32)
+
+    def box(kid):
+        if kid < 0:
+            return tlo[~kid], thi[~kid]
+        a, b = int(rng_l[kid]), int(rng_r[kid])
+        return tlo[a:b + 1].min(axis=0), thi[a:b + 1].max(axis=0)
+
+    for g in range(m):
+        (llo, lhi), (rlo, rhi) = box(int(left[g])), box(int(right[g]))
+        out[g] = [llo[0], lhi[0], llo[1], lhi[1], rlo[0], rhi[0], rlo[1], rhi[1], llo[2], lhi[2], rlo[2], rhi[2]]
+    return out

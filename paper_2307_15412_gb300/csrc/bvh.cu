@@ -224,12 +224,13 @@ __device__ __forceinline__ uint64_t key_delta(const uint32_t *keys, int x) {
   return ((uint64_t)(keys[x] ^ keys[x + 1]) << 32) | (uint32_t)(x ^ (x + 1));
 }
 
-__global__ void __launch_bounds__(kPrepThreads)
-k_hierarchy(int n, const uint32_t *__restrict__ keys, const int32_t *__restrict__ ids,
-            const float *__restrict__ V, const int32_t *__restrict__ F, BvhNode *nodes,
-            float4 *__restrict__ tris, int32_t *flags, BvhHeader *hdr) {
-  const int i = blockIdx.x * kPrepThreads + threadIdx.x;
-  if (i >= n) return;
+// Leaf i of the bottom-up climb (Apetrei 2014 order over the sorted keys):
+// writes the leaf's triangle in Morton order and its box into the parent,
+// and the second of two siblings to arrive goes on with their union; the
+// root's thread writes the header.  The flags must be -1 on entry.
+__device__ __forceinline__ void climb_leaf(int i, int n, const uint32_t *__restrict__ keys, const int32_t *__restrict__ ids,
+                                           const float *__restrict__ V, const int32_t *__restrict__ F, BvhNode *nodes,
+                                           float4 *__restrict__ tris, int32_t *flags, BvhHeader *hdr) {
   const int tid = ids[i];
   const int a = F[3 * tid], b = F[3 * tid + 1], c = F[3 * tid + 2];
   const float3 v0 = make_float3(V[3 * a], V[3 * a + 1], V[3 * a + 2]);
@@ -290,6 +291,38 @@ k_hierarchy(int n, const uint32_t *__restrict__ keys, const int32_t *__restrict_
   }
 }
 
+
+__global__ void __launch_bounds__(kPrepThreads)
+k_hierarchy(int n, const uint32_t *__restrict__ keys, const int32_t *__restrict__ ids,
+            const float *__restrict__ V, const int32_t *__restrict__ F, BvhNode *nodes,
+            float4 *__restrict__ tris, int32_t *flags, BvhHeader *hdr) {
+  const int i = blockIdx.x * kPrepThreads + threadIdx.x;
+  if (i >= n) return;
+  climb_leaf(i, n, keys, ids, V, F, nodes, tris, flags, hdr);
+}
+
+// The refit job of block b (jobs[j].blk0 <= b < jobs[j + 1].blk0).
+__device__ __forceinline__ int refit_job_of(const BuildJob *jobs, int n_jobs, int b) {
+  int lo = 0, hi = n_jobs - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (jobs[mid].blk0 <= b) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+
+__global__ void __launch_bounds__(kRefitThreads) k_refit_reset(const BuildJob *__restrict__ jobs, int n_jobs) {
+  const BuildJob &J = jobs[refit_job_of(jobs, n_jobs, blockIdx.x)];
+  const int i = ((int)blockIdx.x - J.blk0) * kRefitThreads + threadIdx.x;
+  if (i < J.n) J.flags[i] = -1;
+}
+
+__global__ void __launch_bounds__(kRefitThreads) k_refit(const BuildJob *__restrict__ jobs, int n_jobs) {
+  const BuildJob &J = jobs[refit_job_of(jobs, n_jobs, blockIdx.x)];
+  const int i = ((int)blockIdx.x - J.blk0) * kRefitThreads + threadIdx.x;
+  if (i < J.n) climb_leaf(i, J.n, J.keys, J.ids, J.V, J.F, J.nodes, J.tris, J.flags, J.hdr);
+}
+
 __global__ void k_empty_header(BvhHeader *hdr) {
   hdr->n = 0;
   hdr->root = 0;
@@ -297,6 +330,26 @@ __global__ void k_empty_header(BvhHeader *hdr) {
 }
 
 }  // namespace
+
+cudaError_t launch_refit_bvh(SceneDev &s, cudaStream_t st) {
+  const int n = (int)s.nt;
+  if (n == 0) {
+    k_empty_header<<<1, 1, 0, st>>>(s.hdr);
+    return cudaGetLastError();
+  }
+  cudaError_t e = cudaMemsetAsync(s.flags, 0xff, sizeof(int32_t) * (size_t)n, st);
+  if (e != cudaSuccess) return e;
+  k_hierarchy<<<(n + kPrepThreads - 1) / kPrepThreads, kPrepThreads, 0, st>>>(n, s.keys, s.ids, s.V, s.F, s.nodes,
+                                                                              s.tris, s.flags, s.hdr);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_refit_batch(const BuildJob *jobs, int n_jobs, int blocks, cudaStream_t st) {
+  if (n_jobs < 1 || blocks < 1) return cudaSuccess;
+  k_refit_reset<<<blocks, kRefitThreads, 0, st>>>(jobs, n_jobs);
+  k_refit<<<blocks, kRefitThreads, 0, st>>>(jobs, n_jobs);
+  return cudaGetLastError();
+}
 
 cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st) {
   const int n = (int)s.nt;

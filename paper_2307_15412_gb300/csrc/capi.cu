@@ -388,6 +388,7 @@ static rr_status upload_mesh(rr_ctx *c, int scene, const float *verts, int64_t n
   s->nt = nt;
   for (int i = 0; i < 3; ++i) s->vel[i] = vel ? vel[i] : 0.f;
   s->built = false;
+  s->tree = false;
   s->traced = false;
   return RR_OK;
 }
@@ -419,6 +420,40 @@ rr_status rr_build_bvh(rr_ctx *c, int scene) {
   if (st != RR_OK) return st;
   DeviceGuard g(c->device);
   RR_CUDA(c, rr::launch_build_bvh(*s, c->stream), "build_bvh launch");
+  s->built = true;
+  s->tree = true;
+  s->traced = false;
+  return RR_OK;
+}
+
+rr_status rr_scene_update_vertices(rr_ctx *c, int scene, const float *verts, int64_t nv, const float *vel,
+                                   int ptr_is_device) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (nv != s->nv) return fail(c, RR_EINVAL, "scene %d: %lld vertices, %lld uploaded", scene, (long long)nv, (long long)s->nv);
+  if (nv > 0 && !verts) return fail(c, RR_EINVAL, "null vertex array");
+  DeviceGuard g(c->device);
+  if (nv > 0)
+    RR_CUDA(c, cudaMemcpyAsync(s->V, verts, sizeof(float) * 3 * (size_t)nv,
+                               ptr_is_device ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, c->stream),
+            "update vertices");
+  for (int i = 0; i < 3; ++i) s->vel[i] = vel ? vel[i] : 0.f;
+  s->built = false;
+  s->traced = false;
+  if (!ptr_is_device) RR_CUDA(c, cudaStreamSynchronize(c->stream), "update vertices");  // caller may reuse host arrays
+  return RR_OK;
+}
+
+rr_status rr_refit_bvh(rr_ctx *c, int scene) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->tree) return fail(c, RR_ENOTREADY, "scene %d: refit needs a build of its current faces", scene);
+  DeviceGuard g(c->device);
+  RR_CUDA(c, rr::launch_refit_bvh(*s, c->stream), "refit_bvh launch");
   s->built = true;
   s->traced = false;
   return RR_OK;
@@ -673,6 +708,7 @@ struct BatchPlan {
   int gcap[5] = {0, 0, 0, 0, 0};
   int n_cluster() const { return gn[0] + gn[1] + gn[2] + gn[3] + gn[4]; }
   std::vector<SceneDev *> others;   // frames built by the per-scene path (fewer than 2 or very many triangles)
+  int n_refit = 0, refit_blocks = 0; // frames refit instead of built (RR_BATCH_REFIT), after the cluster jobs
   int64_t kmax = 0;                 // largest hit segment
   rr::RadarDev rd;
   int tw = 3, split = 0;
@@ -705,8 +741,9 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
   cudaError_t e;
   if (ev && (e = cudaEventRecord(ev[0], st)) != cudaSuccess) return e;
   if ((e = cudaMemcpyAsync(b.ftab, b.h_ftab, sizeof(rr::FrameJob) * P.n_jobs, cudaMemcpyHostToDevice, st)) != cudaSuccess) return e;
-  if (P.n_cluster() > 0 &&
-      (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * P.n_cluster(), cudaMemcpyHostToDevice, st)) != cudaSuccess)
+  if (P.n_cluster() + P.n_refit > 0 &&
+      (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n_cluster() + P.n_refit), cudaMemcpyHostToDevice,
+                           st)) != cudaSuccess)
     return e;
   if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) return e;
   for (int g = 0, off = 0; g < 5; off += P.gn[g], ++g)
@@ -714,6 +751,8 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
       return e;
   for (SceneDev *s : P.others)
     if ((e = rr::launch_build_bvh(*s, st)) != cudaSuccess) return e;
+  if (P.n_refit && (e = rr::launch_refit_batch(b.btab + P.n_cluster(), P.n_refit, P.refit_blocks, st)) != cudaSuccess)
+    return e;
   if (ev && (e = cudaEventRecord(ev[1], st)) != cudaSuccess) return e;
   if ((e = rr::launch_trace_batch(b.ftab, P.n_jobs, b.jt, b.prefix, batch_order(c, P.n_jobs), P.rd, c->d_err, st, P.tw)) != cudaSuccess) return e;
   if (ev && (e = cudaEventRecord(ev[2], st)) != cudaSuccess) return e;
@@ -791,7 +830,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
   if (!if_out && !rd_out) return fail(c, RR_EINVAL, "need if_out or rd_out");
   if (window != 0 && window != 1) return fail(c, RR_EINVAL, "window must be 0 or 1");
-  if (flags & ~(RR_BATCH_GRAPH | RR_BATCH_AUTOTUNE)) return fail(c, RR_EINVAL, "unknown batch flags 0x%x", flags);
+  if (flags & ~(RR_BATCH_GRAPH | RR_BATCH_AUTOTUNE | RR_BATCH_REFIT)) return fail(c, RR_EINVAL, "unknown batch flags 0x%x", flags);
   if (rd_out && (int64_t)radar->n_chirps * radar->n_samples > 16384)
     return fail(c, RR_EINVAL, "range_doppler needs n_chirps * n_samples <= 16384");
   DeviceGuard g(c->device);
@@ -808,7 +847,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   const int kpc = rr::cluster_keys_per_cta();
   int cmin = 1;       // CTAs the largest mesh of up to 8 x kpc triangles needs
   int n_small = 0;    // cluster-built meshes of up to 8 x kpc triangles
-  std::vector<char> cl_job(n_jobs, 0);
+  std::vector<char> cl_job(n_jobs, 0), rf_job(n_jobs, 0);
   for (int j = 0; j < n_jobs; ++j) {
     if ((st = get_scene(c, jobs[j].scene, &sc[j])) != RR_OK) return st;
     if (seen[jobs[j].scene]) return fail(c, RR_EINVAL, "scene %d appears twice in the batch", jobs[j].scene);
@@ -822,6 +861,11 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     dseg[j + 1] = dseg[j] + (int64_t)gr.n_az + gr.n_el;
     P.kmax = std::max<int64_t>(P.kmax, (int64_t)gr.n_az * gr.n_el);
     const int n = (int)sc[j]->nt;
+    if ((flags & RR_BATCH_REFIT) && sc[j]->tree && n >= 1) {
+      rf_job[j] = 1;
+      ++P.n_refit;
+      continue;
+    }
     const bool cl = clusters && n >= 2 && n <= rr::cluster_build_capacity();
     if (cl) {
       cl_job[j] = 1;
@@ -932,7 +976,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
 
   // device tables, staged in pinned memory (wait until the last copy out of it is done)
   RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
-  int gfill[5];
+  int gfill[5], rfill = 0;
   for (int g = 0, off = 0; g < 5; off += P.gn[g], ++g) gfill[g] = off;
   for (int j = 0; j < n_jobs; ++j) {
     SceneDev *s = sc[j];
@@ -949,7 +993,14 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     f.dir = b.dir + dseg[j];
     b.h_ftab[j] = f;
     const int n = (int)s->nt;
-    if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
+    if (rf_job[j]) {
+      // refit entries follow the cluster jobs in the table
+      rr::BuildJob bj = rr::build_job_for(*s, 1);
+      bj.flags = s->flags;
+      bj.blk0 = P.refit_blocks;
+      P.refit_blocks += (n + rr::kRefitThreads - 1) / rr::kRefitThreads;
+      b.h_btab[P.n_cluster() + rfill++] = bj;
+    } else if (clusters && n >= 2 && n <= rr::cluster_build_capacity()) {
       const int g = group_of(n);
       const rr::BuildJob bj = rr::build_job_for(*s, P.gC[g]);
       b.h_btab[gfill[g]++] = bj;
@@ -972,6 +1023,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     int launches = 4;
     for (int g = 0; g < 5; ++g) launches += P.gn[g] > 0 ? 1 : 0;
     for (SceneDev *s : P.others) launches += s->nt == 0 ? 1 : 3;
+    if (P.n_refit) launches += 2;  // flag reset and climb over all refit frames
     int split;
     if (variant == RR_SYNTH_FP32) {
       split = rr::synth_fp32_batch_split(P.rd, P.kmax, n_jobs, P.split);
@@ -1001,7 +1053,8 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   key = fnv(key, &P.tw, sizeof(P.tw));
   key = fnv(key, &P.split, sizeof(P.split));
   key = fnv(key, b.h_ftab, sizeof(rr::FrameJob) * n_jobs);
-  key = fnv(key, b.h_btab, sizeof(rr::BuildJob) * P.n_cluster());
+  key = fnv(key, &P.n_refit, sizeof(P.n_refit));
+  key = fnv(key, b.h_btab, sizeof(rr::BuildJob) * (P.n_cluster() + P.n_refit));
   for (SceneDev *s : P.others) {
     key = fnv(key, &s, sizeof(s));
     key = fnv(key, &s->nt, sizeof(s->nt));
@@ -1046,6 +1099,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   RR_CUDA(c, cudaEventRecord(b.staged, c->stream), "batch event");
   for (SceneDev *s : sc) {
     s->built = true;
+    s->tree = true;
     s->traced = false;  // the frames' hits are in the batch lists, not in the scenes
   }
   return RR_OK;

@@ -43,6 +43,9 @@ struct BuildJob {
   struct BvhHeader *hdr;
   int32_t n;    // triangles (2 <= n <= cluster_build_capacity())
   int32_t cap;  // keys per CTA: ceil(n / cluster size)
+  // refit only (launch_refit_batch): bottom-up visit flags [n], first block
+  int32_t *flags;
+  int32_t blk0;
 };
 
 struct BvhHeader {
@@ -71,6 +74,7 @@ struct SceneDev {
   BvhHeader *hdr = nullptr;
   int64_t cap_nt = 0, cap_nv = 0;
   bool built = false;
+  bool tree = false;              // a build of the current faces exists (a refit may replace the next build)
   // hit list
   int64_t hit_cap = 0;           // capacity of the arrays below
   int32_t hit_nrx = 0;           // n_rx of the last trace
@@ -135,6 +139,16 @@ struct JobTiles {
 
 // ---- launchers (each returns the launch status) ----
 cudaError_t launch_build_bvh(SceneDev &s, cudaStream_t st);
+// Refit of a built LBVH after its vertices moved (same faces): the tree's
+// topology, sorted codes and ids stay, the Morton-ordered triangles and every
+// box are recomputed from the new vertices by the bottom-up climb of the
+// build (so that unchanged vertices give the built boxes bit for bit).
+cudaError_t launch_refit_bvh(SceneDev &s, cudaStream_t st);
+// Refits of n_jobs scenes in two launches (flag reset, climb); jobs: device
+// table whose entries carry n, flags and blk0 (the prefix of ceil(n / 256)
+// over the table), blocks: the total.
+constexpr int kRefitThreads = 256;
+cudaError_t launch_refit_batch(const BuildJob *jobs, int n_jobs, int blocks, cudaStream_t st);
 // Single-launch cluster builder for 2 <= n <= cluster_build_capacity();
 // sets *used = false (and launches nothing) when it does not apply.
 cudaError_t launch_build_bvh_cluster(SceneDev &s, cudaStream_t st, bool *used);

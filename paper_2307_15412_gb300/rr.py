@@ -70,6 +70,7 @@ class rr_train_cfg(ctypes.Structure):
 
 RR_BATCH_GRAPH = 1
 RR_BATCH_AUTOTUNE = 2
+RR_BATCH_REFIT = 4
 
 SIGNATURES = {
     "rr_create": (_I, [ctypes.POINTER(_P), _I, _P]),
@@ -82,6 +83,8 @@ SIGNATURES = {
     "rr_scene_upload_many": (_I, [_P, _P, _I, _I, _I]),
     "rr_batch_plan": (_I, [_P, _P, _P, _P, _P]),
     "rr_build_bvh": (_I, [_P, _I]),
+    "rr_scene_update_vertices": (_I, [_P, _I, _P, ctypes.c_int64, _P, _I]),
+    "rr_refit_bvh": (_I, [_P, _I]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
     "rr_get_hits": (_I, [_P, _I, _I64, _P, _P, _P, _P, _P, _P]),
@@ -270,6 +273,26 @@ class Context:
     def build_bvh(self, scene: int):
         self._check(self.lib.rr_build_bvh(self.h, scene))
 
+    def scene_update_vertices(self, scene: int, V, vel=None):
+        """New positions for an uploaded scene's vertices (same count and
+        faces): V float32 [nv,3], numpy (host) or a torch CUDA tensor."""
+        on_dev = hasattr(V, "is_cuda") and V.is_cuda
+        if on_dev:
+            import torch
+            assert V.dtype == torch.float32
+            V = V.contiguous()
+        else:
+            V = np.ascontiguousarray(V, np.float32)
+        velp = None
+        if vel is not None:
+            self._vel = np.ascontiguousarray(vel, np.float32).reshape(3)
+            velp = self._vel.ctypes.data
+        self._check(self.lib.rr_scene_update_vertices(self.h, scene, _ptr(V), int(V.shape[0]), velp,
+                                                      1 if on_dev else 0))
+
+    def refit_bvh(self, scene: int):
+        self._check(self.lib.rr_refit_bvh(self.h, scene))
+
     def trace_frame(self, scene: int, radar: Radar, grid: RayGrid, hit_capacity: int = 0, want_count=True):
         """Returns a one-element list filled with the hit count by the next sync()."""
         box = [None]
@@ -307,7 +330,7 @@ class Context:
                                           int(window), _ptr(if_out), _ptr(rd_out)))
 
     def batch_run(self, jobs, radar, if_out=None, rd_out=None, variant: int = SYNTH_FP32, window: int = 0,
-                  graph: bool = False, autotune: bool = False):
+                  graph: bool = False, autotune: bool = False, refit: bool = False):
         """Whole hot path for several frames at once.  jobs: list of
         (scene, RayGrid or rr_raygrid), or a prepared ctypes rr_job array;
         if_out / rd_out: torch CUDA float32 [n_jobs, n_rx, M, N, 2]."""
@@ -320,7 +343,7 @@ class Context:
                 arr[i].reserved = 0
                 arr[i].grid = make_grid(g)
         rs = make_radar(radar)
-        flags = (RR_BATCH_GRAPH if graph else 0) | (RR_BATCH_AUTOTUNE if autotune else 0)
+        flags = (RR_BATCH_GRAPH if graph else 0) | (RR_BATCH_AUTOTUNE if autotune else 0) | (RR_BATCH_REFIT if refit else 0)
         self._check(self.lib.rr_batch_run(self.h, arr, len(arr), ctypes.byref(rs), int(variant), int(window),
                                           _ptr(if_out), _ptr(rd_out), flags))
 

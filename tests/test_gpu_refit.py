@@ -1,0 +1,186 @@
+"""GPU: refit of a built LBVH after its vertices moved (rr_refit_bvh and
+RR_BATCH_REFIT) against the oracle's definition of the boxes and the
+brute-force trace.
+
+Bars:
+  * codes, ids and topology of a refit tree are those of its build, and
+    every child box is the oracle's min / max over the child's triangles
+    (bit-exact: min and max are exact in float32);
+  * nearest hits after a refit equal the FP64 brute-force trace of the
+    moved mesh on >= 99.99 % of rays, distances within 1e-6 relative (the
+    bar of the trace parity tests);
+  * batch frames after a refit equal single-frame runs that rebuild the
+    tree: rel-L2 <= 1e-5 (same hits, FP32 summation order of the hit list).
+"""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import bvh as obvh
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import gpu_hits, per_ray, rel_l2, to_complex
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def _tree(ctx, scene, n):
+    codes = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    ids = torch.empty(n, dtype=torch.int32, device="cuda:0")
+    left = torch.empty(max(n - 1, 1), dtype=torch.int32, device="cuda:0")
+    right = torch.empty_like(left)
+    boxes = torch.empty((max(n - 1, 1), 12), dtype=torch.float32, device="cuda:0")
+    root = ctx.get_bvh(scene, codes, ids, left, right, boxes)
+    ctx.sync()
+    return dict(codes=codes.cpu().numpy(), ids=ids.cpu().numpy(), L=left.cpu().numpy()[:n - 1],
+                R=right.cpu().numpy()[:n - 1], boxes=boxes.cpu().numpy()[:n - 1], root=root[0])
+
+
+def _ranges(L, R, root):
+    """Sorted-position range [rl, rr] of every internal node (post-order)."""
+    m = len(L)
+    rl = np.empty(m, np.int64)
+    rr = np.empty(m, np.int64)
+    stack = [(root, False)]
+    while stack:
+        g, done = stack.pop()
+        if not done:
+            stack.append((g, True))
+            stack.extend([(int(k), False) for k in (L[g], R[g]) if k >= 0])
+            continue
+        a = ~L[g] if L[g] < 0 else rl[L[g]]
+        b = ~R[g] if R[g] < 0 else rr[R[g]]
+        rl[g], rr[g] = a, b
+    return rl, rr
+
+
+def _same_tree(t0, t1):
+    for k in ("codes", "ids", "L", "R"):
+        assert np.array_equal(t0[k], t1[k]), k
+    assert t0["root"] == t1["root"]
+
+
+def _boxes_are_the_definition(tree, V, F):
+    rl, rr = _ranges(tree["L"], tree["R"], tree["root"])
+    want = obvh.subtree_boxes(V, F, tree["ids"], tree["L"], tree["R"], rl, rr)
+    assert np.array_equal(tree["boxes"], want)
+
+
+@pytest.mark.parametrize("nt_target", [600, 20000, 50000, 80000])
+def test_refit_of_unchanged_vertices_gives_the_built_tree(ctx, nt_target):
+    """Both builders (one cluster up to ~60k triangles, the three-kernel path
+    above) leave a tree whose refit with the same vertices changes no bit,
+    and whose every child box (not only the leaves) is the oracle's."""
+    s = I.hand_scene(40, nt_target)
+    n = s.F.shape[0]
+    ctx.scene_upload(20, s.V, s.F, s.vel)
+    ctx.build_bvh(20)
+    built = _tree(ctx, 20, n)
+    _boxes_are_the_definition(built, s.V, s.F)
+    ctx.refit_bvh(20)
+    refit = _tree(ctx, 20, n)
+    _same_tree(built, refit)
+    assert np.array_equal(built["boxes"], refit["boxes"])
+
+
+@pytest.mark.parametrize("nt_target", [2000, 20000])
+def test_refit_to_a_new_pose(ctx, nt_target):
+    """A hand built in one pose, moved to another (same faces) and refit:
+    the tree keeps its order and topology, its boxes are the oracle's for the
+    new vertices, and tracing it finds the brute-force nearest hits."""
+    a = I.hand_scene(41, nt_target)
+    b = I.hand_scene(42, nt_target)
+    assert np.array_equal(a.F, b.F)
+    n = a.F.shape[0]
+    ctx.scene_upload(21, a.V, a.F, a.vel)
+    ctx.build_bvh(21)
+    built = _tree(ctx, 21, n)
+    ctx.scene_update_vertices(21, b.V, b.vel)
+    ctx.refit_bvh(21)
+    refit = _tree(ctx, 21, n)
+    _same_tree(built, refit)
+    _boxes_are_the_definition(refit, b.V, b.F)
+    radar, grid, _ = I.workload_tiny()
+    cnt = ctx.trace_frame(21, radar, grid)
+    ctx.sync()
+    h = gpu_hits(ctx, 21, radar.n_rx, cnt[0])
+    gtri, gt = per_ray(grid.n_rays, h)
+    ref = oracle.frame(b.V, b.F, b.vel, radar, grid)
+    rid = ref["ray_ids"]
+    otri, ot = ref["tri"].astype(np.int64), ref["t"]
+    same = gtri[rid] == otri
+    both = same & (otri >= 0)
+    close = np.ones_like(same)
+    close[both] = np.abs(gt[rid][both] - ot[both]) <= 1e-6 * ot[both]
+    assert (same & close).mean() >= 0.9999
+    assert both.sum() > 100
+
+
+def test_refit_preconditions(ctx):
+    """A refit needs a build of the scene's current faces; a vertex update
+    must keep the vertex count."""
+    from paper_2307_15412_gb300 import rr
+    s = I.hand_scene(43, 600)
+    ctx.scene_upload(22, s.V, s.F, s.vel)
+    with pytest.raises(rr.RRError) as e:
+        ctx.refit_bvh(22)
+    assert e.value.status == rr.RR_ENOTREADY
+    ctx.build_bvh(22)
+    with pytest.raises(rr.RRError) as e:
+        ctx.scene_update_vertices(22, s.V[:-1], s.vel)
+    assert e.value.status == rr.RR_EINVAL
+    ctx.scene_update_vertices(22, s.V, s.vel)
+    ctx.refit_bvh(22)
+    ctx.sync()
+
+
+def test_batch_refit_matches_rebuilt_single_frames(ctx):
+    """A batch run once (builds), then its meshes moved to new poses and the
+    batch run with RR_BATCH_REFIT: two refit launches replace the builds, and
+    every frame equals a single-frame run that rebuilds its tree."""
+    radar = I.Radar(n_samples=128, n_chirps=32, rx=I.rx_l_array())
+    grid = I.RayGrid(96, 96, np.radians(40.0), np.radians(40.0))
+    sizes = [600, 2000, 12000, 20000, 50000]
+    poses_a = [I.hand_scene(50 + k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+               for k, nt in enumerate(sizes)]
+    poses_b = [I.hand_scene(60 + k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+               for k, nt in enumerate(sizes)]
+    for k, s in enumerate(poses_a):
+        ctx.scene_upload(300 + k, s.V, s.F, s.vel)
+    jobs = [(300 + k, grid) for k in range(len(sizes))]
+    out = torch.zeros((len(sizes), radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32,
+                      device="cuda:0")
+    ctx.batch_run(jobs, radar, if_out=out, refit=True)  # no tree yet: builds
+    ctx.sync()
+    built_plan = ctx.batch_plan()
+    for k, s in enumerate(poses_b):
+        assert np.array_equal(s.F, poses_a[k].F)
+        ctx.scene_update_vertices(300 + k, s.V, s.vel)
+    ctx.batch_run(jobs, radar, if_out=out, refit=True)
+    ctx.sync()
+    plan = ctx.batch_plan()
+    assert plan["kernel_launches"] == 2 + 4 + 2  # refit (reset, climb), trace and echo, FP32 synthesis
+    assert built_plan["cluster_ctas"] > 0 and plan["cluster_ctas"] == 0  # nothing cluster-built the second time
+    got = to_complex(out)
+    for k, s in enumerate(poses_b):
+        ctx.scene_upload(310 + k, s.V, s.F, s.vel)
+        single = torch.zeros_like(out[0])
+        ctx.run_frame(310 + k, radar, grid, if_out=single)
+        ctx.sync()
+        ref = to_complex(single)
+        assert np.linalg.norm(ref) > 0
+        assert rel_l2(got[k], ref) <= 1e-5

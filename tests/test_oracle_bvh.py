@@ -100,3 +100,79 @@ def test_hand_codes_and_tree():
     sc = codes[order]
     assert (np.diff(sc.astype(np.int64)) >= 0).all()
     _check_tree(sc, *bvh.radix_tree(sc))
+
+
+def test_subtree_boxes_hand_worked_example():
+    """Three triangles, two of them close together: the radix tree pairs the
+    two near ones under internal node 0 and the root (node 1) takes that pair
+    and the far triangle.  Every box below is worked out by hand from the
+    vertex coordinates (the min / max of the triangles under each child)."""
+    V = np.array([[0.0, 0.0, 0.0], [0.2, 0.1, 0.0], [0.1, 0.3, 0.2],      # T0
+                  [0.3, 0.0, 0.1], [0.4, 0.2, 0.0], [0.2, 0.1, 0.3],      # T1
+                  [10.0, 1.0, 2.0], [10.5, 1.5, 2.0], [10.2, 1.2, 2.5]],  # T2
+                 np.float32)
+    F = np.array([[0, 1, 2], [3, 4, 5], [6, 7, 8]], np.int32)
+    codes = bvh.morton_codes(V, F)
+    order = bvh.sorted_order(codes)
+    assert list(order) == [1, 0, 2]  # T1's centre quantises below T0's
+    L, R, rl, rr, root = bvh.radix_tree(codes[order])
+    assert root == 1 and list(L) == [~0, 0] and list(R) == [~1, ~2]
+    f = np.float32
+    T0 = ([0.0, 0.0, 0.0], [0.2, 0.3, 0.2])
+    T1 = ([0.2, 0.0, 0.0], [0.4, 0.2, 0.3])
+    T2 = ([10.0, 1.0, 2.0], [10.5, 1.5, 2.5])
+    T01 = ([0.0, 0.0, 0.0], [0.4, 0.3, 0.3])
+
+    def row(lb, rb):
+        (llo, lhi), (rlo, rhi) = lb, rb
+        return [llo[0], lhi[0], llo[1], lhi[1], rlo[0], rhi[0], rlo[1], rhi[1], llo[2], lhi[2], rlo[2], rhi[2]]
+
+    want = np.array([row(T1, T0), row(T01, T2)], f)
+    got = bvh.subtree_boxes(V, F, order, L, R, rl, rr)
+    assert got.dtype == np.float32 and np.array_equal(got, want)
+
+
+def _union_boxes(V, F, order, L, R, root):
+    """The same boxes by a different algorithm: a post-order walk that
+    unites the two children's boxes (min / max are exact, so the order of
+    the unions cannot change a bit)."""
+    tri = np.asarray(V, np.float32)[np.asarray(F)[order]]
+    tlo, thi = tri.min(axis=1), tri.max(axis=1)
+    out = np.empty((len(L), 12), np.float32)
+    memo = {}
+    stack = [(root, False)]
+    while stack:
+        g, done = stack.pop()
+        if g < 0:
+            memo[g] = (tlo[~g], thi[~g])
+            continue
+        if not done:
+            stack.append((g, True))
+            stack.extend([(int(L[g]), False), (int(R[g]), False)])
+            continue
+        (llo, lhi), (rlo, rhi) = memo[int(L[g])], memo[int(R[g])]
+        out[g] = [llo[0], lhi[0], llo[1], lhi[1], rlo[0], rhi[0], rlo[1], rhi[1], llo[2], lhi[2], rlo[2], rhi[2]]
+        memo[g] = (np.minimum(llo, rlo), np.maximum(lhi, rhi))
+    return out
+
+
+def test_subtree_boxes_equal_bottom_up_unions_for_a_moved_pose():
+    """The tree of one hand pose refit to another pose (same faces): the
+    range definition and the bottom-up unions agree bit for bit, and every
+    triangle of the new pose lies in all boxes on its root path."""
+    a = I.hand_scene(11, 1500)
+    b = I.hand_scene(12, 1500)
+    assert np.array_equal(a.F, b.F)
+    codes = bvh.morton_codes(a.V, a.F)
+    order = bvh.sorted_order(codes)
+    L, R, rl, rr, root = bvh.radix_tree(codes[order])
+    got = bvh.subtree_boxes(b.V, b.F, order, L, R, rl, rr)
+    assert np.array_equal(got, _union_boxes(b.V, b.F, order, L, R, root))
+    tri = b.V[b.F[order]]
+    for g in range(len(L)):
+        for side, kid in ((0, L[g]), (1, R[g])):
+            a_, z_ = (~kid, ~kid) if kid < 0 else (rl[kid], rr[kid])
+            lo = got[g, [4 * side, 4 * side + 2, 8 + 2 * side]]
+            hi = got[g, [4 * side + 1, 4 * side + 3, 9 + 2 * side]]
+            pts = tri[a_:z_ + 1].reshape(-1, 3)
+            assert (pts >= lo).all() and (pts <= hi).all()
