@@ -264,10 +264,14 @@ __device__ __forceinline__ void climb_leaf(int i, int n, const uint32_t *__restr
       reinterpret_cast<float2 *>(&np->lrz)[1] = make_float2(lo.z, hi.z);
       np->kids.y = cur;
     }
-    __threadfence();
-    const int other = atomicExch(flags + p, as_left ? l : r);
+    // release: this child's box is visible before the flag; acquire: the
+    // sibling's box is visible after it (no full fences on the climb)
+    int other;
+    asm volatile("atom.acq_rel.gpu.global.exch.b32 %0, [%1], %2;"
+                 : "=r"(other)
+                 : "l"(flags + p), "r"(as_left ? l : r)
+                 : "memory");
     if (other < 0) return;  // first to arrive: the sibling's thread goes on
-    __threadfence();
     float4 sxy;
     float2 sz;
     if (as_left) {

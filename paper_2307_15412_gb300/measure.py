@@ -20,6 +20,15 @@ tiny: the ~2k-triangle hand at 0.30 m, 64 x 64 rays over +-30 deg, 1 TX
 synthesis, latency of a lone frame), and `jobs` seeded poses per
 rr_batch_run (CUDA graph, autotuned) for each synthesis variant.
 
+motion: the benchmark's 16 full-frame hands (~22k triangles, 512 x 512
+rays over +-45 deg, 1 TX 3 RX, 64 chirps x 256 samples, split-BF16x3
+synthesis), each moving through a 30-frame joint-angle trajectory
+between two seeded poses while translating at its radial speed (frames
+back to back, 64 x 64 us apart); every step copies each hand's next pose from device memory
+(rr_scene_update_vertices, outside the timed region) and runs the batch
+with the trees rebuilt, or refit (RR_BATCH_REFIT) from the first frame's
+build.
+
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -188,9 +197,89 @@ def measure_tiny(args):
     ctx.close()
 
 
+def measure_motion(args):
+    torch, I, rr, ctx = _setup()
+    radar, grid, nt = I.workload_full_frame()
+    n_scenes, n_poses = 16, 30
+    dt = radar.n_chirps * radar.t_chirp  # back-to-back frames (64 x 64 us)
+    poses = []   # [pose][scene] vertex arrays
+    vels = []
+    for k in range(n_scenes):
+        s0 = I.hand_scene(7000 + k, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+        rng = np.random.default_rng(7100 + k)
+        a1 = I.random_hand_angles(rng)
+        row = []
+        for f in range(n_poses):
+            ang = s0.angles_deg + (a1 - s0.angles_deg) * f / (n_poses - 1)
+            centre = s0.center + s0.vel.astype(np.float64) * dt * f
+            sf = I.hand_scene(0, nt, angles_deg=ang, center=centre)
+            assert np.array_equal(sf.F, s0.F)
+            row.append(sf.V)
+        poses.append(row)
+        vels.append(s0.vel)
+        ctx.scene_upload(k, row[0], s0.F, s0.vel)
+    dev_poses = torch.tensor(np.stack([np.stack([poses[k][f] for k in range(n_scenes)]) for f in range(n_poses)]),
+                             dtype=torch.float32, device="cuda")
+    jobs = [(k, grid) for k in range(n_scenes)]
+    out = torch.empty((n_scenes, radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+
+    def set_pose(f):
+        for k in range(n_scenes):
+            ctx.scene_update_vertices(k, dev_poses[f % n_poses, k], vels[k])
+
+    res = {}
+    for name, refit in (("rebuild", False), ("refit", True)):
+        set_pose(0)
+        ctx.batch_run(jobs, radar, rd_out=out, variant=1, graph=False, autotune=True)  # trees of the first pose
+        for _ in range(3):  # warm-up (and graph capture)
+            ctx.batch_run(jobs, radar, rd_out=out, variant=1, graph=True, autotune=True, refit=refit)
+        ctx.sync()
+        steps = n_poses * 2
+        ctx.timing_enable(steps)
+        for f in range(steps):
+            set_pose(f)
+            flush.zero_()
+            ctx.batch_run(jobs, radar, rd_out=out, variant=1, graph=True, autotune=True, refit=refit)
+        ctx.sync()
+        ms = np.array([ctx.timing_read(i)[4] for i in range(steps)])
+        ctx.timing_enable(0)
+        # stage times (eager) at the trajectory's first and last pose
+        stages = {}
+        set_pose(0)
+        ctx.batch_run(jobs, radar, rd_out=out, variant=1, graph=False, autotune=True)  # trees of the first pose
+        for tag, f in (("first_pose", 0), ("last_pose", n_poses - 1)):
+            ctx.timing_enable(2)
+            for _ in range(2):
+                set_pose(f)
+                flush.zero_()
+                ctx.batch_run(jobs, radar, rd_out=out, variant=1, graph=False, autotune=True, refit=refit)
+            ctx.sync()
+            st = np.array([ctx.timing_read(i) for i in range(2)]).mean(0)
+            ctx.timing_enable(0)
+            stages[tag] = {"build_or_refit": float(st[0]), "trace": float(st[1]), "synth": float(st[2]),
+                           "rd": float(st[3])}
+        if refit:
+            # the refit trees must hold the same hits as fresh builds (nearest hits are exact either way)
+            ref = out.clone()
+            ctx2_out = torch.empty_like(out)
+            for k in range(n_scenes):
+                ctx.scene_upload(100 + k, poses[k][n_poses - 1], I.hand_scene(7000 + k, nt).F, vels[k])
+            ctx.batch_run([(100 + k, grid) for k in range(n_scenes)], radar, rd_out=ctx2_out, variant=1)
+            ctx.sync()
+            d = (ctx2_out - ref).double().norm() / ref.double().norm()
+            stages["rel_l2_vs_rebuilt_trees_last_pose"] = float(d)
+        res[name] = {"frames_per_s": n_scenes / (ms.mean() / 1e3), "ms_per_step": float(ms.mean()),
+                     "stage_ms": stages}
+    print(json.dumps({"workload": "motion: 16 full-frame hands (%d triangles), 30-frame joint-angle trajectories "
+                                  "plus radial translation, 512^2 rays, 64 x 256, BF16x3; L2 flushed per step; "
+                                  "pose copies outside the timed region" % nt, "results": res}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "surrogate", "tiny"])
+    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion"])
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--train", type=int, default=200000)
@@ -202,6 +291,8 @@ def main():
         measure_batch(args)
     elif args.what == "tiny":
         measure_tiny(args)
+    elif args.what == "motion":
+        measure_motion(args)
     else:
         measure_surrogate(args)
 
