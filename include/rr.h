@@ -185,6 +185,35 @@ rr_status rr_trace_frame(rr_ctx *ctx, int scene, const rr_radar *radar, const rr
 rr_status rr_get_hits(rr_ctx *ctx, int scene, int64_t capacity, int32_t *ray, int32_t *tri,
                       float *t, float *d, float *amp, float *ddot);
 
+/* Casts rays to each mesh triangle (Sec. III: multiple rays are cast to
+ * each mesh triangle and the scattering of each face is simulated) instead
+ * of over a ray grid: k = samples_per_side (1..4) gives k^2 rays per
+ * triangle, from radar->tx to the centroids of the k x k sub-triangles of
+ * the triangle's regular subdivision (barycentric ((i + 1/3) / k, (j + 1/3)
+ * / k) for i + j <= k - 1, then ((i + 2/3) / k, (j + 2/3) / k) for i + j <=
+ * k - 2).  A sample is received when its nearest hit is its own triangle
+ * (visibility, same traversal and tie rules as rr_trace_frame); each
+ * received sample stands for area / k^2 of its face and is echoed like a
+ * grid ray with solid angle Omega = (area / k^2) |n . u| / t^2.  The
+ * scene's hit list then holds the received samples (ray index = triangle
+ * id * k^2 + sample), ready for rr_get_hits, rr_synth_if and
+ * rr_alpha_sweep.  hit_capacity <= 0 means nt * k^2.  Errors and the
+ * n_hits_out readback as for rr_trace_frame. */
+rr_status rr_trace_triangles(rr_ctx *ctx, int scene, const rr_radar *radar, int samples_per_side,
+                             int64_t hit_capacity, int64_t *n_hits_out);
+
+/* IF cubes of the scene's last trace (grid or triangles) for n_alpha
+ * values of the material mixture alpha (Eq. 3; 1 <= n_alpha <= 64, each in
+ * [0, 1]), e.g. the sweep 0, 0.1, ..., 1 of the paper's comparison.  The
+ * echo amplitude is linear in alpha and path lengths do not depend on it,
+ * so the call synthesises alpha = 0 and alpha = 1 once and writes
+ * if_out[a] = s(0) + alpha_a (s(1) - s(0)) (device complex64
+ * [n_alpha][n_rx][n_chirps][n_samples]).  alphas: host floats.  The
+ * scene's echo is left at radar->alpha.  Variants and errors as for
+ * rr_synth_if. */
+rr_status rr_alpha_sweep(rr_ctx *ctx, int scene, const rr_radar *radar, rr_synth_variant variant, int n_alpha,
+                         const float *alphas, float *if_out);
+
 /* ---- IF synthesis (Eq. 4, FMCW form) ------------------------------------ */
 
 /* if_out[j][m][n] = sum_k a_kj exp(-j 2 pi (f0 + S t_n)(d_kj + ddot_kj m T_rep) / c)

@@ -157,3 +157,50 @@ def frame(scene_V, scene_F, vel, radar, grid, rays=None):
                     np.asarray(vel, np.float64))
     return dict(ray_ids=rays, tri=tri, t=t, hit_rays=rays[hit], d=d, a=a, ddot=dd,
                 if_cube=synth(d, a, dd, radar))
+
+
+def triangle_samples(V, F, k: int):
+    """Sample points of the per-triangle casting (rays cast to each mesh
+    triangle, Sec. III): for every triangle (id order) the k * k centroids of
+    the sub-triangles of its regular k-subdivision -- "up" cells (i, j) with
+    i + j <= k - 1 at barycentric ((i + 1/3) / k, (j + 1/3) / k) row by row,
+    then "down" cells with i + j <= k - 2 at ((i + 2/3) / k, (j + 2/3) / k).
+    Returns (points float64 [n * k^2, 3], triangle id [n * k^2], sample index
+    [n * k^2]), triangle-major."""
+    b = [((i + 1.0 / 3.0) / k, (j + 1.0 / 3.0) / k) for i in range(k) for j in range(k - i)]
+    b += [((i + 2.0 / 3.0) / k, (j + 2.0 / 3.0) / k) for i in range(k - 1) for j in range(k - 1 - i)]
+    b = np.asarray(b, np.float64)                     # [S, 2]
+    V64 = np.asarray(V, np.float32).astype(np.float64)
+    F = np.asarray(F, np.int64)
+    v0 = V64[F[:, 0]]
+    e1, e2 = V64[F[:, 1]] - v0, V64[F[:, 2]] - v0
+    P = v0[:, None, :] + b[None, :, 0:1] * e1[:, None, :] + b[None, :, 1:2] * e2[:, None, :]
+    n, S = F.shape[0], b.shape[0]
+    return P.reshape(-1, 3), np.repeat(np.arange(n), S), np.tile(np.arange(S), n)
+
+
+def triangle_frame(V, F, vel, radar, k: int):
+    """Frame of the per-triangle casting: a ray from the TX to every sample
+    point (``triangle_samples``), received when its brute-force nearest hit
+    is the sample's own triangle; each received sample stands for area / k^2
+    of its face, seen under the solid angle (area / k^2) |n . u| / t^2, and
+    is echoed and synthesised like a grid ray's hit (t = the exact distance
+    to the sample point).  Returns the per-sample visibility, the received
+    samples' ray ids (triangle id * k^2 + sample), their echo and the IF."""
+    P, tid, samp = triangle_samples(V, F, k)
+    S = k * k
+    origin = np.asarray(radar.tx, np.float64)
+    w = P - origin
+    t = np.sqrt((w * w).sum(axis=1))
+    dirs = w / t[:, None]
+    hit, _ = trace(V, F, origin, dirs)
+    vis = hit == tid
+    V64 = np.asarray(V, np.float32).astype(np.float64)
+    Fi = np.asarray(F, np.int64)
+    nrm = np.cross(V64[Fi[:, 1]] - V64[Fi[:, 0]], V64[Fi[:, 2]] - V64[Fi[:, 0]])   # |nrm| = 2 area
+    omega = 0.5 * np.abs((dirs * nrm[tid]).sum(axis=1)) / (S * t * t)
+    rays = tid * S + samp
+    d, a, dd = echo(V, F, origin, dirs[vis], t[vis], tid[vis].astype(np.int32), omega[vis], radar,
+                    np.asarray(vel, np.float64))
+    return dict(visible=vis, ray_ids=rays, hit_rays=rays[vis], omega=omega, d=d, a=a, ddot=dd,
+                if_cube=synth(d, a, dd, radar))

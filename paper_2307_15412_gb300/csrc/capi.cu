@@ -459,6 +459,26 @@ rr_status rr_refit_bvh(rr_ctx *c, int scene) {
   return RR_OK;
 }
 
+// Hit arrays of a scene with room for cap hits (grown, never shrunk).
+static rr_status ensure_hits(rr_ctx *c, SceneDev *s, int64_t cap) {
+  if (cap <= s->hit_cap && s->hit_ray) return RR_OK;
+  void *old[] = {s->hit_ray, s->hit_tri, s->hit_pos, s->hit_t, s->hit_d, s->hit_a, s->hit_dd};
+  for (void *p : old)
+    if (p) cudaFree(p);
+  s->hit_ray = s->hit_tri = s->hit_pos = nullptr;
+  s->hit_t = s->hit_d = s->hit_a = s->hit_dd = nullptr;
+  s->hit_cap = 0;
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_ray, sizeof(int32_t) * cap), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_tri, sizeof(int32_t) * cap), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_pos, sizeof(int32_t) * cap), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_t, sizeof(float) * cap), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_d, sizeof(float) * cap * RR_MAX_RX), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_a, sizeof(float) * cap * RR_MAX_RX), "hit list");
+  RR_CUDA(c, cudaMalloc((void **)&s->hit_dd, sizeof(float) * cap * RR_MAX_RX), "hit list");
+  s->hit_cap = cap;
+  return RR_OK;
+}
+
 rr_status rr_trace_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_raygrid *grid,
                          int64_t hit_capacity, int64_t *n_hits_out) {
   if (!c) return RR_EINVAL;
@@ -474,22 +494,7 @@ rr_status rr_trace_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_r
   const int64_t n_rays = (int64_t)grid->n_az * grid->n_el;
   const int64_t cap = hit_capacity > 0 ? hit_capacity : n_rays;
   DeviceGuard g(c->device);
-  if (cap > s->hit_cap || !s->hit_ray) {
-    void *old[] = {s->hit_ray, s->hit_tri, s->hit_pos, s->hit_t, s->hit_d, s->hit_a, s->hit_dd};
-    for (void *p : old)
-      if (p) cudaFree(p);
-    s->hit_ray = s->hit_tri = s->hit_pos = nullptr;
-    s->hit_t = s->hit_d = s->hit_a = s->hit_dd = nullptr;
-    s->hit_cap = 0;
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_ray, sizeof(int32_t) * cap), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_tri, sizeof(int32_t) * cap), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_pos, sizeof(int32_t) * cap), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_t, sizeof(float) * cap), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_d, sizeof(float) * cap * RR_MAX_RX), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_a, sizeof(float) * cap * RR_MAX_RX), "hit list");
-    RR_CUDA(c, cudaMalloc((void **)&s->hit_dd, sizeof(float) * cap * RR_MAX_RX), "hit list");
-    s->hit_cap = cap;
-  }
+  if ((st = ensure_hits(c, s, cap)) != RR_OK) return st;
   const rr::RadarDev rd = to_dev(radar);
   const rr::GridDev gd = to_dev(grid);
   RR_CUDA(c, grow(c->dir, c->dir_cap, (int64_t)grid->n_az + grid->n_el), "ray-direction table");
@@ -497,6 +502,11 @@ rr_status rr_trace_frame(rr_ctx *c, int scene, const rr_radar *radar, const rr_r
   s->hit_nrx = radar->n_rx;
   s->hit_used_cap = cap;
   s->traced = true;
+  s->trace_mode = 0;
+  s->last_naz = grid->n_az;
+  s->last_nel = grid->n_el;
+  s->last_haz = grid->half_az;
+  s->last_hel = grid->half_el;
   if (n_hits_out) {
     RR_CUDA(c, cudaMemcpyAsync(c->h_counts + scene, s->hit_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream),
             "hit count readback");
@@ -541,6 +551,84 @@ rr_status rr_synth_if(rr_ctx *c, int scene, const rr_radar *radar, rr_synth_vari
   DeviceGuard g(c->device);
   return run_synth(c, radar, variant, s->hit_count, s->hit_used_cap, s->hit_used_cap, s->hit_d, s->hit_a, s->hit_dd,
                    if_out);
+}
+
+rr_status rr_trace_triangles(rr_ctx *c, int scene, const rr_radar *radar, int samples_per_side, int64_t hit_capacity,
+                             int64_t *n_hits_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->built) return fail(c, RR_ENOTREADY, "scene %d: build_bvh must follow scene_upload", scene);
+  if (!check_radar(c, radar, &st)) return st;
+  const int k = samples_per_side;
+  if (k < 1 || k > rr::kMaxTriSide) return fail(c, RR_EINVAL, "samples_per_side=%d out of [1,%d]", k, rr::kMaxTriSide);
+  const int64_t n_rays = s->nt * k * k;
+  if (n_rays > ((int64_t)1 << 31) - 1) return fail(c, RR_EINVAL, "triangles x samples exceed 2^31");
+  const int64_t cap = hit_capacity > 0 ? hit_capacity : (n_rays > 0 ? n_rays : 1);
+  DeviceGuard g(c->device);
+  if ((st = ensure_hits(c, s, cap)) != RR_OK) return st;
+  const rr::RadarDev rd = to_dev(radar);
+  RR_CUDA(c, rr::launch_trace_tris(*s, rd, k, cap, c->d_err, c->stream), "trace_triangles launch");
+  s->hit_nrx = radar->n_rx;
+  s->hit_used_cap = cap;
+  s->traced = true;
+  s->trace_mode = 1;
+  s->tri_k = k;
+  if (n_hits_out) {
+    RR_CUDA(c, cudaMemcpyAsync(c->h_counts + scene, s->hit_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream),
+            "hit count readback");
+    c->pending.push_back({n_hits_out, nullptr, scene, cap});
+  }
+  return RR_OK;
+}
+
+// Echo of the scene's last trace again with material mixture alpha.
+static rr_status re_echo(rr_ctx *c, SceneDev *s, const rr::RadarDev &rd, float alpha) {
+  if (s->trace_mode == 1) {
+    RR_CUDA(c, rr::launch_echo_tris(*s, rd, s->tri_k, s->hit_used_cap, alpha, c->stream), "echo launch");
+    return RR_OK;
+  }
+  rr_raygrid gr;
+  gr.n_az = s->last_naz;
+  gr.n_el = s->last_nel;
+  gr.half_az = s->last_haz;
+  gr.half_el = s->last_hel;
+  RR_CUDA(c, grow(c->dir, c->dir_cap, (int64_t)gr.n_az + gr.n_el), "ray-direction table");
+  RR_CUDA(c, rr::launch_echo_grid(*s, rd, to_dev(&gr), s->hit_used_cap, c->dir, alpha, c->stream), "echo launch");
+  return RR_OK;
+}
+
+rr_status rr_alpha_sweep(rr_ctx *c, int scene, const rr_radar *radar, rr_synth_variant variant, int n_alpha,
+                         const float *alphas, float *if_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->traced) return fail(c, RR_ENOTREADY, "scene %d: trace_frame or trace_triangles must come first", scene);
+  if ((st = synth_checks(c, radar, variant)) != RR_OK) return st;
+  if (radar->n_rx != s->hit_nrx) return fail(c, RR_EINVAL, "radar n_rx differs from the traced hit list");
+  if (n_alpha < 1 || n_alpha > rr::kMaxAlphas || !alphas || !if_out)
+    return fail(c, RR_EINVAL, "n_alpha=%d out of [1,%d] or null arrays", n_alpha, rr::kMaxAlphas);
+  rr::AlphaList al;
+  al.n = n_alpha;
+  for (int a = 0; a < n_alpha; ++a) {
+    if (!(alphas[a] >= 0.f && alphas[a] <= 1.f)) return fail(c, RR_EINVAL, "alpha[%d] out of [0,1]", a);
+    al.v[a] = alphas[a];
+  }
+  DeviceGuard g(c->device);
+  const rr::RadarDev rd = to_dev(radar);
+  const int64_t cube = (int64_t)radar->n_rx * radar->n_chirps * radar->n_samples;  // complex values
+  RR_CUDA(c, grow(c->if_tmp, c->if_tmp_cap, 4 * cube), "alpha sweep buffers");
+  for (int end = 0; end < 2; ++end) {  // the specular (alpha = 0) and diffuse (alpha = 1) cubes
+    if ((st = re_echo(c, s, rd, (float)end)) != RR_OK) return st;
+    if ((st = run_synth(c, radar, variant, s->hit_count, s->hit_used_cap, s->hit_used_cap, s->hit_d, s->hit_a,
+                        s->hit_dd, c->if_tmp + 2 * cube * end)) != RR_OK)
+      return st;
+  }
+  RR_CUDA(c, rr::launch_alpha_mix(c->if_tmp, c->if_tmp + 2 * cube, cube, al, if_out, c->stream), "alpha mix");
+  // leave the scene's echo at the radar's own alpha
+  return re_echo(c, s, rd, radar->alpha);
 }
 
 rr_status rr_synth_if_from_hits(rr_ctx *c, const rr_radar *radar, rr_synth_variant variant, int64_t K,

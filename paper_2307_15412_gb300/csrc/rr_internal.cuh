@@ -88,6 +88,12 @@ struct SceneDev {
   float *hit_a = nullptr;
   float *hit_dd = nullptr;
   bool traced = false;
+  // the last trace, for a later echo with another material mixture:
+  // 0 = ray grid (n_az x n_el over +-half angles), 1 = rays to each triangle
+  // (tri_k x tri_k samples per triangle)
+  int trace_mode = 0, tri_k = 0;
+  int last_naz = 0, last_nel = 0;
+  double last_haz = 0.0, last_hel = 0.0;
 };
 
 // Radar parameters in the form the kernels use.
@@ -177,6 +183,24 @@ cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64
 // JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1]; order (may be
 // null): device int[n_jobs], filled with the frames by decreasing hit count.
 // Each table entry's dir must hold n_az + n_el entries.
+// Rays cast to each mesh triangle (see trace_tris.cu): k x k samples per
+// triangle (1 <= k <= kMaxTriSide), visible samples appended to the scene's
+// hit list (ray = triangle id * k^2 + sample) and echoed with `alpha`.
+constexpr int kMaxTriSide = 4;
+cudaError_t launch_trace_tris(SceneDev &s, const RadarDev &r, int k, int64_t cap, uint32_t *err, cudaStream_t st);
+cudaError_t launch_echo_tris(SceneDev &s, const RadarDev &r, int k, int64_t cap, float alpha, cudaStream_t st);
+// Echo of the scene's last grid trace again, with material mixture `alpha`
+// (the grid's direction table is refilled first).
+cudaError_t launch_echo_grid(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir, float alpha,
+                             cudaStream_t st);
+// out[a] = s0 + alphas[a] (s1 - s0) for the n cubes of cube_complex complex values.
+constexpr int kMaxAlphas = 64;
+struct AlphaList {
+  int n;
+  float v[kMaxAlphas];
+};
+cudaError_t launch_alpha_mix(const float *s0, const float *s1, int64_t cube_complex, const AlphaList &al, float *out,
+                             cudaStream_t st);
 cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix, int *order,
                                const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,

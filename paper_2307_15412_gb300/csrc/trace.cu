@@ -33,70 +33,7 @@ namespace rr {
 namespace {
 
 constexpr int kTraceThreads = 128;        // 4 warps, each tracing 8 x 4 ray tiles
-constexpr int kPend = 4;                  // leaves a lane may queue before the warp tests them
-constexpr float kBoxSlack = 1.0000004f;   // covers FP32 rounding of the slab test
-
-struct RayPre {
-  float ox, oy, oz;
-  float ix, iy, iz;  // 1 / direction
-  int kx, ky, kz;
-  float Sx, Sy, Sz;
-};
-
-__device__ __forceinline__ float safe_inv(float d) {
-  const float a = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
-  return 1.0f / a;
-}
-
-// slab test; returns entry distance or +inf
-__device__ __forceinline__ float box_entry(const RayPre &r, float lx, float hx, float ly, float hy,
-                                           float lz, float hz, float tmax) {
-  const float tx0 = (lx - r.ox) * r.ix, tx1 = (hx - r.ox) * r.ix;
-  const float ty0 = (ly - r.oy) * r.iy, ty1 = (hy - r.oy) * r.iy;
-  const float tz0 = (lz - r.oz) * r.iz, tz1 = (hz - r.oz) * r.iz;
-  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
-  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
-  return (tn <= tf * kBoxSlack && tn <= tmax) ? tn : INFINITY;
-}
-
-__device__ __forceinline__ float sel3(float x, float y, float z, int k) {
-  return k == 0 ? x : (k == 1 ? y : z);
-}
-
-// Watertight ray-triangle test; updates (best_t, best_pos, best_id).
-__device__ __forceinline__ void tri_test(const RayPre &r, const float4 *__restrict__ tris, int pos,
-                                         float &best_t, int &best_pos, int &best_id) {
-  const float4 a = __ldg(tris + 3 * pos), b = __ldg(tris + 3 * pos + 1), c = __ldg(tris + 3 * pos + 2);
-  const int id = __float_as_int(a.w);
-  const float a0 = a.x - r.ox, a1 = a.y - r.oy, a2 = a.z - r.oz;
-  const float b0 = b.x - r.ox, b1 = b.y - r.oy, b2 = b.z - r.oz;
-  const float c0 = c.x - r.ox, c1 = c.y - r.oy, c2 = c.z - r.oz;
-  const float Akz = sel3(a0, a1, a2, r.kz), Bkz = sel3(b0, b1, b2, r.kz), Ckz = sel3(c0, c1, c2, r.kz);
-  const float Ax = sel3(a0, a1, a2, r.kx) - r.Sx * Akz, Ay = sel3(a0, a1, a2, r.ky) - r.Sy * Akz;
-  const float Bx = sel3(b0, b1, b2, r.kx) - r.Sx * Bkz, By = sel3(b0, b1, b2, r.ky) - r.Sy * Bkz;
-  const float Cx = sel3(c0, c1, c2, r.kx) - r.Sx * Ckz, Cy = sel3(c0, c1, c2, r.ky) - r.Sy * Ckz;
-  // edge functions without contraction: a shared edge gives exactly opposite values
-  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
-  float Vv = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
-  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
-  if (U == 0.f || Vv == 0.f || W == 0.f) {
-    // exact sign from double products of the float operands
-    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
-    Vv = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
-    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
-  }
-  if ((U < 0.f || Vv < 0.f || W < 0.f) && (U > 0.f || Vv > 0.f || W > 0.f)) return;
-  const float det = U + Vv + W;
-  if (det == 0.f) return;
-  const float T = U * (r.Sz * Akz) + Vv * (r.Sz * Bkz) + W * (r.Sz * Ckz);
-  const float t = T / det;
-  if (!(t > 0.f)) return;
-  if (t < best_t || (t == best_t && id < best_id)) {
-    best_t = t;
-    best_pos = pos;
-    best_id = id;
-  }
-}
+#include "traverse.cuh"
 
 // Conservative index rectangle [i0, i1) x [j0, j1) of the rays that can meet
 // the scene box: the box corners in the radar frame bound azimuth exactly
@@ -245,90 +182,7 @@ k_trace(const FrameJob one, const FrameJob *__restrict__ table, const JobTiles *
         else active = true;
       }
     }
-    // Warp-uniform traversal with postponed leaves (the while-while scheme
-    // of Aila and Laine, HPG 2009): each lane walks internal nodes and queues
-    // the leaves whose boxes it enters (up to kPend); the warp runs the
-    // triangle tests only when at least half of its working lanes have
-    // leaves queued or no lane can take a node step, so the long triangle
-    // test runs with most lanes busy instead of for one lane at a time.
-    // Every iteration ends at the votes, so a warp costs the longest of its
-    // rays' walks, not the sum of its lanes' walks.  Pruning uses the best
-    // distance found so far (a bound on the final one) and equal distances
-    // keep the lowest id, so the hit does not depend on the order of the
-    // tests.  A tree of n - 1 internal nodes is walked in at most n - 1 node
-    // steps; more means a malformed tree, reported instead of looping.
-    int stack_node[kStackDepth];
-    float stack_t[kStackDepth];
-    int sp = 0, node = active ? root : -1, visits = 0;
-    int p0 = 0, p1 = 0, p2 = 0, p3 = 0, np = 0;  // queued leaf positions (kPend = 4)
-    while (true) {
-      const bool can_step = node >= 0 && np <= kPend - 2;
-      const uint32_t working = __ballot_sync(0xffffffffu, node >= 0 || np > 0);
-      if (working == 0u) break;
-      const uint32_t queued = __ballot_sync(0xffffffffu, np > 0);
-      const uint32_t steppers = __ballot_sync(0xffffffffu, can_step);
-      if (steppers == 0u || 2 * __popc(queued) >= __popc(working)) {
-        if (np > 0) tri_test(rp, J.tris, p0, best_t, best_pos, best_id);
-        if (np > 1) tri_test(rp, J.tris, p1, best_t, best_pos, best_id);
-        if (np > 2) tri_test(rp, J.tris, p2, best_t, best_pos, best_id);
-        if (np > 3) tri_test(rp, J.tris, p3, best_t, best_pos, best_id);
-        np = 0;
-        continue;
-      }
-      if (!can_step) continue;
-      if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) {
-        atomicOr(err, ERR_BAD_INPUT);
-        node = -1; np = 0; sp = 0;
-        continue;
-      }
-      ++visits;
-      const float4 lxy = __ldg(&J.nodes[node].lxy);
-      const float4 rxy = __ldg(&J.nodes[node].rxy);
-      const float4 lrz = __ldg(&J.nodes[node].lrz);
-      const int4 kids = __ldg(&J.nodes[node].kids);
-      const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
-      const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
-      bool hl = tl < INFINITY, hr = tr < INFINITY;
-      if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
-        atomicOr(err, ERR_BAD_INPUT);
-        node = -1; np = 0; sp = 0;
-        continue;
-      }
-      if (hl && kids.x < 0) {
-        const int q = ~kids.x;
-        if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
-        ++np;
-        hl = false;
-      }
-      if (hr && kids.y < 0) {
-        const int q = ~kids.y;
-        if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
-        ++np;
-        hr = false;
-      }
-      if (hl && hr) {
-        const bool lnear = tl <= tr;
-        if (sp == kStackDepth) {
-          atomicOr(err, ERR_STACK_OVERFLOW);
-          node = -1; np = 0; sp = 0;
-          continue;
-        }
-        stack_node[sp] = lnear ? kids.y : kids.x;
-        stack_t[sp] = lnear ? tr : tl;
-        ++sp;
-        node = lnear ? kids.x : kids.y;
-      } else if (hl) {
-        node = kids.x;
-      } else if (hr) {
-        node = kids.y;
-      } else {
-        node = -1;
-        while (sp > 0) {
-          --sp;
-          if (stack_t[sp] <= best_t) { node = stack_node[sp]; break; }
-        }
-      }
-    }
+    traverse_warp(rp, J, n, root, active, best_t, best_pos, best_id, err);
     // warp-aggregated append
     const bool has = best_pos >= 0;
     const uint32_t mask = __ballot_sync(0xffffffffu, has);
@@ -471,7 +325,7 @@ __device__ __forceinline__ int job_of_hit(const int64_t *__restrict__ pre, int n
 
 __global__ void __launch_bounds__(128)
 k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__restrict__ pre, int n_jobs,
-       const RadarDev r) {
+       const RadarDev r, float alpha) {
   const int64_t total = table ? pre[n_jobs] : min((int64_t)*one.count, one.cap);
   for (int64_t h = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; h < total; h += (int64_t)gridDim.x * blockDim.x) {
     const int job = table ? job_of_hit(pre, n_jobs, h) : 0;
@@ -519,13 +373,25 @@ k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__
       if (co > 0.f) {
         const float sdot = -(mr[0] * uj[0] + mr[1] * uj[1] + mr[2] * uj[2]);
         const float s = sdot > 0.f ? powf(sdot, r.spec_exp) : 0.f;
-        gj = (1.f - r.alpha) * s + r.alpha * (ci * co);
+        gj = (1.f - alpha) * s + alpha * (ci * co);
       }
       const int64_t o = (int64_t)j * J.ld + hl;
       J.hit_d[o] = (float)(t + (double)rj);
       J.hit_a[o] = r.amp_mode == 1 ? 1.f : omega * gj / (tf * rj);
       J.hit_dd[o] = J.vel[0] * (uf[0] + uj[0]) + J.vel[1] * (uf[1] + uj[1]) + J.vel[2] * (uf[2] + uj[2]);
     }
+  }
+}
+
+// The FP64 (sin, cos) table of a grid's azimuths and elevations (as the
+// trace kernel's side job writes it).
+__global__ void k_dir_table(const GridDev g, double2 *__restrict__ dir) {
+  const int na = g.n_az, ne = g.n_el;
+  for (int e = blockIdx.x * blockDim.x + threadIdx.x; e < na + ne; e += gridDim.x * blockDim.x) {
+    const double ang = e < na ? -g.half_az + g.daz * ((e) + 0.5) : -g.half_el + g.del * ((e - na) + 0.5);
+    double sv, cv;
+    sincos(ang, &sv, &cv);
+    dir[e] = make_double2(sv, cv);
   }
 }
 
@@ -586,7 +452,22 @@ cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64
   if (e != cudaSuccess) return e;
   const int64_t want = (cap + 127) / 128;
   const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
-  k_echo<<<blocks, 128, 0, st>>>(one, nullptr, nullptr, 1, r);
+  k_echo<<<blocks, 128, 0, st>>>(one, nullptr, nullptr, 1, r, r.alpha);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_echo_grid(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir, float alpha,
+                             cudaStream_t st) {
+  if (!dir) return cudaErrorInvalidValue;
+  k_dir_table<<<(g.n_az + g.n_el + 255) / 256, 256, 0, st>>>(g, dir);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return e;
+  FrameJob one = frame_job_for(s, g, cap);
+  one.dir = dir;
+  const int sms = sm_count();
+  const int64_t want = (cap + 127) / 128;
+  const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
+  k_echo<<<blocks, 128, 0, st>>>(one, nullptr, nullptr, 1, r, alpha);
   return cudaGetLastError();
 }
 
@@ -606,7 +487,7 @@ cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, 
   k_batch_hit_prefix<<<1, 1024, 0, st>>>(table, n_jobs, hit_prefix, order);
   e = cudaGetLastError();
   if (e != cudaSuccess) return e;
-  k_echo<<<4 * sms, 128, 0, st>>>(none, table, hit_prefix, n_jobs, r);
+  k_echo<<<4 * sms, 128, 0, st>>>(none, table, hit_prefix, n_jobs, r, r.alpha);
   return cudaGetLastError();
 }
 

@@ -1,0 +1,162 @@
+// traverse.cuh -- closest-hit traversal of the LBVH shared by the ray-grid
+// trace (trace.cu) and the per-triangle casting (trace_tris.cu): slab test,
+// watertight ray-triangle test, and the warp-uniform walk with postponed
+// leaves.  Included inside namespace rr { namespace { ... } }.
+constexpr int kPend = 4;                  // leaves a lane may queue before the warp tests them
+constexpr float kBoxSlack = 1.0000004f;   // covers FP32 rounding of the slab test
+
+struct RayPre {
+  float ox, oy, oz;
+  float ix, iy, iz;  // 1 / direction
+  int kx, ky, kz;
+  float Sx, Sy, Sz;
+};
+
+__device__ __forceinline__ float safe_inv(float d) {
+  const float a = fabsf(d) < 1e-30f ? copysignf(1e-30f, d) : d;
+  return 1.0f / a;
+}
+
+// slab test; returns entry distance or +inf
+__device__ __forceinline__ float box_entry(const RayPre &r, float lx, float hx, float ly, float hy,
+                                           float lz, float hz, float tmax) {
+  const float tx0 = (lx - r.ox) * r.ix, tx1 = (hx - r.ox) * r.ix;
+  const float ty0 = (ly - r.oy) * r.iy, ty1 = (hy - r.oy) * r.iy;
+  const float tz0 = (lz - r.oz) * r.iz, tz1 = (hz - r.oz) * r.iz;
+  const float tn = fmaxf(fmaxf(fminf(tx0, tx1), fminf(ty0, ty1)), fmaxf(fminf(tz0, tz1), 0.f));
+  const float tf = fminf(fminf(fmaxf(tx0, tx1), fmaxf(ty0, ty1)), fmaxf(tz0, tz1));
+  return (tn <= tf * kBoxSlack && tn <= tmax) ? tn : INFINITY;
+}
+
+__device__ __forceinline__ float sel3(float x, float y, float z, int k) {
+  return k == 0 ? x : (k == 1 ? y : z);
+}
+
+// Watertight ray-triangle test; updates (best_t, best_pos, best_id).
+__device__ __forceinline__ void tri_test(const RayPre &r, const float4 *__restrict__ tris, int pos,
+                                         float &best_t, int &best_pos, int &best_id) {
+  const float4 a = __ldg(tris + 3 * pos), b = __ldg(tris + 3 * pos + 1), c = __ldg(tris + 3 * pos + 2);
+  const int id = __float_as_int(a.w);
+  const float a0 = a.x - r.ox, a1 = a.y - r.oy, a2 = a.z - r.oz;
+  const float b0 = b.x - r.ox, b1 = b.y - r.oy, b2 = b.z - r.oz;
+  const float c0 = c.x - r.ox, c1 = c.y - r.oy, c2 = c.z - r.oz;
+  const float Akz = sel3(a0, a1, a2, r.kz), Bkz = sel3(b0, b1, b2, r.kz), Ckz = sel3(c0, c1, c2, r.kz);
+  const float Ax = sel3(a0, a1, a2, r.kx) - r.Sx * Akz, Ay = sel3(a0, a1, a2, r.ky) - r.Sy * Akz;
+  const float Bx = sel3(b0, b1, b2, r.kx) - r.Sx * Bkz, By = sel3(b0, b1, b2, r.ky) - r.Sy * Bkz;
+  const float Cx = sel3(c0, c1, c2, r.kx) - r.Sx * Ckz, Cy = sel3(c0, c1, c2, r.ky) - r.Sy * Ckz;
+  // edge functions without contraction: a shared edge gives exactly opposite values
+  float U = __fsub_rn(__fmul_rn(Cx, By), __fmul_rn(Cy, Bx));
+  float Vv = __fsub_rn(__fmul_rn(Ax, Cy), __fmul_rn(Ay, Cx));
+  float W = __fsub_rn(__fmul_rn(Bx, Ay), __fmul_rn(By, Ax));
+  if (U == 0.f || Vv == 0.f || W == 0.f) {
+    // exact sign from double products of the float operands
+    U = (float)((double)Cx * (double)By - (double)Cy * (double)Bx);
+    Vv = (float)((double)Ax * (double)Cy - (double)Ay * (double)Cx);
+    W = (float)((double)Bx * (double)Ay - (double)By * (double)Ax);
+  }
+  if ((U < 0.f || Vv < 0.f || W < 0.f) && (U > 0.f || Vv > 0.f || W > 0.f)) return;
+  const float det = U + Vv + W;
+  if (det == 0.f) return;
+  const float T = U * (r.Sz * Akz) + Vv * (r.Sz * Bkz) + W * (r.Sz * Ckz);
+  const float t = T / det;
+  if (!(t > 0.f)) return;
+  if (t < best_t || (t == best_t && id < best_id)) {
+    best_t = t;
+    best_pos = pos;
+    best_id = id;
+  }
+}
+
+
+// Closest hit of this lane's ray (rp) in the frame's tree (J.nodes, J.tris,
+// n triangles, root); `active` lanes start at the root, the others only take part in the
+// warp's votes.  Updates (best_t, best_pos, best_id); a malformed tree or a
+// full stack sets the error word and ends the lane's walk.  All 32 lanes of
+// the warp must call it together.
+__device__ __forceinline__ void traverse_warp(const RayPre &rp, const FrameJob &J, int n, int root, bool active,
+                                              float &best_t, int &best_pos, int &best_id, uint32_t *err) {
+  // Warp-uniform traversal with postponed leaves (the while-while scheme
+  // of Aila and Laine, HPG 2009): each lane walks internal nodes and queues
+  // the leaves whose boxes it enters (up to kPend); the warp runs the
+  // triangle tests only when at least half of its working lanes have
+  // leaves queued or no lane can take a node step, so the long triangle
+  // test runs with most lanes busy instead of for one lane at a time.
+  // Every iteration ends at the votes, so a warp costs the longest of its
+  // rays' walks, not the sum of its lanes' walks.  Pruning uses the best
+  // distance found so far (a bound on the final one) and equal distances
+  // keep the lowest id, so the hit does not depend on the order of the
+  // tests.  A tree of n - 1 internal nodes is walked in at most n - 1 node
+  // steps; more means a malformed tree, reported instead of looping.
+  int stack_node[kStackDepth];
+  float stack_t[kStackDepth];
+  int sp = 0, node = active ? root : -1, visits = 0;
+  int p0 = 0, p1 = 0, p2 = 0, p3 = 0, np = 0;  // queued leaf positions (kPend = 4)
+  while (true) {
+    const bool can_step = node >= 0 && np <= kPend - 2;
+    const uint32_t working = __ballot_sync(0xffffffffu, node >= 0 || np > 0);
+    if (working == 0u) break;
+    const uint32_t queued = __ballot_sync(0xffffffffu, np > 0);
+    const uint32_t steppers = __ballot_sync(0xffffffffu, can_step);
+    if (steppers == 0u || 2 * __popc(queued) >= __popc(working)) {
+      if (np > 0) tri_test(rp, J.tris, p0, best_t, best_pos, best_id);
+      if (np > 1) tri_test(rp, J.tris, p1, best_t, best_pos, best_id);
+      if (np > 2) tri_test(rp, J.tris, p2, best_t, best_pos, best_id);
+      if (np > 3) tri_test(rp, J.tris, p3, best_t, best_pos, best_id);
+      np = 0;
+      continue;
+    }
+    if (!can_step) continue;
+    if ((unsigned)node >= (unsigned)(n - 1) || visits >= n) {
+      atomicOr(err, ERR_BAD_INPUT);
+      node = -1; np = 0; sp = 0;
+      continue;
+    }
+    ++visits;
+    const float4 lxy = __ldg(&J.nodes[node].lxy);
+    const float4 rxy = __ldg(&J.nodes[node].rxy);
+    const float4 lrz = __ldg(&J.nodes[node].lrz);
+    const int4 kids = __ldg(&J.nodes[node].kids);
+    const float tl = box_entry(rp, lxy.x, lxy.y, lxy.z, lxy.w, lrz.x, lrz.y, best_t);
+    const float tr = box_entry(rp, rxy.x, rxy.y, rxy.z, rxy.w, lrz.z, lrz.w, best_t);
+    bool hl = tl < INFINITY, hr = tr < INFINITY;
+    if ((kids.x < 0 && (unsigned)~kids.x >= (unsigned)n) || (kids.y < 0 && (unsigned)~kids.y >= (unsigned)n)) {
+      atomicOr(err, ERR_BAD_INPUT);
+      node = -1; np = 0; sp = 0;
+      continue;
+    }
+    if (hl && kids.x < 0) {
+      const int q = ~kids.x;
+      if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
+      ++np;
+      hl = false;
+    }
+    if (hr && kids.y < 0) {
+      const int q = ~kids.y;
+      if (np == 0) p0 = q; else if (np == 1) p1 = q; else if (np == 2) p2 = q; else p3 = q;
+      ++np;
+      hr = false;
+    }
+    if (hl && hr) {
+      const bool lnear = tl <= tr;
+      if (sp == kStackDepth) {
+        atomicOr(err, ERR_STACK_OVERFLOW);
+        node = -1; np = 0; sp = 0;
+        continue;
+      }
+      stack_node[sp] = lnear ? kids.y : kids.x;
+      stack_t[sp] = lnear ? tr : tl;
+      ++sp;
+      node = lnear ? kids.x : kids.y;
+    } else if (hl) {
+      node = kids.x;
+    } else if (hr) {
+      node = kids.y;
+    } else {
+      node = -1;
+      while (sp > 0) {
+        --sp;
+        if (stack_t[sp] <= best_t) { node = stack_node[sp]; break; }
+      }
+    }
+  }
+}

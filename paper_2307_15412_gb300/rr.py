@@ -85,6 +85,8 @@ SIGNATURES = {
     "rr_build_bvh": (_I, [_P, _I]),
     "rr_scene_update_vertices": (_I, [_P, _I, _P, ctypes.c_int64, _P, _I]),
     "rr_refit_bvh": (_I, [_P, _I]),
+    "rr_trace_triangles": (_I, [_P, _I, _P, _I, ctypes.c_int64, _P]),
+    "rr_alpha_sweep": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
     "rr_get_hits": (_I, [_P, _I, _I64, _P, _P, _P, _P, _P, _P]),
@@ -292,6 +294,27 @@ class Context:
 
     def refit_bvh(self, scene: int):
         self._check(self.lib.rr_refit_bvh(self.h, scene))
+
+    def trace_triangles(self, scene: int, radar: Radar, samples_per_side: int = 2, hit_capacity: int = 0,
+                        want_count=True):
+        """Rays to k x k sample points of every triangle; returns a
+        one-element list filled with the received-sample count by sync()."""
+        box = [None]
+        cell = _I64(0)
+        rs = make_radar(radar)
+        self._check(self.lib.rr_trace_triangles(self.h, scene, ctypes.byref(rs), int(samples_per_side),
+                                                int(hit_capacity), ctypes.byref(cell) if want_count else None))
+        if want_count:
+            self._pending.append((cell, box))
+        return box
+
+    def alpha_sweep(self, scene: int, radar: Radar, alphas, out, variant: int = SYNTH_FP32):
+        """IF cubes of the last trace for each alpha: out torch CUDA float32
+        [n_alpha, n_rx, M, N, 2]."""
+        arr = np.ascontiguousarray(alphas, np.float32)
+        rs = make_radar(radar)
+        self._check(self.lib.rr_alpha_sweep(self.h, scene, ctypes.byref(rs), int(variant), len(arr),
+                                            arr.ctypes.data, _ptr(out)))
 
     def trace_frame(self, scene: int, radar: Radar, grid: RayGrid, hit_capacity: int = 0, want_count=True):
         """Returns a one-element list filled with the hit count by the next sync()."""
