@@ -29,6 +29,13 @@ back to back, 64 x 64 us apart); every step copies each hand's next pose from de
 with the trees rebuilt, or refit (RR_BATCH_REFIT) from the first frame's
 build.
 
+triangles: the benchmark's full-frame hand (~22k triangles, 1 TX 3 RX,
+64 chirps x 256 samples) with rays cast to each triangle (k x k samples
+per face, k = 1, 2, 4) instead of a grid: one frame = build_bvh,
+trace_triangles, split-BF16x3 synthesis and range-Doppler, timed with CUDA
+events (L2 flushed before each); and the alpha sweep of 11 values against
+11 separate echo + synthesis passes.
+
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -277,9 +284,73 @@ def measure_motion(args):
     ctx.close()
 
 
+def measure_triangles(args):
+    torch, I, rr, ctx = _setup()
+    radar, _, nt = I.workload_full_frame()
+    s = I.hand_scene(8000, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+    ctx.scene_upload(0, s.V, s.F, s.vel)
+    n_tri = int(s.F.shape[0])
+    cube = torch.empty((radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda")
+    rdc = torch.empty_like(cube)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+        return float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+
+    res = {}
+    for k in (1, 2, 4):
+        def frame():
+            ctx.build_bvh(0)
+            ctx.trace_triangles(0, radar, k, want_count=False)
+            ctx.synth_if(0, radar, cube, variant=1)
+            ctx.range_doppler(cube, rdc)
+        ms_frame = timed(frame, args.steps * 4)
+        ctx.build_bvh(0)
+
+        def trace_only():
+            ctx.trace_triangles(0, radar, k, want_count=False)
+        ms_trace = timed(trace_only, args.steps * 4)
+        cnt = ctx.trace_triangles(0, radar, k)
+        ctx.sync()
+        res["k%d" % k] = {"rays": n_tri * k * k, "received": int(cnt[0]), "frames_per_s": 1e3 / ms_frame,
+                          "ms_frame": ms_frame, "ms_trace_triangles": ms_trace,
+                          "rays_per_s": n_tri * k * k / (ms_trace / 1e3)}
+    # alpha sweep on the k = 2 hit list
+    cnt = ctx.trace_triangles(0, radar, 2)
+    ctx.sync()
+    alphas = np.linspace(0.0, 1.0, 11).astype(np.float32)
+    sweep = torch.empty((len(alphas),) + tuple(cube.shape), dtype=torch.float32, device="cuda")
+    ms_sweep = timed(lambda: ctx.alpha_sweep(0, radar, alphas, sweep, variant=1), args.steps * 4)
+
+    def separate():
+        for a in alphas:
+            radar.alpha = float(a)
+            ctx.trace_triangles(0, radar, 2, want_count=False)
+            ctx.synth_if(0, radar, sweep[0], variant=1)
+        radar.alpha = 0.5
+    ms_sep = timed(separate, args.steps)
+    res["alpha_sweep_11"] = {"ms_sweep": ms_sweep, "ms_11_separate_trace_echo_synth": ms_sep}
+    print(json.dumps({"workload": "triangles: full-frame hand (%d triangles), rays to k x k points of every face, "
+                                  "1 TX 3 RX, 64 x 256, BF16x3 synthesis; L2 flushed before each timed call"
+                                  % n_tri, "results": res}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion"])
+    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion", "triangles"])
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--train", type=int, default=200000)
@@ -293,6 +364,8 @@ def main():
         measure_tiny(args)
     elif args.what == "motion":
         measure_motion(args)
+    elif args.what == "triangles":
+        measure_triangles(args)
     else:
         measure_surrogate(args)
 
