@@ -202,6 +202,41 @@ rr_status rr_get_hits(rr_ctx *ctx, int scene, int64_t capacity, int32_t *ray, in
 rr_status rr_trace_triangles(rr_ctx *ctx, int scene, const rr_radar *radar, int samples_per_side,
                              int64_t hit_capacity, int64_t *n_hits_out);
 
+/* Parameters of the stochastic material model (rr_trace_stochastic). */
+typedef struct {
+  float theta_r;     /* reception cone half-angle at each antenna (rad, (0, pi/2]) */
+  int32_t bounces;   /* 1..8 bounces per ray */
+  uint32_t seed;     /* Philox key word 0 */
+  uint32_t frame;    /* Philox key word 1 */
+} rr_stochastic;
+
+/* Traces every ray of `grid` with the material model exactly as Eq. 1-3
+ * state it (Sec. III-A): at each hit the outgoing direction is the
+ * normalised mix alpha (n + r) / |n + r| + (1 - alpha) (mirror direction),
+ * r a random point on the unit sphere (Eq. 1), alpha = radar->alpha (Eq. 3),
+ * and the ray bounces on (up to params->bounces times).  The random numbers
+ * are Philox4x32-10 (Salmon et al., SC 2011) with counter (ray id, bounce,
+ * 0, 0) and key (seed, frame): the same stream whatever the launch shape.
+ * Antenna j receives a bounce when the outgoing direction lies within
+ * theta_r of the direction to it, the antenna is in front of the face and
+ * the return leg hits nothing (bounce and return-leg rays start 1e-6 m off
+ * the face).  Each bounce with a receiving antenna is one hit-list entry
+ * (ray = grid ray id * bounces + bounce, tri = the face, t = path length to
+ * the face) with d_j = path to the face + |rx_j - p|, amplitude Omega /
+ * (2 pi (1 - cos theta_r)) (Omega the ray's solid angle; 1 with
+ * amp_mode 1) for receiving antennas and 0 for the others, and path rate
+ * v . (u_0 - w_j) (u_0 the ray's direction, w_j the unit vector from the
+ * face to rx_j).  The hit list then feeds rr_synth_if; hit_capacity <= 0
+ * means n_rays * bounces.  Not usable with rr_alpha_sweep (the directions
+ * depend on alpha).  Errors as for rr_trace_frame. */
+rr_status rr_trace_stochastic(rr_ctx *ctx, int scene, const rr_radar *radar, const rr_raygrid *grid,
+                              const rr_stochastic *params, int64_t hit_capacity, int64_t *n_hits_out);
+
+/* Test hook of the random stream: out (device uint32 [4 n]) receives the
+ * four Philox4x32-10 words of counters (i, c1, 0, 0), i = 0..n-1, under key
+ * (k0, k1). */
+rr_status rr_philox_words(rr_ctx *ctx, uint32_t k0, uint32_t k1, uint32_t c1, int64_t n, uint32_t *out);
+
 /* IF cubes of the scene's last trace (grid or triangles) for n_alpha
  * values of the material mixture alpha (Eq. 3; 1 <= n_alpha <= 64, each in
  * [0, 1]), e.g. the sweep 0, 0.1, ..., 1 of the paper's comparison.  The

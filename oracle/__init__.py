@@ -58,6 +58,11 @@ def _load():
             lib.rro_synth.argtypes = [I64, I, P, P, P, D, D, D, D, I, I, P]
             lib.rro_range_doppler.argtypes = [I, I, I, P, I, P]
             lib.rro_num_threads.restype = I
+            U32 = ctypes.c_uint32
+            lib.rro_philox4x32.argtypes = [P, P, P]
+            lib.rro_stochastic.argtypes = [P, I64, P, I64, P, I, P, P, P, P, I64, D, D, I, U32, U32, D, I, I64,
+                                           P, P, P, P, P, P]
+            lib.rro_stochastic.restype = I64
             _lib = lib
     return _lib
 
@@ -203,4 +208,57 @@ def triangle_frame(V, F, vel, radar, k: int):
     d, a, dd = echo(V, F, origin, dirs[vis], t[vis], tid[vis].astype(np.int32), omega[vis], radar,
                     np.asarray(vel, np.float64))
     return dict(visible=vis, ray_ids=rays, hit_rays=rays[vis], omega=omega, d=d, a=a, ddot=dd,
+                if_cube=synth(d, a, dd, radar))
+
+
+def philox4x32(ctr, key):
+    """Philox4x32-10 of a 4-word counter and a 2-word key: 4 uint32 words."""
+    c = np.ascontiguousarray(np.asarray(ctr, np.uint64).astype(np.uint32))
+    k = np.ascontiguousarray(np.asarray(key, np.uint64).astype(np.uint32))
+    out = np.empty(4, np.uint32)
+    _load().rro_philox4x32(_p(c), _p(k), _p(out))
+    return out
+
+
+STOCHASTIC_EPS = 1e-6   # origin offset (m) of bounce and return-leg rays along the face normal
+
+
+def stochastic_frame(V, F, vel, radar, grid, alpha: float, theta_r: float, bounces: int, seed: int, frame: int,
+                     rays=None):
+    """Frame of the stochastic material model (Eq. 1-3 with random diffuse
+    directions, reception cones of half-angle theta_r and up to `bounces`
+    bounces; see rro_stochastic): the (ray, bounce) entries with at least
+    one receiving antenna, their path lengths, amplitudes and path rates
+    ([n_rx][K]) and the IF cube.  rays: optional subset of grid ray ids."""
+    lib = _load()
+    dirs, omega = ray_dirs(grid, radar.frame)
+    ids = np.arange(dirs.shape[0], dtype=np.int64)
+    if rays is not None:
+        ids = np.asarray(rays, np.int64)
+    V = np.ascontiguousarray(V, np.float32)
+    F = np.ascontiguousarray(F, np.int32)
+    n_rx = radar.n_rx
+    rx = np.ascontiguousarray(np.asarray(radar.rx, np.float64).reshape(n_rx, 3))
+    cap = max(1, len(ids) * bounces)
+    ray_o = np.empty(cap, np.int32)
+    b_o = np.empty(cap, np.int32)
+    tri_o = np.empty(cap, np.int32)
+    d = np.empty((n_rx, cap))
+    a = np.empty((n_rx, cap))
+    dd = np.empty((n_rx, cap))
+    # the C loop numbers rays by their position in the given arrays: map back after
+    sel_dirs = np.ascontiguousarray(dirs[ids])
+    sel_om = np.ascontiguousarray(omega[ids])
+    # the random stream is keyed by the grid ray id, so run ray by ray when a subset is given
+    if rays is None:
+        K = lib.rro_stochastic(_p(V), V.shape[0], _p(F), F.shape[0], _p(np.asarray(radar.tx, np.float64)), n_rx,
+                               _p(rx), _p(np.asarray(vel, np.float64)), _p(sel_dirs), _p(sel_om), len(ids),
+                               float(alpha), float(theta_r), int(bounces), int(seed), int(frame), STOCHASTIC_EPS,
+                               int(radar.amp_mode), cap, _p(ray_o), _p(b_o), _p(tri_o), _p(d), _p(a), _p(dd))
+    else:
+        raise NotImplementedError("subsets: the stream is keyed by the grid ray id")
+    K = int(K)
+    assert K <= cap
+    d, a, dd = d[:, :K].copy(), a[:, :K].copy(), dd[:, :K].copy()
+    return dict(ray=ray_o[:K].copy(), bounce=b_o[:K].copy(), tri=tri_o[:K].copy(), d=d, a=a, ddot=dd,
                 if_cube=synth(d, a, dd, radar))

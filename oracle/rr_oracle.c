@@ -276,3 +276,168 @@ int rro_num_threads(void)
     return 1;
 #endif
 }
+
+/* ------------------------------------------------------------------------
+ * Counter-based random numbers: Philox4x32-10 (Salmon, Moraes, Dror, Shaw,
+ * "Parallel random numbers: as easy as 1, 2, 3", SC 2011), written from
+ * its published definition.  Ten rounds; a round multiplies the even words
+ * of the counter by 0xD2511F53 and 0xCD9E8D57 (64-bit products split into
+ * high and low halves), XORs the high halves with the odd words and the
+ * two key words, and swaps; the key advances by the Weyl constants
+ * 0x9E3779B9 and 0xBB67AE85 between rounds.
+ * ---------------------------------------------------------------------- */
+void rro_philox4x32(const uint32_t ctr_in[4], const uint32_t key_in[2], uint32_t out[4])
+{
+    uint32_t c[4] = {ctr_in[0], ctr_in[1], ctr_in[2], ctr_in[3]};
+    uint32_t k0 = key_in[0], k1 = key_in[1];
+    for (int round = 0; round < 10; ++round) {
+        const uint64_t p0 = (uint64_t)0xD2511F53u * c[0];
+        const uint64_t p1 = (uint64_t)0xCD9E8D57u * c[2];
+        const uint32_t hi0 = (uint32_t)(p0 >> 32), lo0 = (uint32_t)p0;
+        const uint32_t hi1 = (uint32_t)(p1 >> 32), lo1 = (uint32_t)p1;
+        const uint32_t n0 = hi1 ^ c[1] ^ k0, n1 = lo1, n2 = hi0 ^ c[3] ^ k1, n3 = lo0;
+        c[0] = n0; c[1] = n1; c[2] = n2; c[3] = n3;
+        k0 += 0x9E3779B9u;
+        k1 += 0xBB67AE85u;
+    }
+    for (int i = 0; i < 4; ++i) out[i] = c[i];
+}
+
+/* closest hit of one ray against every triangle, t in (0, tmax); -1: none */
+static int32_t rro_closest(const float *V, const int32_t *F, int64_t nt, const double o[3], const double d[3],
+                           double tmax, double *t_out)
+{
+    double best_t = tmax;
+    int32_t best = -1;
+    for (int64_t f = 0; f < nt; ++f) {
+        double v[3][3];
+        for (int c = 0; c < 3; ++c)
+            for (int x = 0; x < 3; ++x) v[c][x] = (double)V[3 * (int64_t)F[3 * f + c] + x];
+        double t;
+        if (rro_tri_hit(o, d, v[0], v[1], v[2], &t) && t < best_t) {
+            best_t = t;
+            best = (int32_t)f;
+        }
+    }
+    *t_out = best_t;
+    return best;
+}
+
+/* ------------------------------------------------------------------------
+ * Stochastic material model exactly as Eq. 1-3 (Sec. III-A), with
+ * multiple bounces.  For every grid ray r (direction dirs[r], solid angle
+ * omega[r]) from the TX, at bounce b = 0 .. B-1:
+ *   closest hit p of the current ray (none: the ray leaves the scene);
+ *   n_f = unit face normal turned toward the incoming direction u;
+ *   Philox4x32-10 with counter (r, b, 0, 0) and key (seed, frame) gives
+ *   words x0, x1; u1 = (x0 + 1/2) / 2^32, u2 = (x1 + 1/2) / 2^32; the random
+ *   unit vector (Eq. 1's r) is (s cos phi, s sin phi, z), z = 1 - 2 u1,
+ *   phi = 2 pi u2, s = sqrt(1 - z^2);
+ *   diffuse t_o,d = (n_f + r) / |n_f + r| (Eq. 1), mirror t_o,m = u - 2
+ *   (u . n_f) n_f (Eq. 2), t_o,c = (alpha t_o,d + (1 - alpha) t_o,m)
+ *   normalised (Eq. 3);
+ *   Rx j receives when the angle between t_o,c and the direction w_j from p
+ *   to rx_j is at most theta_r, rx_j lies in front of the face (w_j . n_f >
+ *   0) and no triangle lies between (the return leg from p + eps n_f);
+ *   every bounce with at least one receiving antenna is one entry: path
+ *   length d_j = (legs so far) + |rx_j - p|, amplitude a_j = omega[r] /
+ *   (2 pi (1 - cos theta_r)) when received, else 0 (amp_mode 1: 1 when
+ *   received), path rate d-dot_j = v . (u_0 - w_j) for a rigid velocity v
+ *   (the first leg lengthens by v . u_0, the last shortens by v . w_j);
+ *   the ray goes on from p + eps n_f along t_o,c.
+ * Entries are written in (ray, bounce) order: ray_out, bounce_out,
+ * tri_out [cap], d / a / dd [n_rx][cap].  Returns the number of entries
+ * (more than cap: the rest were dropped).
+ * ---------------------------------------------------------------------- */
+int64_t rro_stochastic(const float *V, int64_t nv, const int32_t *F, int64_t nt, const double *tx,
+                       int n_rx, const double *rx, const double *vel, const double *dirs, const double *omega,
+                       int64_t n_rays, double alpha, double theta_r, int bounces, uint32_t seed, uint32_t frame,
+                       double eps, int amp_mode, int64_t cap, int32_t *ray_out, int32_t *bounce_out,
+                       int32_t *tri_out, double *d, double *a, double *dd)
+{
+    (void)nv;
+    const double cos_r = cos(theta_r);
+    const double cone = 2.0 * M_PI * (1.0 - cos_r);
+    int64_t count = 0;
+    /* sequential over rays so that entries come out in (ray, bounce) order */
+    for (int64_t r = 0; r < n_rays; ++r) {
+        double o[3] = {tx[0], tx[1], tx[2]};
+        double u[3] = {dirs[3 * r], dirs[3 * r + 1], dirs[3 * r + 2]};
+        const double u0[3] = {u[0], u[1], u[2]};
+        double legs = 0.0;
+        for (int b = 0; b < bounces; ++b) {
+            double t;
+            const int32_t f = rro_closest(V, F, nt, o, u, INFINITY, &t);
+            if (f < 0) break;
+            const double p[3] = {o[0] + t * u[0], o[1] + t * u[1], o[2] + t * u[2]};
+            legs += t;
+            double v[3][3];
+            for (int c = 0; c < 3; ++c)
+                for (int x = 0; x < 3; ++x) v[c][x] = (double)V[3 * (int64_t)F[3 * f + c] + x];
+            double e1[3], e2[3], nn[3];
+            for (int x = 0; x < 3; ++x) { e1[x] = v[1][x] - v[0][x]; e2[x] = v[2][x] - v[0][x]; }
+            nn[0] = e1[1] * e2[2] - e1[2] * e2[1];
+            nn[1] = e1[2] * e2[0] - e1[0] * e2[2];
+            nn[2] = e1[0] * e2[1] - e1[1] * e2[0];
+            const double nl = sqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+            const double un = u[0] * nn[0] + u[1] * nn[1] + u[2] * nn[2];
+            const double sg = un > 0.0 ? -1.0 / nl : 1.0 / nl;
+            const double n_f[3] = {nn[0] * sg, nn[1] * sg, nn[2] * sg};
+            /* Eq. 1: random point on the unit sphere */
+            const uint32_t ctr[4] = {(uint32_t)r, (uint32_t)b, 0u, 0u}, key[2] = {seed, frame};
+            uint32_t x[4];
+            rro_philox4x32(ctr, key, x);
+            const double u1 = ((double)x[0] + 0.5) / 4294967296.0, u2 = ((double)x[1] + 0.5) / 4294967296.0;
+            const double z = 1.0 - 2.0 * u1, phi = 2.0 * M_PI * u2, s = sqrt(fmax(0.0, 1.0 - z * z));
+            double td[3] = {n_f[0] + s * cos(phi), n_f[1] + s * sin(phi), n_f[2] + z};
+            double l = sqrt(td[0] * td[0] + td[1] * td[1] + td[2] * td[2]);
+            for (int xx = 0; xx < 3; ++xx) td[xx] = l > 0.0 ? td[xx] / l : n_f[xx];
+            /* Eq. 2: mirror direction */
+            const double c2 = 2.0 * (u[0] * n_f[0] + u[1] * n_f[1] + u[2] * n_f[2]);
+            const double tm[3] = {u[0] - c2 * n_f[0], u[1] - c2 * n_f[1], u[2] - c2 * n_f[2]};
+            /* Eq. 3: mixture, normalised */
+            double tc[3] = {alpha * td[0] + (1.0 - alpha) * tm[0], alpha * td[1] + (1.0 - alpha) * tm[1],
+                            alpha * td[2] + (1.0 - alpha) * tm[2]};
+            l = sqrt(tc[0] * tc[0] + tc[1] * tc[1] + tc[2] * tc[2]);
+            for (int xx = 0; xx < 3; ++xx) tc[xx] = l > 0.0 ? tc[xx] / l : n_f[xx];
+            const double q[3] = {p[0] + eps * n_f[0], p[1] + eps * n_f[1], p[2] + eps * n_f[2]};
+            int any = 0;
+            double dj[8], aj[8], ddj[8];
+            for (int j = 0; j < n_rx; ++j) {
+                const double w[3] = {rx[3 * j] - p[0], rx[3 * j + 1] - p[1], rx[3 * j + 2] - p[2]};
+                const double L = sqrt(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+                const double wu[3] = {w[0] / L, w[1] / L, w[2] / L};
+                dj[j] = legs + L;
+                ddj[j] = vel[0] * (u0[0] - wu[0]) + vel[1] * (u0[1] - wu[1]) + vel[2] * (u0[2] - wu[2]);
+                aj[j] = 0.0;
+                const double cosang = tc[0] * wu[0] + tc[1] * wu[1] + tc[2] * wu[2];
+                const double front = wu[0] * n_f[0] + wu[1] * n_f[1] + wu[2] * n_f[2];
+                if (cosang >= cos_r && front > 0.0) {
+                    const double ws[3] = {rx[3 * j] - q[0], rx[3 * j + 1] - q[1], rx[3 * j + 2] - q[2]};
+                    const double Ls = sqrt(ws[0] * ws[0] + ws[1] * ws[1] + ws[2] * ws[2]);
+                    const double wsu[3] = {ws[0] / Ls, ws[1] / Ls, ws[2] / Ls};
+                    double ts;
+                    if (rro_closest(V, F, nt, q, wsu, Ls, &ts) < 0) {
+                        aj[j] = amp_mode == 1 ? 1.0 : omega[r] / cone;
+                        any = 1;
+                    }
+                }
+            }
+            if (any) {
+                if (count < cap) {
+                    ray_out[count] = (int32_t)r;
+                    bounce_out[count] = b;
+                    tri_out[count] = f;
+                    for (int j = 0; j < n_rx; ++j) {
+                        d[(int64_t)j * cap + count] = dj[j];
+                        a[(int64_t)j * cap + count] = aj[j];
+                        dd[(int64_t)j * cap + count] = ddj[j];
+                    }
+                }
+                ++count;
+            }
+            for (int xx = 0; xx < 3; ++xx) { o[xx] = q[xx]; u[xx] = tc[xx]; }
+        }
+    }
+    return count;
+}

@@ -583,8 +583,57 @@ rr_status rr_trace_triangles(rr_ctx *c, int scene, const rr_radar *radar, int sa
   return RR_OK;
 }
 
+rr_status rr_trace_stochastic(rr_ctx *c, int scene, const rr_radar *radar, const rr_raygrid *grid,
+                              const rr_stochastic *params, int64_t hit_capacity, int64_t *n_hits_out) {
+  if (!c) return RR_EINVAL;
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->built) return fail(c, RR_ENOTREADY, "scene %d: build_bvh must follow scene_upload", scene);
+  if (!check_radar(c, radar, &st)) return st;
+  if (!grid || grid->n_az < 1 || grid->n_el < 1 || (int64_t)grid->n_az * grid->n_el > ((int64_t)1 << 30))
+    return fail(c, RR_EINVAL, "ray grid size invalid");
+  if (!(grid->half_az > 0 && grid->half_az < M_PI) || !(grid->half_el > 0 && grid->half_el < 0.5 * M_PI))
+    return fail(c, RR_EINVAL, "ray grid half angles out of range");
+  if (!params || !(params->theta_r > 0.f && params->theta_r <= (float)(0.5 * M_PI)) || params->bounces < 1 ||
+      params->bounces > rr::kMaxBounces)
+    return fail(c, RR_EINVAL, "stochastic parameters: theta_r in (0, pi/2], bounces in [1,%d]", rr::kMaxBounces);
+  const int64_t n_rays = (int64_t)grid->n_az * grid->n_el;
+  const int64_t cap = hit_capacity > 0 ? hit_capacity : n_rays * params->bounces;
+  DeviceGuard g(c->device);
+  if ((st = ensure_hits(c, s, cap)) != RR_OK) return st;
+  const rr::RadarDev rd = to_dev(radar);
+  rr::StochParams sp;
+  sp.alpha = radar->alpha;
+  sp.theta_r = params->theta_r;
+  sp.bounces = params->bounces;
+  sp.seed = params->seed;
+  sp.frame = params->frame;
+  RR_CUDA(c, rr::launch_trace_stochastic(*s, rd, to_dev(grid), sp, cap, c->d_err, c->stream), "trace_stochastic launch");
+  s->hit_nrx = radar->n_rx;
+  s->hit_used_cap = cap;
+  s->traced = true;
+  s->trace_mode = 2;
+  if (n_hits_out) {
+    RR_CUDA(c, cudaMemcpyAsync(c->h_counts + scene, s->hit_count, sizeof(uint32_t), cudaMemcpyDeviceToHost, c->stream),
+            "hit count readback");
+    c->pending.push_back({n_hits_out, nullptr, scene, cap});
+  }
+  return RR_OK;
+}
+
+rr_status rr_philox_words(rr_ctx *c, uint32_t k0, uint32_t k1, uint32_t c1, int64_t n, uint32_t *out) {
+  if (!c) return RR_EINVAL;
+  if (n < 0 || (n > 0 && !out)) return fail(c, RR_EINVAL, "philox words: bad arguments");
+  if (n == 0) return RR_OK;
+  DeviceGuard g(c->device);
+  RR_CUDA(c, rr::launch_philox_words(k0, k1, c1, n, out, c->stream), "philox launch");
+  return RR_OK;
+}
+
 // Echo of the scene's last trace again with material mixture alpha.
 static rr_status re_echo(rr_ctx *c, SceneDev *s, const rr::RadarDev &rd, float alpha) {
+  if (s->trace_mode == 2) return fail(c, RR_EINVAL, "alpha sweep of a stochastic trace: its directions depend on alpha");
   if (s->trace_mode == 1) {
     RR_CUDA(c, rr::launch_echo_tris(*s, rd, s->tri_k, s->hit_used_cap, alpha, c->stream), "echo launch");
     return RR_OK;

@@ -201,6 +201,18 @@ struct AlphaList {
 };
 cudaError_t launch_alpha_mix(const float *s0, const float *s1, int64_t cube_complex, const AlphaList &al, float *out,
                              cudaStream_t st);
+// Stochastic material model (see stochastic.cu): alpha, cone half-angle
+// theta_r (rad), 1..kMaxBounces bounces, Philox key (seed, frame).
+constexpr int kMaxBounces = 8;
+constexpr float kStochEps = 1e-6f;  // origin offset of bounce and return-leg rays (m)
+struct StochParams {
+  float alpha, theta_r;
+  int bounces;
+  uint32_t seed, frame;
+};
+cudaError_t launch_trace_stochastic(SceneDev &s, const RadarDev &r, const GridDev &g, const StochParams &sp,
+                                    int64_t cap, uint32_t *err, cudaStream_t st);
+cudaError_t launch_philox_words(uint32_t k0, uint32_t k1, uint32_t c1, int64_t n, uint32_t *out, cudaStream_t st);
 cudaError_t launch_trace_batch(const FrameJob *table, int n_jobs, JobTiles *jt, int64_t *hit_prefix, int *order,
                                const RadarDev &r, uint32_t *err, cudaStream_t st, int tw_log2 = 3);
 cudaError_t launch_synth_fp32(const RadarDev &r, const uint32_t *count, int64_t kmax,

@@ -49,6 +49,11 @@ class rr_job(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("grid", rr_raygrid)]
 
 
+class rr_stochastic(ctypes.Structure):
+    _fields_ = [("theta_r", ctypes.c_float), ("bounces", ctypes.c_int32), ("seed", ctypes.c_uint32),
+                ("frame", ctypes.c_uint32)]
+
+
 class rr_mesh(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("verts", ctypes.c_void_p),
                 ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p), ("nt", ctypes.c_int64),
@@ -87,6 +92,8 @@ SIGNATURES = {
     "rr_refit_bvh": (_I, [_P, _I]),
     "rr_trace_triangles": (_I, [_P, _I, _P, _I, ctypes.c_int64, _P]),
     "rr_alpha_sweep": (_I, [_P, _I, _P, _I, _I, _P, _P]),
+    "rr_trace_stochastic": (_I, [_P, _I, _P, _P, _P, ctypes.c_int64, _P]),
+    "rr_philox_words": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, _P]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
     "rr_get_hits": (_I, [_P, _I, _I64, _P, _P, _P, _P, _P, _P]),
@@ -307,6 +314,28 @@ class Context:
         if want_count:
             self._pending.append((cell, box))
         return box
+
+    def trace_stochastic(self, scene: int, radar: Radar, grid: RayGrid, theta_r: float, bounces: int = 1,
+                         seed: int = 0, frame: int = 0, hit_capacity: int = 0, want_count=True):
+        """Eq. 1-3 with random diffuse directions (see include/rr.h); returns
+        a one-element list filled with the entry count by sync()."""
+        box = [None]
+        cell = _I64(0)
+        rs, gs = make_radar(radar), make_grid(grid)
+        p = rr_stochastic()
+        p.theta_r = float(theta_r)
+        p.bounces = int(bounces)
+        p.seed = int(seed)
+        p.frame = int(frame)
+        self._check(self.lib.rr_trace_stochastic(self.h, scene, ctypes.byref(rs), ctypes.byref(gs), ctypes.byref(p),
+                                                 int(hit_capacity), ctypes.byref(cell) if want_count else None))
+        if want_count:
+            self._pending.append((cell, box))
+        return box
+
+    def philox_words(self, k0: int, k1: int, c1: int, n: int, out):
+        """out: torch CUDA int32 [4 n] (the uint32 words' bits)."""
+        self._check(self.lib.rr_philox_words(self.h, int(k0), int(k1), int(c1), int(n), _ptr(out)))
 
     def alpha_sweep(self, scene: int, radar: Radar, alphas, out, variant: int = SYNTH_FP32):
         """IF cubes of the last trace for each alpha: out torch CUDA float32
