@@ -36,6 +36,12 @@ trace_triangles, split-BF16x3 synthesis and range-Doppler, timed with CUDA
 events (L2 flushed before each); and the alpha sweep of 11 values against
 11 separate echo + synthesis passes.
 
+stochastic: the benchmark's full-frame hand and 512 x 512 ray grid with
+the stochastic material model (random diffuse directions, reception cones
+of 10 deg, 1 / 2 / 3 bounces, alpha = 0.5): one frame = build_bvh,
+trace_stochastic, split-BF16x3 synthesis and range-Doppler, timed with CUDA
+events (L2 flushed before each), and the stochastic trace alone (rays/s).
+
 Each prints one JSON line.
 """
 from __future__ import annotations
@@ -348,9 +354,54 @@ def measure_triangles(args):
     ctx.close()
 
 
+def measure_stochastic(args):
+    torch, I, rr, ctx = _setup()
+    radar, grid, nt = I.workload_full_frame()
+    s = I.hand_scene(8100, nt, range_m=I.FULL_FRAME_RANGE, speed=I.FULL_FRAME_SPEED)
+    ctx.scene_upload(0, s.V, s.F, s.vel)
+    ctx.build_bvh(0)
+    cube = torch.empty((radar.n_rx, radar.n_chirps, radar.n_samples, 2), dtype=torch.float32, device="cuda")
+    rdc = torch.empty_like(cube)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+    th = math.radians(10.0)
+
+    def timed(fn, reps):
+        for _ in range(3):
+            fn()
+        ctx.sync()
+        ev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(reps)]
+        for e0, e1 in ev:
+            flush.zero_()
+            e0.record(stream)
+            fn()
+            e1.record(stream)
+        ctx.sync()
+        torch.cuda.synchronize()
+        return float(np.mean([e0.elapsed_time(e1) for e0, e1 in ev]))
+
+    res = {}
+    for B in (1, 2, 3):
+        def frame():
+            ctx.build_bvh(0)
+            ctx.trace_stochastic(0, radar, grid, th, B, 1, 0, want_count=False)
+            ctx.synth_if(0, radar, cube, variant=1)
+            ctx.range_doppler(cube, rdc)
+        ms_frame = timed(frame, args.steps * 4)
+        ms_trace = timed(lambda: ctx.trace_stochastic(0, radar, grid, th, B, 1, 0, want_count=False), args.steps * 4)
+        cnt = ctx.trace_stochastic(0, radar, grid, th, B, 1, 0)
+        ctx.sync()
+        res["bounces%d" % B] = {"entries": int(cnt[0]), "frames_per_s": 1e3 / ms_frame, "ms_frame": ms_frame,
+                                "ms_trace": ms_trace, "rays_per_s": grid.n_rays / (ms_trace / 1e3)}
+    print(json.dumps({"workload": "stochastic: full-frame hand (%d triangles), 512^2 rays over +-45 deg, alpha 0.5, "
+                                  "reception cones of 10 deg, 1 TX 3 RX, 64 x 256, BF16x3; L2 flushed before each "
+                                  "timed call" % int(s.F.shape[0]), "results": res}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion", "triangles"])
+    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion", "triangles", "stochastic"])
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--train", type=int, default=200000)
@@ -366,6 +417,8 @@ def main():
         measure_motion(args)
     elif args.what == "triangles":
         measure_triangles(args)
+    elif args.what == "stochastic":
+        measure_stochastic(args)
     else:
         measure_surrogate(args)
 
