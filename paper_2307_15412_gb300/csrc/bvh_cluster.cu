@@ -18,6 +18,7 @@
 //     atomics instead of device-wide ones; the final nodes go to global
 //     memory as they are completed.
 // Meshes too large for one cluster use the three-kernel path of bvh.cu.
+#include <cstring>
 #include <cooperative_groups.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
@@ -604,6 +605,7 @@ int cluster_size_for(int n, bool batch) {
 
 BuildJob build_job_for(const SceneDev &s, int C) {
   BuildJob j;
+  memset(&j, 0, sizeof(j));  // whole table entries (padding included) are hashed into the batch graph key
   j.V = s.V;
   j.F = s.F;
   j.nodes = s.nodes;

@@ -23,6 +23,7 @@
 //          Sec. III-B path length): d_j = t + |p - rx_j|, a_j = Omega g_j /
 //          (t r_j), d-dot_j = v . (u + u_j).  FP64 is slow on this part, so
 //          it is kept to the plane intersection.
+#include <cstring>
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -418,6 +419,7 @@ int sm_count() {
 
 FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap) {
   FrameJob j;
+  memset(&j, 0, sizeof(j));  // whole table entries (padding included) are hashed into the batch graph key
   j.nodes = s.nodes;
   j.tris = s.tris;
   j.hdr = s.hdr;
