@@ -516,3 +516,59 @@ def surrogate_init_params(dims, seed: int) -> np.ndarray:
         parts.append(rng.uniform(-bound, bound, size=n_out * n_in))
         parts.append(np.zeros(n_out))
     return np.concatenate(parts).astype(np.float32)
+
+
+# --------------------------------------------------------------------------
+# Imaging workload (Sec. II and IV): square MIMO array, SFCW steps, volume
+# --------------------------------------------------------------------------
+
+IMAGING_F0 = 72e9            # first SFCW carrier (Hz)
+IMAGING_DF = 10e9 / 128      # step: 10 GHz over 128 steps, the last below 82 GHz
+IMAGING_NF = 128
+IMAGING_RANGE = 0.315        # hand centre on the array's boresight (m)
+
+
+def mimo_square_array(n_per_side: int = 47, pitch: float = 3e-3, z: float = 0.0):
+    """Synthetic stand-in for the 94 TX / 94 RX square array (exact positions
+    are not published): a square of side n_per_side * pitch (14.1 cm at 47 x
+    3 mm), TX along its top and bottom edges, RX along its left and right
+    edges, pitch apart, centred on the boresight in the plane z.  Returns
+    (tx [2 n][3], rx [2 n][3]) float64."""
+    half = 0.5 * n_per_side * pitch
+    along = -half + pitch * (np.arange(n_per_side) + 0.5)
+    zeros = np.zeros(n_per_side)
+    tx = np.concatenate([np.stack([along, zeros + half, zeros + z], 1),
+                         np.stack([along, zeros - half, zeros + z], 1)])
+    rx = np.concatenate([np.stack([zeros - half, along, zeros + z], 1),
+                         np.stack([zeros + half, along, zeros + z], 1)])
+    return tx, rx
+
+
+@dataclasses.dataclass
+class Volume:
+    """Voxel grid: centre of voxel (ix, iy, iz) = (x0 + ix dx, y0 + iy dy, z0 + iz dz)."""
+
+    x0: float
+    y0: float
+    z0: float
+    dx: float
+    dy: float
+    dz: float
+    nx: int
+    ny: int
+    nz: int
+
+    @property
+    def n(self) -> int:
+        return self.nx * self.ny * self.nz
+
+
+def imaging_volume() -> Volume:
+    """x, y in [-10, 10] cm and z in [26, 34] cm at 1 mm: 201 x 201 x 81 voxels."""
+    return Volume(-0.10, -0.10, 0.26, 1e-3, 1e-3, 1e-3, 201, 201, 81)
+
+
+def workload_imaging() -> Tuple[RayGrid, int]:
+    """Ray grid of each TX (512 x 512 over +-20 deg, covering a hand at
+    0.315 m) and the hand's triangle count (~20k)."""
+    return RayGrid(512, 512, math.radians(20.0), math.radians(20.0)), 20000
