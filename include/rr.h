@@ -288,6 +288,68 @@ rr_status rr_range_doppler(rr_ctx *ctx, const float *if_in, int n_rx, int n_chir
  * surrogate represents a frame.  A cell with r = 0 is copied unchanged. */
 rr_status rr_phase_reference(rr_ctx *ctx, const float *in, int64_t n_frames, int n_rx, int64_t cells, float *out);
 
+/* ---- imaging workload (Sec. II and IV) ---------------------------------- */
+
+/* SFCW sweep of the imaging radar (Sec. II): CW step n = 0..n_f-1 at the
+ * carrier f0 + n df; the material model of rr_radar. */
+typedef struct {
+  double f0;          /* first carrier (Hz), > 0 */
+  double df;          /* frequency step (Hz), >= 0 */
+  int32_t n_f;        /* steps, 1..4096 */
+  int32_t amp_mode;   /* 0: material-lobe amplitude; 1: unit amplitude per hit (Eq. 4 as printed) */
+  double alpha;       /* Eq. 3 mixture weight, 0 specular .. 1 diffuse */
+  double spec_exp;    /* exponent of the specular lobe, > 0 */
+  double frame[9];    /* array -> world rotation of every TX's ray grid, row-major */
+} rr_sfcw;
+
+/* Baseband of every TX-RX pair of a MIMO array (Sec. II; Eq. 4 with the
+ * carrier of each CW step): each TX shoots the ray grid from its own
+ * position (Sec. III-A), and every hit's echo reaches every RX with the
+ * path d = t + |p - rx_j| and the amplitude of rr_trace_frame (Sec. III-A
+ * material model, Sec. III-B):
+ *   s[t][j][n] = sum over hits of a exp(-j 2 pi (f0 + n df) d / c).
+ * tx_pos [n_tx][3], rx_pos [n_rx][3]: host arrays, world metres, n_tx and
+ * n_rx in 1..4096.  s_out: device float32 [n_tx][n_rx][n_f][2] (re, im).
+ * Hits are summed in the order the trace appends them, which may differ
+ * between runs (results then differ by FP32 rounding).
+ * The scene needs a build (rr_build_bvh); its hit list holds the last TX's
+ * hits afterwards, without echo rows (rr_synth_if then reports
+ * RR_ENOTREADY).  Errors: RR_EINVAL (null pointer, sizes, sweep, grid),
+ * RR_ENOTREADY (no BVH), RR_ENOMEM, RR_ECUDA; device faults latch into
+ * rr_sync. */
+rr_status rr_mimo_sfcw(rr_ctx *ctx, int scene, const rr_sfcw *sweep, const rr_raygrid *grid, const double *tx_pos,
+                       int n_tx, const double *rx_pos, int n_rx, float *s_out);
+
+/* Voxel volume: voxel (ix, iy, iz) has its centre at (x0 + ix dx, y0 + iy dy,
+ * z0 + iz dz); volumes are stored [nz][ny][nx] (x fastest). */
+typedef struct {
+  double x0, y0, z0;    /* centre of voxel (0, 0, 0), world metres */
+  double dx, dy, dz;    /* voxel pitch (m) */
+  int32_t nx, ny, nz;   /* >= 1 each, nx * ny * nz < 2^31 */
+  int32_t reserved;     /* 0 */
+} rr_volume;
+
+/* Brute-force SFCW back-projection (Sec. IV-A) of the pairs' baseband:
+ *   img(v) = sum over t, j, n of s[t][j][n] exp(+j 2 pi (f0 + n df) R / c),
+ *   R = |v - tx_t| + |v - rx_j|,
+ * at every voxel centre v.  s: device float32 [n_tx][n_rx][n_f][2];
+ * tx_pos, rx_pos: host double [n][3] (n_tx + n_rx <= 8192); img: device
+ * float32 [nz][ny][nx][2].  FP32 arithmetic: Horner's rule over the steps,
+ * phases reduced to cycles with the product's rounding error recovered.
+ * Errors: RR_EINVAL, RR_ENOMEM, RR_ECUDA. */
+rr_status rr_backproject(rr_ctx *ctx, const float *s, const double *tx_pos, int n_tx, const double *rx_pos, int n_rx,
+                         double f0, double df, int n_f, const rr_volume *vol, float *img);
+
+/* Maximum projection of a volume (Sec. IV-A, IV-B): per (y, x) the largest
+ * |img| over z, in dB relative to the volume's largest amplitude and
+ * floored at -dyn_range_db (an all-zero volume gives the floor); z_out,
+ * if not NULL, receives the z index of that maximum (the lowest on ties).
+ * img: device float32 [nz][ny][nx][2]; db_out: device float32 [ny][nx];
+ * z_out: device int32 [ny][nx] or NULL.  Errors: RR_EINVAL, RR_ENOMEM,
+ * RR_ECUDA. */
+rr_status rr_max_projection(rr_ctx *ctx, const float *img, const rr_volume *vol, double dyn_range_db, float *db_out,
+                            int32_t *z_out);
+
 /* ---- whole frame --------------------------------------------------------- */
 
 /* One frame of the hot path on a scene already uploaded: build_bvh,

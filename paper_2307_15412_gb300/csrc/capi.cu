@@ -41,6 +41,18 @@ struct rr_ctx {
   int64_t if_tmp_cap = 0;          // floats
   double2 *dir = nullptr;          // FP64 ray-direction table of the last single-frame trace
   int64_t dir_cap = 0;
+  // imaging (rr_mimo_sfcw, rr_backproject, rr_max_projection)
+  double *img_rx = nullptr;        // RX positions [n_rx][3]
+  int64_t img_rx_cap = 0;
+  unsigned char *img_geom = nullptr;  // per-hit geometry records of one TX
+  int64_t img_geom_cap = 0;
+  float *img_part = nullptr;       // per-split partial sums of one TX
+  int64_t img_part_cap = 0;
+  float4 *img_pos = nullptr;       // back-projection positions: TX then RX
+  int64_t img_pos_cap = 0;
+  float *img_amp = nullptr;        // maximum-projection amplitudes
+  int64_t img_amp_cap = 0;
+  uint32_t *img_gmax = nullptr;    // the volume's maximum (float bits)
   // batches (rr_batch_run): hit-list segments, tables and scratch
   struct Batch {
     int32_t *ray = nullptr, *tri = nullptr, *pos = nullptr;
@@ -273,6 +285,11 @@ rr_status rr_destroy(rr_ctx *c) {
   if (c->if_tmp) cudaFree(c->if_tmp);
   if (c->tc_cst) cudaFree(c->tc_cst);
   if (c->dir) cudaFree(c->dir);
+  {
+    void *dev[] = {c->img_rx, c->img_geom, c->img_part, c->img_pos, c->img_amp, c->img_gmax};
+    for (void *p : dev)
+      if (p) cudaFree(p);
+  }
   for (cudaEvent_t e : c->tev) cudaEventDestroy(e);
   {
     auto &b = c->batch;
@@ -714,6 +731,132 @@ rr_status rr_batch_plan(const rr_ctx *c, int *ray_tile_log2, int *split, int *cl
   if (split) *split = b.last_split;
   if (cluster_ctas) *cluster_ctas = b.last_c;
   if (kernel_launches) *kernel_launches = b.last_launches;
+  return RR_OK;
+}
+
+static bool check_volume(rr_ctx *c, const rr_volume *vol) {
+  if (!vol || vol->nx < 1 || vol->ny < 1 || vol->nz < 1 ||
+      (int64_t)vol->nx * vol->ny * vol->nz > (int64_t)INT32_MAX) {
+    fail(c, RR_EINVAL, "volume sizes invalid");
+    return false;
+  }
+  const double f[6] = {vol->x0, vol->y0, vol->z0, vol->dx, vol->dy, vol->dz};
+  for (double x : f)
+    if (!isfinite(x)) {
+      fail(c, RR_EINVAL, "volume origin and pitch must be finite");
+      return false;
+    }
+  return true;
+}
+
+static bool finite_positions(const double *p, int n) {
+  for (int i = 0; i < 3 * n; ++i)
+    if (!isfinite(p[i])) return false;
+  return true;
+}
+
+static rr::VolumeDev volume_dev(const rr_volume *v) {
+  rr::VolumeDev d;
+  d.x0 = (float)v->x0; d.y0 = (float)v->y0; d.z0 = (float)v->z0;
+  d.dx = (float)v->dx; d.dy = (float)v->dy; d.dz = (float)v->dz;
+  d.nx = v->nx; d.ny = v->ny; d.nz = v->nz;
+  return d;
+}
+
+rr_status rr_mimo_sfcw(rr_ctx *c, int scene, const rr_sfcw *sw, const rr_raygrid *grid, const double *tx_pos,
+                       int n_tx, const double *rx_pos, int n_rx, float *s_out) {
+  if (!c) return RR_EINVAL;
+  if (!sw || !grid || !tx_pos || !rx_pos || !s_out) return fail(c, RR_EINVAL, "mimo_sfcw: null argument");
+  if (n_tx < 1 || n_tx > 4096 || n_rx < 1 || n_rx > 4096) return fail(c, RR_EINVAL, "n_tx, n_rx must be in 1..4096");
+  if (sw->n_f < 1 || sw->n_f > 4096 || !(sw->f0 > 0) || !isfinite(sw->f0) || !(sw->df >= 0) || !isfinite(sw->df))
+    return fail(c, RR_EINVAL, "sweep: f0 > 0, df >= 0 finite, n_f in 1..4096");
+  if (sw->amp_mode != 0 && sw->amp_mode != 1) return fail(c, RR_EINVAL, "sweep amp_mode must be 0 or 1");
+  if (!(sw->alpha >= 0 && sw->alpha <= 1) || !(sw->spec_exp > 0) || !isfinite(sw->spec_exp))
+    return fail(c, RR_EINVAL, "sweep: alpha in [0, 1], spec_exp > 0");
+  if (!finite_positions(tx_pos, n_tx) || !finite_positions(rx_pos, n_rx))
+    return fail(c, RR_EINVAL, "antenna positions must be finite");
+  SceneDev *s;
+  rr_status st = get_scene(c, scene, &s);
+  if (st != RR_OK) return st;
+  if (!s->built) return fail(c, RR_ENOTREADY, "scene %d: build_bvh must follow scene_upload", scene);
+  if (grid->n_az < 1 || grid->n_el < 1 || (int64_t)grid->n_az * grid->n_el > ((int64_t)1 << 30))
+    return fail(c, RR_EINVAL, "ray grid size invalid");
+  if (!(grid->half_az > 0 && grid->half_az < M_PI) || !(grid->half_el > 0 && grid->half_el < 0.5 * M_PI))
+    return fail(c, RR_EINVAL, "ray grid half angles out of range");
+  const int64_t cap = (int64_t)grid->n_az * grid->n_el;
+  const int n_f = sw->n_f;
+  DeviceGuard g(c->device);
+  if ((st = ensure_hits(c, s, cap)) != RR_OK) return st;
+  RR_CUDA(c, grow(c->dir, c->dir_cap, (int64_t)grid->n_az + grid->n_el), "ray-direction table");
+  RR_CUDA(c, grow(c->img_rx, c->img_rx_cap, 3 * (int64_t)n_rx), "RX positions");
+  RR_CUDA(c, grow(c->img_geom, c->img_geom_cap, cap * rr::kMimoGeomBytes), "hit geometry");
+  RR_CUDA(c, grow(c->img_part, c->img_part_cap, (int64_t)rr::mimo_sfcw_splits(n_rx, n_f) * n_rx * n_f * 2),
+          "partial sums");
+  RR_CUDA(c, cudaMemcpyAsync(c->img_rx, rx_pos, sizeof(double) * 3 * n_rx, cudaMemcpyHostToDevice, c->stream),
+          "RX positions");
+  // one TX at a time: a one-sample radar at that TX carrying the material model
+  rr_radar rad;
+  memset(&rad, 0, sizeof(rad));
+  memcpy(rad.frame, sw->frame, sizeof(rad.frame));
+  rad.n_rx = 1;
+  rad.n_samples = n_f;
+  rad.n_chirps = 1;
+  rad.amp_mode = sw->amp_mode;
+  rad.f0 = sw->f0;
+  rad.bandwidth = sw->df * n_f;
+  rad.t_chirp = 1.0;
+  rad.t_rep = 1.0;
+  rad.alpha = sw->alpha;
+  rad.spec_exp = sw->spec_exp;
+  const rr::GridDev gd = to_dev(grid);
+  for (int t = 0; t < n_tx; ++t) {
+    for (int k = 0; k < 3; ++k) rad.tx[k] = tx_pos[3 * t + k];
+    const rr::RadarDev rd = to_dev(&rad);
+    RR_CUDA(c, rr::launch_trace_hits(*s, rd, gd, cap, c->dir, c->d_err, c->stream), "mimo trace launch");
+    RR_CUDA(c, rr::launch_mimo_sfcw(*s, rd, gd, cap, c->dir, c->img_rx, n_rx, sw->f0, sw->df, n_f, c->img_geom,
+                                    c->img_part, s_out + (int64_t)t * n_rx * n_f * 2, c->stream),
+            "mimo synthesis launch");
+  }
+  s->traced = false;
+  return RR_OK;
+}
+
+rr_status rr_backproject(rr_ctx *c, const float *s, const double *tx_pos, int n_tx, const double *rx_pos, int n_rx,
+                         double f0, double df, int n_f, const rr_volume *vol, float *img) {
+  if (!c) return RR_EINVAL;
+  if (!s || !tx_pos || !rx_pos || !img) return fail(c, RR_EINVAL, "backproject: null argument");
+  if (n_tx < 1 || n_rx < 1 || n_tx + n_rx > 8192) return fail(c, RR_EINVAL, "n_tx, n_rx >= 1, n_tx + n_rx <= 8192");
+  if (n_f < 1 || n_f > 4096 || !(f0 > 0) || !isfinite(f0) || !(df >= 0) || !isfinite(df))
+    return fail(c, RR_EINVAL, "f0 > 0, df >= 0 finite, n_f in 1..4096");
+  if (!check_volume(c, vol)) return RR_EINVAL;
+  if (!finite_positions(tx_pos, n_tx) || !finite_positions(rx_pos, n_rx))
+    return fail(c, RR_EINVAL, "antenna positions must be finite");
+  DeviceGuard g(c->device);
+  std::vector<float4> pos((size_t)(n_tx + n_rx));
+  for (int i = 0; i < n_tx + n_rx; ++i) {
+    const double *p = i < n_tx ? tx_pos + 3 * i : rx_pos + 3 * (i - n_tx);
+    pos[i] = make_float4((float)p[0], (float)p[1], (float)p[2], 0.f);
+  }
+  RR_CUDA(c, grow(c->img_pos, c->img_pos_cap, (int64_t)pos.size()), "antenna positions");
+  RR_CUDA(c, cudaMemcpyAsync(c->img_pos, pos.data(), sizeof(float4) * pos.size(), cudaMemcpyHostToDevice, c->stream),
+          "antenna positions");
+  RR_CUDA(c, rr::launch_backproject(s, c->img_pos, n_tx, n_rx, f0, df, n_f, volume_dev(vol), img, c->stream),
+          "backproject launch");
+  return RR_OK;
+}
+
+rr_status rr_max_projection(rr_ctx *c, const float *img, const rr_volume *vol, double dyn_range_db, float *db_out,
+                            int32_t *z_out) {
+  if (!c) return RR_EINVAL;
+  if (!img || !db_out) return fail(c, RR_EINVAL, "max_projection: null argument");
+  if (!(dyn_range_db >= 0) || !isfinite(dyn_range_db)) return fail(c, RR_EINVAL, "dyn_range_db must be >= 0");
+  if (!check_volume(c, vol)) return RR_EINVAL;
+  DeviceGuard g(c->device);
+  RR_CUDA(c, grow(c->img_amp, c->img_amp_cap, (int64_t)vol->nx * vol->ny), "projection amplitudes");
+  if (!c->img_gmax) RR_CUDA(c, cudaMalloc((void **)&c->img_gmax, sizeof(uint32_t)), "projection maximum");
+  RR_CUDA(c, rr::launch_max_projection(img, volume_dev(vol), (float)dyn_range_db, db_out, z_out, c->img_amp,
+                                       c->img_gmax, c->stream),
+          "max_projection launch");
   return RR_OK;
 }
 

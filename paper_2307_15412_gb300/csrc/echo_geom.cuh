@@ -1,0 +1,82 @@
+// echo_geom.cuh -- the echo of one hit (Sec. III-A material model, Eq. 1-3
+// as expected lobes; Sec. III-B path length), shared by the ray-grid echo
+// (trace.cu) and the MIMO imaging synthesis (imaging.cu) so that both use
+// the same arithmetic.  Included inside namespace rr { namespace { ... } }.
+
+// Geometry of a hit: exact point, distance, unit face normal turned toward
+// the ray, the ray's mirror direction (Eq. 2), cos of incidence and the
+// ray's solid angle.
+struct EchoGeom {
+  double p[3];
+  double t;
+  float nf[3];
+  float uf[3];
+  float mr[3];
+  float ci;
+  float omega;
+};
+
+// Hit hl of frame J (ray grid of J.g, directions from the FP64 table J.dir)
+// seen from r.tx: the distance is recomputed in FP64 from the triangle's
+// plane and the exact ray direction (FP32 traversal decides *which*
+// triangle, FP64 fixes *where*); a degenerate plane keeps the traversal
+// distance.  Writes the refined distance back to J.hit_t.
+__device__ __forceinline__ EchoGeom echo_geometry(const FrameJob &J, const RadarDev &r, int64_t hl) {
+  EchoGeom G;
+  const int ray = J.hit_ray[hl];
+  const int pos = J.hit_pos[hl];
+  const int i_el = ray / J.g.n_az, i_az = ray - i_el * J.g.n_az;
+  const double2 scA = J.dir[i_az], scE = J.dir[J.g.n_az + i_el];
+  const double sa = scA.x, ca = scA.y, se = scE.x, ce = scE.y;
+  const double ur[3] = {ce * sa, se, ce * ca};
+  double u[3];
+#pragma unroll
+  for (int k = 0; k < 3; ++k) u[k] = r.R[3 * k] * ur[0] + r.R[3 * k + 1] * ur[1] + r.R[3 * k + 2] * ur[2];
+  const float4 fa = __ldg(J.tris + 3 * pos), fb = __ldg(J.tris + 3 * pos + 1), fc = __ldg(J.tris + 3 * pos + 2);
+  const double v0[3] = {fa.x, fa.y, fa.z};
+  const double e1[3] = {(double)fb.x - v0[0], (double)fb.y - v0[1], (double)fb.z - v0[2]};
+  const double e2[3] = {(double)fc.x - v0[0], (double)fc.y - v0[1], (double)fc.z - v0[2]};
+  double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
+  const double un = u[0] * nn[0] + u[1] * nn[1] + u[2] * nn[2];
+  const double num = nn[0] * (v0[0] - r.tx[0]) + nn[1] * (v0[1] - r.tx[1]) + nn[2] * (v0[2] - r.tx[2]);
+  double t = num / un;
+  if (!(t > 0.0)) t = (double)J.hit_t[hl];
+  J.hit_t[hl] = (float)t;
+  G.t = t;
+  for (int k = 0; k < 3; ++k) G.p[k] = r.tx[k] + t * u[k];
+  const double inl = rsqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
+  const double sgn = un > 0.0 ? -inl : inl;
+  for (int k = 0; k < 3; ++k) {
+    G.nf[k] = (float)(nn[k] * sgn);
+    G.uf[k] = (float)u[k];
+  }
+  G.ci = -(G.uf[0] * G.nf[0] + G.uf[1] * G.nf[1] + G.uf[2] * G.nf[2]);
+  for (int k = 0; k < 3; ++k) G.mr[k] = G.uf[k] + 2.f * G.ci * G.nf[k];
+  G.omega = (float)(ce * J.g.daz * J.g.del);
+  return G;
+}
+
+// The echo of geometry (p, t, nf, mr, ci, omega) at a receiver at rx:
+// total path d = t + |p - rx| (FP64 sum), amplitude a = Omega g / (t r)
+// with g the alpha-mix of the specular lobe and the Lambertian term (or 1
+// with amp_mode 1), and the unit vector uj from the hit to the receiver.
+// The hit-to-receiver vector is taken in FP64 and rounded to FP32.
+__device__ __forceinline__ void echo_at_rx(const double *p, double t, const float *nf, const float *mr, float ci,
+                                           float omega, const double *rx, float alpha, float spec_exp, int amp_mode,
+                                           double &d, float &a, float *uj) {
+  const float w[3] = {(float)(p[0] - rx[0]), (float)(p[1] - rx[1]), (float)(p[2] - rx[2])};
+  const float rj = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
+  const float irf = 1.f / rj;
+  uj[0] = w[0] * irf;
+  uj[1] = w[1] * irf;
+  uj[2] = w[2] * irf;
+  const float co = -(uj[0] * nf[0] + uj[1] * nf[1] + uj[2] * nf[2]);
+  float gj = 0.f;
+  if (co > 0.f) {
+    const float sdot = -(mr[0] * uj[0] + mr[1] * uj[1] + mr[2] * uj[2]);
+    const float s = sdot > 0.f ? powf(sdot, spec_exp) : 0.f;
+    gj = (1.f - alpha) * s + alpha * (ci * co);
+  }
+  d = t + (double)rj;
+  a = amp_mode == 1 ? 1.f : omega * gj / ((float)t * rj);
+}

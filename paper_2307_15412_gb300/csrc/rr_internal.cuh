@@ -178,6 +178,31 @@ FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap);
 // dir: device double2[n_az + n_el] for the ray-direction table.
 cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
                          uint32_t *err, cudaStream_t st, int tw_log2 = 3);
+// The traversal alone (hit list: ray, triangle, position, traversal
+// distance; the FP64 direction table), without the echo.
+cudaError_t launch_trace_hits(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
+                              uint32_t *err, cudaStream_t st, int tw_log2 = 3);
+// Imaging (imaging.cu).  Per-hit geometry of the scene's hit list seen from
+// r.tx ([cap] records of kMimoGeomBytes), then the SFCW baseband of that TX
+// for every RX: out [n_rx][n_f][2] (FP32), rx [n_rx][3] (FP64, device);
+// part: mimo_sfcw_splits(n_rx, n_f) x n_rx x n_f x 2 floats of scratch.
+constexpr int kMimoGeomBytes = 64;
+int mimo_sfcw_splits(int n_rx, int n_f);
+cudaError_t launch_mimo_sfcw(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
+                             const double *rx, int n_rx, double f0, double df, int n_f, void *geom, float *part,
+                             float *out, cudaStream_t st);
+struct VolumeDev {
+  float x0, y0, z0, dx, dy, dz;
+  int nx, ny, nz;
+};
+// Brute-force back-projection: img [nz][ny][nx][2] from s [n_tx][n_rx][n_f][2];
+// pos: n_tx TX then n_rx RX positions (float4, device).
+cudaError_t launch_backproject(const float *s, const float4 *pos, int n_tx, int n_rx, double f0, double df, int n_f,
+                               const VolumeDev &v, float *img, cudaStream_t st);
+// Maximum projection along z in dB (floored at -dyn_db) and its z index;
+// gmax: one device word of scratch.
+cudaError_t launch_max_projection(const float *img, const VolumeDev &v, float dyn_db, float *db, int32_t *z,
+                                  float *amp_tmp, uint32_t *gmax, cudaStream_t st);
 // Trace + echo of n_jobs frames in three launches plus two one-CTA scans.
 // table: device FrameJob[n_jobs] (counters zeroed by the caller); jt: device
 // JobTiles[n_jobs + 1]; hit_prefix: device int64[n_jobs + 1]; order (may be

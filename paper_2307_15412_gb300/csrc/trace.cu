@@ -35,6 +35,7 @@ namespace {
 
 constexpr int kTraceThreads = 128;        // 4 warps, each tracing 8 x 4 ray tiles
 #include "traverse.cuh"
+#include "echo_geom.cuh"
 
 // Conservative index rectangle [i0, i1) x [j0, j1) of the rays that can meet
 // the scene box: the box corners in the radar frame bound azimuth exactly
@@ -332,54 +333,15 @@ k_echo(const FrameJob one, const FrameJob *__restrict__ table, const int64_t *__
     const int job = table ? job_of_hit(pre, n_jobs, h) : 0;
     const FrameJob &J = table ? table[job] : one;
     const int64_t hl = table ? h - pre[job] : h;
-    const int ray = J.hit_ray[hl];
-    const int pos = J.hit_pos[hl];
-    const int i_el = ray / J.g.n_az, i_az = ray - i_el * J.g.n_az;
-    // exact ray direction (FP64), as the grid defines it
-    const double2 scA = J.dir[i_az], scE = J.dir[J.g.n_az + i_el];
-    const double sa = scA.x, ca = scA.y, se = scE.x, ce = scE.y;
-    const double ur[3] = {ce * sa, se, ce * ca};
-    double u[3];
-#pragma unroll
-    for (int k = 0; k < 3; ++k) u[k] = r.R[3 * k] * ur[0] + r.R[3 * k + 1] * ur[1] + r.R[3 * k + 2] * ur[2];
-    const float4 fa = __ldg(J.tris + 3 * pos), fb = __ldg(J.tris + 3 * pos + 1), fc = __ldg(J.tris + 3 * pos + 2);
-    const double v0[3] = {fa.x, fa.y, fa.z};
-    const double e1[3] = {(double)fb.x - v0[0], (double)fb.y - v0[1], (double)fb.z - v0[2]};
-    const double e2[3] = {(double)fc.x - v0[0], (double)fc.y - v0[1], (double)fc.z - v0[2]};
-    double nn[3] = {e1[1] * e2[2] - e1[2] * e2[1], e1[2] * e2[0] - e1[0] * e2[2], e1[0] * e2[1] - e1[1] * e2[0]};
-    const double un = u[0] * nn[0] + u[1] * nn[1] + u[2] * nn[2];
-    const double num = nn[0] * (v0[0] - r.tx[0]) + nn[1] * (v0[1] - r.tx[1]) + nn[2] * (v0[2] - r.tx[2]);
-    double t = num / un;
-    if (!(t > 0.0)) t = (double)J.hit_t[hl];  // degenerate plane: keep the traversal distance
-    J.hit_t[hl] = (float)t;
-    const double p[3] = {r.tx[0] + t * u[0], r.tx[1] + t * u[1], r.tx[2] + t * u[2]};
-    // unit face normal turned toward the incoming ray (two-sided faces)
-    const double inl = rsqrt(nn[0] * nn[0] + nn[1] * nn[1] + nn[2] * nn[2]);
-    const double sgn = un > 0.0 ? -inl : inl;
-    const float nf[3] = {(float)(nn[0] * sgn), (float)(nn[1] * sgn), (float)(nn[2] * sgn)};
-    const float uf[3] = {(float)u[0], (float)u[1], (float)u[2]};
-    const float ci = -(uf[0] * nf[0] + uf[1] * nf[1] + uf[2] * nf[2]);
-    // Eq. 2 mirror direction u - 2 (u . n_f) n_f
-    const float mr[3] = {uf[0] + 2.f * ci * nf[0], uf[1] + 2.f * ci * nf[1], uf[2] + 2.f * ci * nf[2]};
-    const float omega = (float)(ce * J.g.daz * J.g.del);
-    const float tf = (float)t;
+    const EchoGeom G = echo_geometry(J, r, hl);
     for (int j = 0; j < r.n_rx; ++j) {
-      // hit -> RX j in FP32 (the difference taken in FP64): about 1e-7 relative
-      const float w[3] = {(float)(p[0] - r.rx[j][0]), (float)(p[1] - r.rx[j][1]), (float)(p[2] - r.rx[j][2])};
-      const float rj = sqrtf(w[0] * w[0] + w[1] * w[1] + w[2] * w[2]);
-      const float irf = 1.f / rj;
-      const float uj[3] = {w[0] * irf, w[1] * irf, w[2] * irf};
-      const float co = -(uj[0] * nf[0] + uj[1] * nf[1] + uj[2] * nf[2]);
-      float gj = 0.f;
-      if (co > 0.f) {
-        const float sdot = -(mr[0] * uj[0] + mr[1] * uj[1] + mr[2] * uj[2]);
-        const float s = sdot > 0.f ? powf(sdot, r.spec_exp) : 0.f;
-        gj = (1.f - alpha) * s + alpha * (ci * co);
-      }
+      double d;
+      float a, uj[3];
+      echo_at_rx(G.p, G.t, G.nf, G.mr, G.ci, G.omega, r.rx[j], alpha, r.spec_exp, r.amp_mode, d, a, uj);
       const int64_t o = (int64_t)j * J.ld + hl;
-      J.hit_d[o] = (float)(t + (double)rj);
-      J.hit_a[o] = r.amp_mode == 1 ? 1.f : omega * gj / (tf * rj);
-      J.hit_dd[o] = J.vel[0] * (uf[0] + uj[0]) + J.vel[1] * (uf[1] + uj[1]) + J.vel[2] * (uf[2] + uj[2]);
+      J.hit_d[o] = (float)d;
+      J.hit_a[o] = a;
+      J.hit_dd[o] = J.vel[0] * (G.uf[0] + uj[0]) + J.vel[1] * (G.uf[1] + uj[1]) + J.vel[2] * (G.uf[2] + uj[2]);
     }
   }
 }
@@ -439,19 +401,26 @@ FrameJob frame_job_for(SceneDev &s, const GridDev &g, int64_t cap) {
   return j;
 }
 
-cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
-                         uint32_t *err, cudaStream_t st, int tw_log2) {
+cudaError_t launch_trace_hits(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
+                              uint32_t *err, cudaStream_t st, int tw_log2) {
   if (!dir) return cudaErrorInvalidValue;
   // hit counter and tile counter
   cudaError_t e = cudaMemsetAsync(s.hit_count, 0, 2 * sizeof(uint32_t), st);
   if (e != cudaSuccess) return e;
+  FrameJob one = frame_job_for(s, g, cap);
+  one.dir = dir;
+  k_trace<<<trace_ctas_per_sm() * sm_count(), kTraceThreads, 0, st>>>(one, nullptr, nullptr, 1, r, tw_log2,
+                                                                      reinterpret_cast<int *>(s.hit_count + 1), err);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_trace(SceneDev &s, const RadarDev &r, const GridDev &g, int64_t cap, double2 *dir,
+                         uint32_t *err, cudaStream_t st, int tw_log2) {
+  cudaError_t e = launch_trace_hits(s, r, g, cap, dir, err, st, tw_log2);
+  if (e != cudaSuccess) return e;
   const int sms = sm_count();
   FrameJob one = frame_job_for(s, g, cap);
   one.dir = dir;
-  k_trace<<<trace_ctas_per_sm() * sms, kTraceThreads, 0, st>>>(one, nullptr, nullptr, 1, r, tw_log2,
-                                                               reinterpret_cast<int *>(s.hit_count + 1), err);
-  e = cudaGetLastError();
-  if (e != cudaSuccess) return e;
   const int64_t want = (cap + 127) / 128;
   const int blocks = (int)(want < 2 * sms ? (want < 1 ? 1 : want) : 2 * sms);
   k_echo<<<blocks, 128, 0, st>>>(one, nullptr, nullptr, 1, r, r.alpha);

@@ -399,9 +399,71 @@ def measure_stochastic(args):
     ctx.close()
 
 
+def measure_imaging(args):
+    """Imaging workload (Sec. II and IV): SFCW baseband of the 94 x 94
+    pairs of the square array for a ~20k-triangle hand at 0.315 m (512^2
+    rays per TX), brute-force back-projection into 201 x 201 x 81 voxels,
+    maximum projection to a -15 dB image."""
+    torch, I, rr, ctx = _setup()
+    grid, nt = I.workload_imaging()
+    s = I.hand_scene(8, nt, center=(0.0, 0.0, I.IMAGING_RANGE))
+    tx, rx = I.mimo_square_array()
+    vol = I.imaging_volume()
+    F0, DF, NF = I.IMAGING_F0, I.IMAGING_DF, I.IMAGING_NF
+    ctx.scene_upload(0, s.V, s.F, None)
+    ctx.build_bvh(0)
+    base = torch.empty((len(tx), len(rx), NF, 2), dtype=torch.float32, device="cuda")
+    img = torch.empty((vol.nz, vol.ny, vol.nx, 2), dtype=torch.float32, device="cuda")
+    db = torch.empty((vol.ny, vol.nx), dtype=torch.float32, device="cuda")
+    zi = torch.empty((vol.ny, vol.nx), dtype=torch.int32, device="cuda")
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device="cuda")
+    stream = torch.cuda.current_stream()
+
+    def run(ev=None):
+        if ev:
+            ev[0].record(stream)
+        ctx.mimo_sfcw(0, grid, tx, rx, base, F0, DF, NF, alpha=0.5)
+        if ev:
+            ev[1].record(stream)
+        ctx.backproject(base, tx, rx, F0, DF, NF, vol, img)
+        if ev:
+            ev[2].record(stream)
+        ctx.max_projection(img, vol, 15.0, db, zi)
+        if ev:
+            ev[3].record(stream)
+
+    for _ in range(2):
+        run()
+    ctx.sync()
+    evs = []
+    for _ in range(args.steps):
+        flush.zero_()
+        ev = [torch.cuda.Event(enable_timing=True) for _ in range(4)]
+        run(ev)
+        evs.append(ev)
+    ctx.sync()
+    torch.cuda.synchronize()
+    t = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in evs]).mean(0)
+    pairs = len(tx) * len(rx)
+    macs = float(vol.n) * pairs * NF
+    fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    achieved = 8.0 * macs / (t[1] / 1e3) / 1e12
+    print(json.dumps({"workload": "imaging: ~20k-triangle hand at 0.315 m, 94 TX x 94 RX square array (47 per side, "
+                                  "3 mm), 512^2 rays per TX over +-20 deg, alpha 0.5, SFCW 72 GHz + n 10/128 GHz, "
+                                  "n = 0..127; volume 201 x 201 x 81 at 1 mm; L2 flushed before each step",
+                      "ms": {"mimo_sfcw": float(t[0]), "backproject": float(t[1]), "max_projection": float(t[2]),
+                             "total": float(t.sum())},
+                      "backproject": {"complex_macs": macs, "gmacs_per_s": macs / (t[1] / 1e3) / 1e9,
+                                      "tflops_8_per_mac": achieved, "fp32_peak_tflops": fp32_peak,
+                                      "frac": achieved / fp32_peak,
+                                      "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"},
+                      "images_per_s": 1e3 / float(t.sum())}))
+    ctx.close()
+
+
 def main():
     ap = argparse.ArgumentParser()
-    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion", "triangles", "stochastic"])
+    ap.add_argument("what", choices=["batch", "surrogate", "tiny", "motion", "triangles", "stochastic", "imaging"])
     ap.add_argument("--jobs", type=int, default=256)
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--train", type=int, default=200000)
@@ -419,6 +481,8 @@ def main():
         measure_triangles(args)
     elif args.what == "stochastic":
         measure_stochastic(args)
+    elif args.what == "imaging":
+        measure_imaging(args)
     else:
         measure_surrogate(args)
 

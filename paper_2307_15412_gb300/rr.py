@@ -54,6 +54,25 @@ class rr_stochastic(ctypes.Structure):
                 ("frame", ctypes.c_uint32)]
 
 
+class rr_sfcw(ctypes.Structure):
+    _fields_ = [("f0", ctypes.c_double), ("df", ctypes.c_double), ("n_f", ctypes.c_int32),
+                ("amp_mode", ctypes.c_int32), ("alpha", ctypes.c_double), ("spec_exp", ctypes.c_double),
+                ("frame", ctypes.c_double * 9)]
+
+
+class rr_volume(ctypes.Structure):
+    _fields_ = [("x0", ctypes.c_double), ("y0", ctypes.c_double), ("z0", ctypes.c_double),
+                ("dx", ctypes.c_double), ("dy", ctypes.c_double), ("dz", ctypes.c_double),
+                ("nx", ctypes.c_int32), ("ny", ctypes.c_int32), ("nz", ctypes.c_int32), ("reserved", ctypes.c_int32)]
+
+
+def make_volume(v) -> rr_volume:
+    if isinstance(v, rr_volume):
+        return v
+    return rr_volume(float(v.x0), float(v.y0), float(v.z0), float(v.dx), float(v.dy), float(v.dz),
+                     int(v.nx), int(v.ny), int(v.nz), 0)
+
+
 class rr_mesh(ctypes.Structure):
     _fields_ = [("scene", ctypes.c_int32), ("reserved", ctypes.c_int32), ("verts", ctypes.c_void_p),
                 ("nv", ctypes.c_int64), ("tris", ctypes.c_void_p), ("nt", ctypes.c_int64),
@@ -93,6 +112,9 @@ SIGNATURES = {
     "rr_trace_triangles": (_I, [_P, _I, _P, _I, ctypes.c_int64, _P]),
     "rr_alpha_sweep": (_I, [_P, _I, _P, _I, _I, _P, _P]),
     "rr_trace_stochastic": (_I, [_P, _I, _P, _P, _P, ctypes.c_int64, _P]),
+    "rr_mimo_sfcw": (_I, [_P, _I, _P, _P, _P, _I, _P, _I, _P]),
+    "rr_backproject": (_I, [_P, _P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P]),
+    "rr_max_projection": (_I, [_P, _P, _P, ctypes.c_double, _P, _P]),
     "rr_philox_words": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, _P]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
@@ -332,6 +354,39 @@ class Context:
         if want_count:
             self._pending.append((cell, box))
         return box
+
+    def mimo_sfcw(self, scene: int, grid, tx, rx, s_out, f0: float, df: float, n_f: int, alpha: float = 0.5,
+                  spec_exp: float = 8.0, amp_mode: int = 0, frame=None):
+        """SFCW baseband of every TX-RX pair (Sec. II, Eq. 4): s_out torch
+        CUDA float32 [n_tx][n_rx][n_f][2]; tx, rx host [n][3] (m)."""
+        sw = rr_sfcw()
+        sw.f0, sw.df, sw.n_f, sw.amp_mode = float(f0), float(df), int(n_f), int(amp_mode)
+        sw.alpha, sw.spec_exp = float(alpha), float(spec_exp)
+        fr = np.eye(3) if frame is None else np.asarray(frame, np.float64).reshape(3, 3)
+        for k in range(9):
+            sw.frame[k] = float(fr.ravel()[k])
+        txa = np.ascontiguousarray(np.asarray(tx, np.float64).reshape(-1, 3))
+        rxa = np.ascontiguousarray(np.asarray(rx, np.float64).reshape(-1, 3))
+        gs = make_grid(grid)
+        self._check(self.lib.rr_mimo_sfcw(self.h, int(scene), ctypes.byref(sw), ctypes.byref(gs), txa.ctypes.data,
+                                          int(txa.shape[0]), rxa.ctypes.data, int(rxa.shape[0]), _ptr(s_out)))
+
+    def backproject(self, s, tx, rx, f0: float, df: float, n_f: int, volume, img):
+        """Brute-force SFCW back-projection (Sec. IV-A) into img, torch CUDA
+        float32 [nz][ny][nx][2]."""
+        txa = np.ascontiguousarray(np.asarray(tx, np.float64).reshape(-1, 3))
+        rxa = np.ascontiguousarray(np.asarray(rx, np.float64).reshape(-1, 3))
+        vol = make_volume(volume)
+        self._check(self.lib.rr_backproject(self.h, _ptr(s), txa.ctypes.data, int(txa.shape[0]), rxa.ctypes.data,
+                                            int(rxa.shape[0]), float(f0), float(df), int(n_f), ctypes.byref(vol),
+                                            _ptr(img)))
+
+    def max_projection(self, img, volume, dyn_range_db: float, db_out, z_out=None):
+        """Maximum projection along z in dB (Sec. IV-A): db_out float32
+        [ny][nx], z_out int32 [ny][nx] or None."""
+        vol = make_volume(volume)
+        self._check(self.lib.rr_max_projection(self.h, _ptr(img), ctypes.byref(vol), float(dyn_range_db),
+                                               _ptr(db_out), _ptr(z_out)))
 
     def philox_words(self, k0: int, k1: int, c1: int, n: int, out):
         """out: torch CUDA int32 [4 n] (the uint32 words' bits)."""

@@ -1,0 +1,241 @@
+"""GPU: the imaging workload (Sec. II and IV) through the C-ABI against the
+oracle.
+
+Bars:
+  * SFCW baseband on the GPU's own hits (the rays and triangles the
+    single-radar trace finds from that TX): rel-L2 <= 1e-5 against the
+    oracle's FP64 echo and Eq. 4 sum over those hits, with FP64 plane
+    distances (the hit list's FP32 path lengths alone carry ~1e-5 cycles of
+    phase at 80 GHz); end to end against the oracle's frame (FP64
+    brute-force trace): rel-L2 <= 1e-3 (the whole-frame bar);
+  * back-projection: rel-L2 <= 1e-4 and max error <= 3e-4 of the largest
+    |I| against the FP64 definition (FP32 path lengths carry ~1e-5 cycles
+    of phase);
+  * point target: the image at the scatterer is n_pairs * n_f within 1e-4
+    and is the neighbourhood's maximum;
+  * maximum projection: z index exact where the largest two amplitudes
+    differ by more than 1e-5, dB within 1e-4 dB of numpy on the same volume.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import oracle
+from oracle import imaging as oim
+from paper_2307_15412_gb300 import inputs as I
+
+from gpu_helpers import gpu_hits, rel_l2, to_complex
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+
+C = 299_792_458.0
+F0, DF, NF = I.IMAGING_F0, I.IMAGING_DF, I.IMAGING_NF
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    import __graft_entry__ as g
+    g.build()
+    from paper_2307_15412_gb300 import rr
+    c = rr.Context(0)
+    yield c
+    c.close()
+
+
+def _buf(*shape, dtype=torch.float32):
+    return torch.zeros(shape, dtype=dtype, device="cuda:0")
+
+
+def _sfcw_radar(tx, rx_rows):
+    return I.Radar(f0=F0, bandwidth=DF * NF, t_chirp=1e-3, n_samples=NF, n_chirps=1, tx=tuple(tx),
+                   rx=tuple(map(tuple, rx_rows)))
+
+
+def _fp64_rows(scene, tx, rows, grid, h):
+    """The oracle's FP64 echo and SFCW sum over the GPU's hits (ray,
+    triangle) from tx, with the FP64 distance to the triangle's plane."""
+    dirs, omega = oracle.ray_dirs(grid)
+    u = dirs[h["ray"]]
+    V = scene.V.astype(np.float64)
+    tri = h["tri"].astype(np.int64)
+    v0, v1, v2 = (V[scene.F[tri, k]] for k in range(3))
+    n = np.cross(v1 - v0, v2 - v0)
+    t = np.einsum("ij,ij->i", n, v0 - np.asarray(tx)) / np.einsum("ij,ij->i", n, u)
+    radar = _sfcw_radar(tx, rows)
+    d, a, dd = oracle.echo(scene.V, scene.F, np.asarray(tx, np.float64), u, t, h["tri"], omega[h["ray"]], radar,
+                           np.zeros(3))
+    return oracle.synth(d, a, dd, radar)[:, 0, :]
+
+
+def test_mimo_sfcw_on_the_gpu_hits_and_end_to_end(ctx):
+    s = I.hand_scene(5, 2000, center=(0.0, 0.0, I.IMAGING_RANGE))
+    tx_all, rx_all = I.mimo_square_array()
+    tx = tx_all[[0, 23, 46, 47, 70, 93]]
+    rx = rx_all[[0, 11, 30, 46, 47, 60, 80, 93, 5, 52]]
+    grid = I.RayGrid(64, 64, math.radians(20.0), math.radians(20.0))
+    ctx.scene_upload(70, s.V, s.F, None)
+    ctx.build_bvh(70)
+    out = _buf(len(tx), len(rx), NF, 2)
+    ctx.mimo_sfcw(70, grid, tx, rx, out, F0, DF, NF)
+    ctx.sync()
+    got = to_complex(out)
+    # (1) each TX's rows on the hit list the single-radar path traces for it
+    ctx.scene_upload(71, s.V, s.F, None)
+    ctx.build_bvh(71)
+    for t in range(len(tx)):
+        for j0 in (0, 8):
+            rows = rx[j0:j0 + 8]
+            radar = _sfcw_radar(tx[t], rows)
+            cnt = ctx.trace_frame(71, radar, grid)
+            ctx.sync()
+            h = gpu_hits(ctx, 71, len(rows), cnt[0])
+            assert h["ray"].size > 50
+            ref = _fp64_rows(s, tx[t], rows, grid, h)
+            assert rel_l2(got[t, j0:j0 + len(rows)], ref) <= 1e-5
+    # (2) end to end against the oracle's own trace and echo
+    ref = oim.mimo_sfcw(s.V, s.F, tx, rx, grid, F0, DF, NF)
+    assert rel_l2(got, ref) <= 1e-3
+    # a second run: the same hits, summed in the trace's append order
+    out2 = _buf(len(tx), len(rx), NF, 2)
+    ctx.mimo_sfcw(70, grid, tx, rx, out2, F0, DF, NF)
+    ctx.sync()
+    assert rel_l2(to_complex(out2), got) <= 1e-6
+
+
+def test_mimo_sfcw_empty_and_missed_scenes(ctx):
+    tx, rx = I.mimo_square_array(3, 6e-3)
+    grid = I.RayGrid(32, 32, math.radians(10.0), math.radians(10.0))
+    ctx.scene_upload(72, np.zeros((3, 3), np.float32), np.zeros((0, 3), np.int32), None)
+    ctx.build_bvh(72)
+    out = _buf(len(tx), len(rx), 16, 2) + 7.0
+    ctx.mimo_sfcw(72, grid, tx, rx, out, F0, DF, 16)
+    ctx.sync()
+    assert torch.count_nonzero(out) == 0
+    # a plate behind the array: no ray reaches it
+    V, F = I.plate((0.0, 0.0, -0.3), 0.05, 0.05)
+    ctx.scene_upload(73, V, F, None)
+    ctx.build_bvh(73)
+    out = _buf(len(tx), len(rx), 16, 2) + 7.0
+    ctx.mimo_sfcw(73, grid, tx, rx, out, F0, DF, 16)
+    ctx.sync()
+    assert torch.count_nonzero(out) == 0
+
+
+def test_imaging_argument_checks(ctx):
+    from paper_2307_15412_gb300 import rr
+    tx, rx = I.mimo_square_array(2, 6e-3)
+    grid = I.RayGrid(16, 16, 0.3, 0.3)
+    out = _buf(len(tx), len(rx), 8, 2)
+    ctx.scene_upload(74, *I.plate((0.0, 0.0, 0.3), 0.05, 0.05), None)
+    with pytest.raises(rr.RRError) as e:
+        ctx.mimo_sfcw(74, grid, tx, rx, out, F0, DF, 8)
+    assert e.value.status == rr.RR_ENOTREADY
+    ctx.build_bvh(74)
+    for bad in (dict(n_f=0), dict(f0=-1.0), dict(alpha=1.5)):
+        kw = dict(f0=F0, df=DF, n_f=8, alpha=0.5)
+        kw.update(bad)
+        with pytest.raises(rr.RRError) as e:
+            ctx.mimo_sfcw(74, grid, tx, rx, out, kw["f0"], kw["df"], kw["n_f"], alpha=kw["alpha"])
+        assert e.value.status == rr.RR_EINVAL
+    vol = I.Volume(0.0, 0.0, 0.3, 1e-3, 1e-3, 1e-3, 0, 4, 4)
+    img = _buf(4, 4, 4, 2)
+    with pytest.raises(rr.RRError) as e:
+        ctx.backproject(out, tx, rx, F0, DF, 8, vol, img)
+    assert e.value.status == rr.RR_EINVAL
+    with pytest.raises(rr.RRError) as e:
+        ctx.max_projection(img, I.Volume(0.0, 0.0, 0.3, 1e-3, 1e-3, 1e-3, 4, 4, 4), -3.0, _buf(4, 4))
+    assert e.value.status == rr.RR_EINVAL
+
+
+def test_backproject_matches_the_definition(ctx):
+    tx, rx = I.mimo_square_array(5, 6e-3)
+    rng = np.random.default_rng(11)
+    s = (rng.standard_normal((10, 10, NF)) + 1j * rng.standard_normal((10, 10, NF))).astype(np.complex64)
+    vol = I.Volume(-0.02, -0.016, 0.29, 2e-3, 2e-3, 2.5e-3, 21, 17, 9)
+    s_dev = torch.from_numpy(np.stack([s.real, s.imag], -1).astype(np.float32)).cuda()
+    img = _buf(vol.nz, vol.ny, vol.nx, 2)
+    ctx.backproject(s_dev, tx, rx, F0, DF, NF, vol, img)
+    ctx.sync()
+    got = to_complex(img).ravel()
+    ref = oim.backproject(s.astype(np.complex128), tx, rx, F0, DF, oim.volume_voxels(vol))
+    assert rel_l2(got, ref) <= 1e-4
+    assert np.abs(got - ref).max() <= 3e-4 * np.abs(ref).max()
+    img2 = _buf(vol.nz, vol.ny, vol.nx, 2)
+    ctx.backproject(s_dev, tx, rx, F0, DF, NF, vol, img2)
+    ctx.sync()
+    assert torch.equal(img, img2)
+
+
+def test_backproject_point_target_full_array(ctx):
+    """The full 94 x 94 array and 128 steps: an ideal point scatterer on a
+    voxel centre images to 8836 * 128 there, the largest value around it."""
+    tx, rx = I.mimo_square_array()
+    q = np.array([0.012, -0.021, 0.307])
+    f = F0 + DF * np.arange(NF)
+    R = np.linalg.norm(q - tx, axis=1)[:, None] + np.linalg.norm(q - rx, axis=1)[None, :]
+    s = np.exp(-2j * np.pi * R[:, :, None] * f[None, None, :] / C)
+    s_dev = torch.from_numpy(np.stack([s.real, s.imag], -1).astype(np.float32)).cuda()
+    vol = I.Volume(q[0] - 2e-3, q[1] - 2e-3, q[2] - 2e-3, 1e-3, 1e-3, 1e-3, 5, 5, 5)
+    img = _buf(5, 5, 5, 2)
+    ctx.backproject(s_dev, tx, rx, F0, DF, NF, vol, img)
+    ctx.sync()
+    a = np.abs(to_complex(img))
+    full = 94 * 94 * NF
+    assert abs(a[2, 2, 2] - full) <= 1e-4 * full
+    assert np.argmax(a) == 62
+
+
+def test_full_size_volume_sampled_and_projection(ctx):
+    """The imaging workload in the launch configuration the measurement
+    times: the full array's SFCW baseband of a hand (20k triangles, 512^2
+    rays per TX), back-projected into the 201 x 201 x 81 volume; sampled
+    voxels against the FP64 definition on the GPU's baseband, the maximum
+    projection against numpy on the GPU's volume."""
+    grid, nt = I.workload_imaging()
+    s = I.hand_scene(8, nt, center=(0.0, 0.0, I.IMAGING_RANGE))
+    tx, rx = I.mimo_square_array()
+    vol = I.imaging_volume()
+    ctx.scene_upload(75, s.V, s.F, None)
+    ctx.build_bvh(75)
+    base = _buf(94, 94, NF, 2)
+    ctx.mimo_sfcw(75, grid, tx, rx, base, F0, DF, NF)
+    img = _buf(vol.nz, vol.ny, vol.nx, 2)
+    ctx.backproject(base, tx, rx, F0, DF, NF, vol, img)
+    db = _buf(vol.ny, vol.nx)
+    zi = torch.zeros((vol.ny, vol.nx), dtype=torch.int32, device="cuda:0")
+    ctx.max_projection(img, vol, 15.0, db, zi)
+    ctx.sync()
+    sb = to_complex(base)
+    assert np.linalg.norm(sb) > 0
+    # two TX rows against the FP64 sum over the single-radar path's hits
+    ctx.scene_upload(76, s.V, s.F, None)
+    ctx.build_bvh(76)
+    for t in (3, 60):
+        radar = _sfcw_radar(tx[t], rx[[0, 40, 93]])
+        cnt = ctx.trace_frame(76, radar, grid)
+        ctx.sync()
+        h = gpu_hits(ctx, 76, 3, cnt[0])
+        ref = _fp64_rows(s, tx[t], rx[[0, 40, 93]], grid, h)
+        assert rel_l2(sb[t, [0, 40, 93]], ref) <= 1e-5
+    vimg = to_complex(img)
+    amp = np.abs(vimg)
+    top = amp.max()
+    rng = np.random.default_rng(2)
+    flat = rng.choice(vol.n, size=12, replace=False)
+    peak = int(np.argmax(amp))
+    flat = np.concatenate([flat, [peak]])
+    vox = oim.volume_voxels(vol)[flat]
+    ref = oim.backproject(sb, tx, rx, F0, DF, vox)
+    got = vimg.ravel()[flat]
+    assert np.abs(got - ref).max() <= 3e-4 * top
+    # maximum projection against numpy on the same volume
+    want_db, want_z = oim.max_projection(vimg, 15.0)
+    srt = np.sort(amp, axis=0)
+    unique = (srt[-1] - srt[-2]) > 1e-5 * srt[-1]
+    assert np.array_equal(zi.cpu().numpy()[unique], want_z[unique])
+    assert np.abs(db.cpu().numpy() - want_db).max() <= 1e-4
