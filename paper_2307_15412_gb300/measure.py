@@ -409,6 +409,8 @@ def measure_imaging(args):
     s = I.hand_scene(8, nt, center=(0.0, 0.0, I.IMAGING_RANGE))
     tx, rx = I.mimo_square_array()
     vol = I.imaging_volume()
+    if args.nz:
+        vol.nz = int(args.nz)  # a thinner slab of the volume (profiling captures)
     F0, DF, NF = I.IMAGING_F0, I.IMAGING_DF, I.IMAGING_NF
     ctx.scene_upload(0, s.V, s.F, None)
     ctx.build_bvh(0)
@@ -450,7 +452,7 @@ def measure_imaging(args):
     achieved = 8.0 * macs / (t[1] / 1e3) / 1e12
     print(json.dumps({"workload": "imaging: ~20k-triangle hand at 0.315 m, 94 TX x 94 RX square array (47 per side, "
                                   "3 mm), 512^2 rays per TX over +-20 deg, alpha 0.5, SFCW 72 GHz + n 10/128 GHz, "
-                                  "n = 0..127; volume 201 x 201 x 81 at 1 mm; L2 flushed before each step",
+                                  "n = 0..127; volume 201 x 201 x %d at 1 mm; L2 flushed before each step" % vol.nz,
                       "ms": {"mimo_sfcw": float(t[0]), "backproject": float(t[1]), "max_projection": float(t[2]),
                              "total": float(t.sum())},
                       "backproject": {"complex_macs": macs, "gmacs_per_s": macs / (t[1] / 1e3) / 1e9,
@@ -470,6 +472,7 @@ def main():
     ap.add_argument("--test", type=int, default=4096)
     ap.add_argument("--epochs", type=int, default=40)
     ap.add_argument("--lr", type=float, default=1e-3)
+    ap.add_argument("--nz", type=int, default=0, help="imaging: z slices of the volume (0: the full 81)")
     args = ap.parse_args()
     if args.what == "batch":
         measure_batch(args)
