@@ -77,10 +77,21 @@ struct rr_ctx {
     int64_t dir_cap = 0;
     // the plan of the last batch (rr_batch_plan)
     int last_tw = 0, last_split = 0, last_c = 0, last_launches = 0;
-    // CUDA graph of the last batch
-    cudaGraphExec_t exec = nullptr;
-    cudaStream_t cap_stream = nullptr;      // stream the graph is captured on
-    uint64_t key = 0;
+    // CUDA graphs of the last two batch shapes (a caller may alternate two
+    // sets of scenes or outputs), least recently used replaced first
+    struct GraphSlot {
+      cudaGraphExec_t exec = nullptr;
+      uint64_t key = 0, used = 0;
+    } graphs[2];
+    uint64_t graph_tick = 0;
+    cudaStream_t cap_stream = nullptr;      // stream the graphs are captured on
+    bool any_graph() const { return graphs[0].exec || graphs[1].exec; }
+    void drop_graphs() {
+      for (GraphSlot &g : graphs) {
+        if (g.exec) cudaGraphExecDestroy(g.exec);
+        g.exec = nullptr;
+      }
+    }
     // autotuner choices per batch shape: (ray-tile width log2, split-K)
     std::map<uint64_t, std::pair<int, int>> tuned;
   } batch;
@@ -300,7 +311,7 @@ rr_status rr_destroy(rr_ctx *c) {
     if (b.h_ftab) cudaFreeHost(b.h_ftab);
     if (b.h_btab) cudaFreeHost(b.h_btab);
     if (b.staged) cudaEventDestroy(b.staged);
-    if (b.exec) cudaGraphExecDestroy(b.exec);
+    b.drop_graphs();
     if (b.cap_stream) cudaStreamDestroy(b.cap_stream);
   }
   if (c->sur) rr::surrogate_free(c->sur);
@@ -1025,6 +1036,16 @@ cudaError_t batch_enqueue(rr_ctx *c, const BatchPlan &P, cudaStream_t st, cudaEv
       (e = cudaMemcpyAsync(b.btab, b.h_btab, sizeof(rr::BuildJob) * (P.n_cluster() + P.n_refit), cudaMemcpyHostToDevice,
                            st)) != cudaSuccess)
     return e;
+  // the staging tables may be refilled once these copies are done (an
+  // external event node in a captured graph, so the host can wait on it):
+  // the next call need not wait for the whole batch
+  {
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if ((e = cudaStreamIsCapturing(st, &cs)) != cudaSuccess) return e;
+    e = cs == cudaStreamCaptureStatusActive ? cudaEventRecordWithFlags(b.staged, st, cudaEventRecordExternal)
+                                            : cudaEventRecord(b.staged, st);
+    if (e != cudaSuccess) return e;
+  }
   if ((e = cudaMemsetAsync(b.counts, 0, sizeof(uint32_t) * P.n_jobs, st)) != cudaSuccess) return e;
   for (int g = 0, off = 0; g < 5; off += P.gn[g], ++g)
     if (P.gn[g] && (e = rr::launch_build_bvh_cluster_table(b.btab + off, P.gn[g], P.gC[g], P.gcap[g], st)) != cudaSuccess)
@@ -1194,7 +1215,7 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaMalloc((void **)&b.a, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     RR_CUDA(c, cudaMalloc((void **)&b.dd, sizeof(float) * total * RR_MAX_RX), "batch hit list");
     b.cap = total;
-    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    b.drop_graphs();
   }
   // per-hit constants of the tensor-core synthesis: n_rx rows of `cap`
   if (variant != RR_SYNTH_FP32 && (b.tc_cst_rows < n_rx || !b.tc_cst)) {
@@ -1203,10 +1224,10 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     b.tc_cst_rows = 0;
     RR_CUDA(c, cudaMalloc((void **)&b.tc_cst, sizeof(float4) * b.cap * n_rx), "batch synthesis constants");
     b.tc_cst_rows = n_rx;
-    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    b.drop_graphs();
   }
   if (n_jobs > b.jobs_cap || !b.counts) {
-    if (b.staged) RR_CUDA(c, cudaEventSynchronize(b.staged), "batch staging");
+    RR_CUDA(c, cudaStreamSynchronize(c->stream), "batch tables");  // earlier batches may still read them
     void *old[] = {b.counts, b.ftab, b.btab, b.jt, b.prefix};
     for (void *p : old)
       if (p) cudaFree(p);
@@ -1225,13 +1246,13 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     RR_CUDA(c, cudaMallocHost((void **)&b.h_ftab, sizeof(rr::FrameJob) * nj), "batch tables");
     RR_CUDA(c, cudaMallocHost((void **)&b.h_btab, sizeof(rr::BuildJob) * nj), "batch tables");
     b.jobs_cap = n_jobs;
-    if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    b.drop_graphs();
   }
   if (!b.staged) RR_CUDA(c, cudaEventCreateWithFlags(&b.staged, cudaEventDisableTiming), "batch event");
   const int64_t cube = (int64_t)2 * n_rx * radar->n_chirps * radar->n_samples;
   P.ifb = if_out;
   if (!P.ifb) {
-    if (cube * n_jobs > b.if_tmp_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+    if (cube * n_jobs > b.if_tmp_cap && b.any_graph()) b.drop_graphs();
     RR_CUDA(c, grow(b.if_tmp, b.if_tmp_cap, cube * n_jobs), "batch IF buffer");
     P.ifb = b.if_tmp;
   }
@@ -1249,9 +1270,9 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
   int64_t need = batch_partials_need(P, P.split);
   if (tune)
     for (int sp : {0, 1, 2, 4}) need = std::max(need, batch_partials_need(P, sp));
-  if (need > b.partials_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  if (need > b.partials_cap && b.any_graph()) b.drop_graphs();
   RR_CUDA(c, grow(b.partials, b.partials_cap, need), "batch partials");
-  if (dseg[n_jobs] > b.dir_cap && b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+  if (dseg[n_jobs] > b.dir_cap && b.any_graph()) b.drop_graphs();
   RR_CUDA(c, grow(b.dir, b.dir_cap, dseg[n_jobs]), "batch ray-direction tables");
 
   // device tables, staged in pinned memory (wait until the last copy out of it is done)
@@ -1349,12 +1370,17 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
     c->tev_used[slot] = 1;
     ev = &c->tev[5 * slot];
   }
-  if ((flags & RR_BATCH_GRAPH) && b.exec && b.key == key) {
+  auto *hit = (flags & RR_BATCH_GRAPH) ? (b.graphs[0].exec && b.graphs[0].key == key   ? &b.graphs[0]
+                                          : b.graphs[1].exec && b.graphs[1].key == key ? &b.graphs[1]
+                                                                                       : nullptr)
+                                       : nullptr;
+  if (hit) {
+    hit->used = ++b.graph_tick;
     if (ev) {
       RR_CUDA(c, cudaEventRecord(ev[0], c->stream), "timing");
       for (int k = 1; k < 4; ++k) RR_CUDA(c, cudaEventRecord(ev[k], c->stream), "timing");
     }
-    RR_CUDA(c, cudaGraphLaunch(b.exec, c->stream), "batch graph launch");
+    RR_CUDA(c, cudaGraphLaunch(hit->exec, c->stream), "batch graph launch");
     if (ev) RR_CUDA(c, cudaEventRecord(ev[4], c->stream), "timing");
   } else {
     RR_CUDA(c, batch_enqueue(c, P, c->stream, ev), "batch launch");
@@ -1362,7 +1388,9 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
       // capture on a stream of the context's own (the caller's stream may be
       // the legacy default stream, which cannot be captured); nothing runs
       // during capture, and the graph is launched on the caller's stream
-      if (b.exec) { cudaGraphExecDestroy(b.exec); b.exec = nullptr; }
+      auto &slot = (!b.graphs[0].exec || (b.graphs[1].exec && b.graphs[0].used <= b.graphs[1].used)) ? b.graphs[0]
+                                                                                                      : b.graphs[1];
+      if (slot.exec) { cudaGraphExecDestroy(slot.exec); slot.exec = nullptr; }
       if (!b.cap_stream) RR_CUDA(c, cudaStreamCreateWithFlags(&b.cap_stream, cudaStreamNonBlocking), "capture stream");
       cudaGraph_t graph = nullptr;
       RR_CUDA(c, cudaStreamBeginCapture(b.cap_stream, cudaStreamCaptureModeThreadLocal), "batch capture");
@@ -1370,13 +1398,13 @@ extern "C" rr_status rr_batch_run(rr_ctx *c, const rr_job *jobs, int n_jobs, con
       const cudaError_t ec = cudaStreamEndCapture(b.cap_stream, &graph);
       if (ee != cudaSuccess) { if (graph) cudaGraphDestroy(graph); return cuda_fail(c, ee, "batch capture"); }
       RR_CUDA(c, ec, "batch capture");
-      const cudaError_t ei = cudaGraphInstantiate(&b.exec, graph, 0);
+      const cudaError_t ei = cudaGraphInstantiate(&slot.exec, graph, 0);
       cudaGraphDestroy(graph);
-      if (ei != cudaSuccess) { b.exec = nullptr; return cuda_fail(c, ei, "batch graph instantiate"); }
-      b.key = key;
+      if (ei != cudaSuccess) { slot.exec = nullptr; return cuda_fail(c, ei, "batch graph instantiate"); }
+      slot.key = key;
+      slot.used = ++b.graph_tick;
     }
   }
-  RR_CUDA(c, cudaEventRecord(b.staged, c->stream), "batch event");
   for (SceneDev *s : sc) {
     s->built = true;
     s->tree = true;
