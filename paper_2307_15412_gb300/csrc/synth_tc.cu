@@ -333,7 +333,12 @@ __device__ __forceinline__ void fold_row(uint32_t tmem, int warp, int nt, bool s
 
 // Cost units of one block of kHitsPerBlock hits with T expansion terms: the
 // operand stores of one producer warp (8 A rows, LO / 8 B columns per term).
-__host__ __device__ __forceinline__ int block_cost(int LO, int T) { return 8 + (LO / 8) * T; }
+// Cost units of one block of a pair with T expansion terms.  A block takes
+// the same time with one term as with two (measured: 1.41 us per block for
+// both, the producer's operand generation sets the pace), so T = 1 is
+// costed as T = 2; otherwise the CTAs whose shares hold the one-term pairs
+// (the last ones in the plan's order) would get more blocks of equal time.
+__host__ __device__ __forceinline__ int block_cost(int LO, int T) { return 8 + (LO / 8) * (T < 2 ? 2 : T); }
 
 // The CTA that owns the block starting at cost unit s when W units are
 // shared by P CTAs, CTA c taking [floor(W c / P), floor(W (c + 1) / P)).
