@@ -239,3 +239,60 @@ def test_full_size_volume_sampled_and_projection(ctx):
     unique = (srt[-1] - srt[-2]) > 1e-5 * srt[-1]
     assert np.array_equal(zi.cpu().numpy()[unique], want_z[unique])
     assert np.abs(db.cpu().numpy() - want_db).max() <= 1e-4
+
+
+@pytest.mark.parametrize("n_f, offset", [(37, 0), (64, 1), (1, 0)])
+def test_backproject_ragged_shapes(ctx, n_f, offset):
+    """Odd step counts and rows not 16-byte aligned take the one-step loads;
+    a volume of 1001 voxels ends inside a thread's four voxels."""
+    tx, rx = I.mimo_square_array(3, 7e-3)
+    rng = np.random.default_rng(20 + n_f)
+    s = (rng.standard_normal((6, 6, n_f)) + 1j * rng.standard_normal((6, 6, n_f))).astype(np.complex64)
+    flat = np.stack([s.real, s.imag], -1).astype(np.float32).ravel()
+    store = torch.zeros(flat.size + 2 * offset, dtype=torch.float32, device="cuda:0")
+    store[2 * offset:] = torch.from_numpy(flat).cuda()
+    s_dev = store[2 * offset:]
+    vol = I.Volume(-0.013, 0.004, 0.27, 1.5e-3, 2e-3, 3e-3, 13, 11, 7)
+    img = _buf(vol.nz, vol.ny, vol.nx, 2)
+    ctx.backproject(s_dev, tx, rx, F0, DF, n_f, vol, img)
+    ctx.sync()
+    got = to_complex(img).ravel()
+    ref = oim.backproject(s.astype(np.complex128), tx, rx, F0, DF, oim.volume_voxels(vol))
+    assert rel_l2(got, ref) <= 1e-4
+    assert np.abs(got - ref).max() <= 3e-4 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("n_f", [1, 300, 2500])
+def test_mimo_sfcw_step_counts(ctx, n_f):
+    """Step counts that leave idle lanes (300: 19 groups of 16 steps), one
+    step, and more groups than a CTA's threads (2500: 157 groups, two CTAs
+    per RX along y) against the FP64 sum over the GPU's hits."""
+    s = I.hand_scene(6, 1000, center=(0.0, 0.0, I.IMAGING_RANGE))
+    tx_all, rx_all = I.mimo_square_array()
+    tx, rx = tx_all[[10, 60]], rx_all[[3, 50, 90]]
+    grid = I.RayGrid(48, 48, math.radians(20.0), math.radians(20.0))
+    ctx.scene_upload(77, s.V, s.F, None)
+    ctx.build_bvh(77)
+    out = _buf(len(tx), len(rx), n_f, 2)
+    ctx.mimo_sfcw(77, grid, tx, rx, out, F0, DF, n_f)
+    ctx.sync()
+    got = to_complex(out)
+    ctx.scene_upload(78, s.V, s.F, None)
+    ctx.build_bvh(78)
+    for t in range(len(tx)):
+        radar = I.Radar(f0=F0, bandwidth=DF * n_f, t_chirp=1e-3, n_samples=n_f, n_chirps=1, tx=tuple(tx[t]),
+                        rx=tuple(map(tuple, rx)))
+        cnt = ctx.trace_frame(78, radar, grid)
+        ctx.sync()
+        h = gpu_hits(ctx, 78, len(rx), cnt[0])
+        assert h["ray"].size > 20
+        dirs, omega = oracle.ray_dirs(grid)
+        u = dirs[h["ray"]]
+        V = s.V.astype(np.float64)
+        tri = h["tri"].astype(np.int64)
+        v0, v1, v2 = (V[s.F[tri, k]] for k in range(3))
+        nrm = np.cross(v1 - v0, v2 - v0)
+        tt = np.einsum("ij,ij->i", nrm, v0 - tx[t]) / np.einsum("ij,ij->i", nrm, u)
+        d, a, dd = oracle.echo(s.V, s.F, tx[t], u, tt, h["tri"], omega[h["ray"]], radar, np.zeros(3))
+        ref = oracle.synth(d, a, dd, radar)[:, 0, :]
+        assert rel_l2(got[t], ref) <= 1e-5
