@@ -75,8 +75,8 @@ __global__ void __launch_bounds__(kSfcwThreads)
 k_mimo_sfcw(const uint32_t *__restrict__ count, int64_t cap, const MimoGeom *__restrict__ geom,
             const double *__restrict__ rx, float alpha, float spec_exp, int amp_mode, double k0, double k1, int n_f,
             int n_rx, int gb, float *__restrict__ part) {
-  __shared__ float s_a[kSfcwThreads], s_p0[kSfcwThreads], s_p1h[kSfcwThreads], s_p1l[kSfcwThreads];
-  __shared__ float s_wc[kSfcwThreads], s_ws[kSfcwThreads];
+  __shared__ float4 s_h[kSfcwThreads];   // per hit: a, p0, p1 head, p1 tail
+  __shared__ float2 s_w[kSfcwThreads];   // per hit: the step phasor (cos, sin)
   __shared__ float2 s_red[kSfcwThreads * kStepsPerThread];
   const int j = blockIdx.x;
   const int lanes = kSfcwThreads / gb;          // hit lanes: threads sharing a step group
@@ -118,24 +118,22 @@ k_mimo_sfcw(const uint32_t *__restrict__ count, int64_t cap, const MimoGeom *__r
       sincospif(2.f * (float)(c1 - rint(c1)), &ws, &wc);
     }
     __syncthreads();
-    s_a[threadIdx.x] = a;
-    s_p0[threadIdx.x] = p0;
-    s_p1h[threadIdx.x] = p1h;
-    s_p1l[threadIdx.x] = p1l;
-    s_wc[threadIdx.x] = wc;
-    s_ws[threadIdx.x] = ws;
+    s_h[threadIdx.x] = make_float4(a, p0, p1h, p1l);
+    s_w[threadIdx.x] = make_float2(wc, ws);
     __syncthreads();
     const int m = (int)min((int64_t)kSfcwThreads, total - h0);
     if (active)
       for (int k = l; k < m; k += lanes) {
         // a exp(-j 2 pi phase) at the group's first step, then rotated by
         // the step phasor exp(-j 2 pi df d / c) for the group's other steps
-        const float q = fn0 * s_p1h[k];
-        float ph = (q - rintf(q)) + fmaf(fn0, s_p1l[k], s_p0[k]);
+        const float4 hk = s_h[k];
+        const float2 wk = s_w[k];
+        const float q = fn0 * hk.z;
+        float ph = (q - rintf(q)) + fmaf(fn0, hk.w, hk.y);
         ph -= rintf(ph);
         float sn, cs;
         sincospif(2.f * ph, &sn, &cs);
-        const float ak = s_a[k], c = s_wc[k], sw = s_ws[k];
+        const float ak = hk.x, c = wk.x, sw = wk.y;
         float zr = ak * cs, zi = -ak * sn;
 #pragma unroll
         for (int i = 0; i < kStepsPerThread; ++i) {
