@@ -211,6 +211,31 @@ __device__ __forceinline__ void put2(unsigned char *hi_base, unsigned char *lo_b
   }
 }
 
+// The B pair of one complex value z = re + j im: (re, -im) at off_re and
+// (im, re) at off_im, as put2 writes them, from one rounding split:
+// round-to-nearest is symmetric, so negating the high half and swapping the
+// halves give put2's bits (up to the sign of a zero low part).
+template <bool TF32>
+__device__ __forceinline__ void put2_cplx(unsigned char *hi_base, unsigned char *lo_base, uint32_t off_re,
+                                          uint32_t off_im, float re, float im) {
+  if (TF32) {
+    uint32_t tr, ti;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(tr) : "f"(re));
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(ti) : "f"(im));
+    *reinterpret_cast<uint2 *>(hi_base + off_re) = make_uint2(tr, ti ^ 0x80000000u);
+    *reinterpret_cast<uint2 *>(hi_base + off_im) = make_uint2(ti, tr);
+  } else {
+    const __nv_bfloat162 hv = __floats2bfloat162_rn(re, im);
+    const float2 f = __bfloat1622float2(hv);
+    const __nv_bfloat162 lv = __floats2bfloat162_rn(re - f.x, im - f.y);
+    const uint32_t h = bf16x2_bits(hv), l = bf16x2_bits(lv);
+    *reinterpret_cast<uint32_t *>(hi_base + off_re) = h ^ 0x80000000u;
+    *reinterpret_cast<uint32_t *>(lo_base + off_re) = l ^ 0x80000000u;
+    *reinterpret_cast<uint32_t *>(hi_base + off_im) = __byte_perm(h, 0u, 0x1032);
+    *reinterpret_cast<uint32_t *>(lo_base + off_im) = __byte_perm(l, 0u, 0x1032);
+  }
+}
+
 // Byte offset of (row or column x, block-local hit k) in an operand region
 // in the 128-byte swizzled K-major layout: 128-byte rows (x), the 16-byte
 // chunk c of row x stored at chunk c ^ (x % 8).  BF16: one 128-byte atom
@@ -755,8 +780,9 @@ k_synth_tc(const __grid_constant__ SynthTcParams p) {
           for (int t = 0; t < kTerms; ++t) {
             if (t >= nterms) break;  // columns of unused terms are not read
             const float re = w * B0.x, im = w * B0.y;
-            put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + l, lane), re, -im);        // Re half
-            put2<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + LO + l, lane), im, re);    // Im half
+            // Re half (re, -im), Im half (im, re)
+            put2_cplx<TF32>(B, B + lo_b, op_off<TF32>(2 * LO * t + l, lane), op_off<TF32>(2 * LO * t + LO + l, lane),
+                            re, im);
             w *= bl1;
           }
         }
