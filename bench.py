@@ -113,6 +113,17 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(x: float, ws: int, device) -> float:
+    """The largest of every rank's x (all ranks call it; ws == 1: x)."""
+    if ws <= 1:
+        return float(x)
+    import torch
+    import torch.distributed as dist
+    tt = torch.tensor([float(x)], device=device, dtype=torch.float64)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
 def make_scenes(rank: int):
     from paper_2307_15412_gb300 import inputs as I
     radar, grid, nt = I.workload_full_frame()
@@ -285,11 +296,7 @@ def run_gpu(args):
     if ws > 1:
         dist.barrier()
     clocks = sampler.stop()
-    t_dev = float(step_ms.sum()) / 1e3
-    if ws > 1:
-        tt = torch.tensor([t_dev], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_dev = float(tt.item())
+    t_dev = max_over_ranks(float(step_ms.sum()) / 1e3, ws, dev)
     value = ws * B * K / t_dev
 
     # the plain FP32 path beside it, same steps and timing
@@ -375,11 +382,7 @@ def run_gpu(args):
     for i in range(K_e2e):
         e2e_step(i)
     back_done[(K_e2e - 1) % 2].synchronize()
-    t_e2e = time.perf_counter() - t0
-    if ws > 1:
-        tt = torch.tensor([t_e2e], device=dev, dtype=torch.float64)
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_e2e = float(tt.item())
+    t_e2e = max_over_ranks(time.perf_counter() - t0, ws, dev)
     h2d = int(sum(s.V.nbytes + s.F.nbytes for s in scenes))
     d2h = rd_out.numel() * 4
     ctx.sync()
