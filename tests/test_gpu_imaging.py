@@ -296,3 +296,29 @@ def test_mimo_sfcw_step_counts(ctx, n_f):
         d, a, dd = oracle.echo(s.V, s.F, tx[t], u, tt, h["tri"], omega[h["ray"]], radar, np.zeros(3))
         ref = oracle.synth(d, a, dd, radar)[:, 0, :]
         assert rel_l2(got[t], ref) <= 1e-5
+
+
+def test_max_projection_ties_and_zero_volume(ctx):
+    """Equal largest amplitudes along z give the lowest z index (numpy's
+    argmax rule); an all-zero volume gives the floor everywhere."""
+    vol = I.Volume(0.0, 0.0, 0.3, 1e-3, 1e-3, 1e-3, 5, 3, 4)
+    img = np.zeros((4, 3, 5, 2), np.float32)
+    img[1, :, :, 0] = 2.0
+    img[3, :, :, 1] = -2.0          # same amplitude two slices later
+    img[2, 1, 2, 0] = 4.0           # the volume's maximum
+    dev = torch.from_numpy(img).cuda()
+    db = _buf(3, 5)
+    zi = torch.zeros((3, 5), dtype=torch.int32, device="cuda:0")
+    ctx.max_projection(dev, vol, 15.0, db, zi)
+    ctx.sync()
+    want_z = np.ones((3, 5), np.int32)
+    want_z[1, 2] = 2
+    assert np.array_equal(zi.cpu().numpy(), want_z)
+    want_db = np.full((3, 5), 20 * np.log10(0.5), np.float32)
+    want_db[1, 2] = 0.0
+    assert np.abs(db.cpu().numpy() - want_db).max() <= 1e-4
+    zero = _buf(4, 3, 5, 2)
+    ctx.max_projection(zero, vol, 12.0, db, zi)
+    ctx.sync()
+    assert torch.all(db == -12.0)
+    assert torch.count_nonzero(zi) == 0
