@@ -423,7 +423,7 @@ rr_status rr_batch_plan(const rr_ctx *ctx, int *ray_tile_log2, int *split, int *
 
 /* A multilayer perceptron that maps hand parameters to a range-Doppler cube,
  * trained on frames the tracer itself produces, with the tracer as its
- * fallback and judge.  The paper has no learned part: this is an
+ * fallback and accuracy check.  The paper has no learned part: this is an
  * acceleration of the method's per-pose output.  The network is
  *   h_l = relu(h_{l-1} W_l^T + b_l) (l < L),  y = h_{L-1} W_L^T + b_L,
  * W_l stored [out][in]; BF16 weights and activations on the tensor cores

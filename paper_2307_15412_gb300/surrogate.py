@@ -1,5 +1,5 @@
 """Learned surrogate of the radar frame, with the ray tracer as its data
-source, fallback and judge.
+source, fallback and accuracy check.
 
   frames(raw)      range-Doppler cubes of parameter vectors from the tracer
                    (rr_batch_run over batches of seeded hand scenes)
