@@ -350,6 +350,14 @@ rr_status rr_backproject(rr_ctx *ctx, const float *s, const double *tx_pos, int 
 rr_status rr_max_projection(rr_ctx *ctx, const float *img, const rr_volume *vol, double dyn_range_db, float *db_out,
                             int32_t *z_out);
 
+/* out = x0 + alpha (x1 - x0) over n_complex complex values (float32 re, im;
+ * device arrays; out may alias neither input).  The echo amplitude is
+ * linear in Eq. 3's alpha and the path lengths do not depend on it, so the
+ * baseband and its back-projected volume are too: an alpha sweep (Sec.
+ * IV-B: alpha from 0 to 1 in steps of 0.1) computes alpha = 0 and 1 once
+ * and mixes them.  Errors: RR_EINVAL, RR_ECUDA. */
+rr_status rr_alpha_mix(rr_ctx *ctx, const float *x0, const float *x1, int64_t n_complex, double alpha, float *out);
+
 /* ---- whole frame --------------------------------------------------------- */
 
 /* One frame of the hot path on a scene already uploaded: build_bvh,

@@ -856,6 +856,18 @@ rr_status rr_backproject(rr_ctx *c, const float *s, const double *tx_pos, int n_
   return RR_OK;
 }
 
+rr_status rr_alpha_mix(rr_ctx *c, const float *x0, const float *x1, int64_t n_complex, double alpha, float *out) {
+  if (!c) return RR_EINVAL;
+  if (!x0 || !x1 || !out || n_complex < 0 || !isfinite(alpha)) return fail(c, RR_EINVAL, "alpha_mix: bad arguments");
+  if (n_complex == 0) return RR_OK;
+  DeviceGuard g(c->device);
+  rr::AlphaList al;
+  al.n = 1;
+  al.v[0] = (float)alpha;
+  RR_CUDA(c, rr::launch_alpha_mix(x0, x1, n_complex, al, out, c->stream), "alpha_mix launch");
+  return RR_OK;
+}
+
 rr_status rr_max_projection(rr_ctx *c, const float *img, const rr_volume *vol, double dyn_range_db, float *db_out,
                             int32_t *z_out) {
   if (!c) return RR_EINVAL;

@@ -446,6 +446,26 @@ def measure_imaging(args):
     ctx.sync()
     torch.cuda.synchronize()
     t = np.array([[e[k].elapsed_time(e[k + 1]) for k in range(3)] for e in evs]).mean(0)
+    # the alpha sweep of Sec. IV-B (alpha = 0, 0.1, ..., 1): alpha = 0 and 1
+    # imaged once, every alpha's volume their mix, then its projection
+    base1 = torch.empty_like(base)
+    img1 = torch.empty_like(img)
+    mix = torch.empty_like(img)
+    dbs = torch.empty((11, vol.ny, vol.nx), dtype=torch.float32, device="cuda")
+    flush.zero_()
+    es, ee = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    es.record(stream)
+    ctx.mimo_sfcw(0, grid, tx, rx, base, F0, DF, NF, alpha=0.0)
+    ctx.backproject(base, tx, rx, F0, DF, NF, vol, img)
+    ctx.mimo_sfcw(0, grid, tx, rx, base1, F0, DF, NF, alpha=1.0)
+    ctx.backproject(base1, tx, rx, F0, DF, NF, vol, img1)
+    for k in range(11):
+        ctx.alpha_mix(img, img1, k / 10.0, mix)
+        ctx.max_projection(mix, vol, 15.0, dbs[k])
+    ee.record(stream)
+    ctx.sync()
+    torch.cuda.synchronize()
+    t_sweep = es.elapsed_time(ee)
     pairs = len(tx) * len(rx)
     macs = float(vol.n) * pairs * NF
     fp32_peak = 152 * 128 * 2 * 2.07e9 / 1e12
@@ -459,7 +479,8 @@ def measure_imaging(args):
                                       "tflops_8_per_mac": achieved, "fp32_peak_tflops": fp32_peak,
                                       "frac": achieved / fp32_peak,
                                       "peak_source": "152 SMs x 128 FP32 lanes x 2 flop x 2070 MHz (max SM clock)"},
-                      "images_per_s": 1e3 / float(t.sum())}))
+                      "images_per_s": 1e3 / float(t.sum()),
+                      "alpha_sweep_11": {"ms": t_sweep, "ms_if_each_alpha_imaged": 11 * float(t.sum())}}))
     ctx.close()
 
 

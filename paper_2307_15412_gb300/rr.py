@@ -115,6 +115,7 @@ SIGNATURES = {
     "rr_mimo_sfcw": (_I, [_P, _I, _P, _P, _P, _I, _P, _I, _P]),
     "rr_backproject": (_I, [_P, _P, _P, _I, _P, _I, ctypes.c_double, ctypes.c_double, _I, _P, _P]),
     "rr_max_projection": (_I, [_P, _P, _P, ctypes.c_double, _P, _P]),
+    "rr_alpha_mix": (_I, [_P, _P, _P, ctypes.c_int64, ctypes.c_double, _P]),
     "rr_philox_words": (_I, [_P, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_int64, _P]),
     "rr_trace_frame": (_I, [_P, _I, ctypes.POINTER(rr_radar), ctypes.POINTER(rr_raygrid), _I64,
                             ctypes.POINTER(_I64)]),
@@ -380,6 +381,11 @@ class Context:
         self._check(self.lib.rr_backproject(self.h, _ptr(s), txa.ctypes.data, int(txa.shape[0]), rxa.ctypes.data,
                                             int(rxa.shape[0]), float(f0), float(df), int(n_f), ctypes.byref(vol),
                                             _ptr(img)))
+
+    def alpha_mix(self, x0, x1, alpha: float, out):
+        """out = x0 + alpha (x1 - x0) for complex float32 [..., 2] tensors."""
+        n = x0.numel() // 2
+        self._check(self.lib.rr_alpha_mix(self.h, _ptr(x0), _ptr(x1), int(n), float(alpha), _ptr(out)))
 
     def max_projection(self, img, volume, dyn_range_db: float, db_out, z_out=None):
         """Maximum projection along z in dB (Sec. IV-A): db_out float32

@@ -322,3 +322,30 @@ def test_max_projection_ties_and_zero_volume(ctx):
     ctx.sync()
     assert torch.all(db == -12.0)
     assert torch.count_nonzero(zi) == 0
+
+
+def test_alpha_sweep_by_mixing_images(ctx):
+    """The baseband and its image are linear in alpha (Eq. 3): the mix of
+    the alpha = 0 and 1 results equals the direct result at alpha = 0.3,
+    for the baseband and for the back-projected volume."""
+    s = I.hand_scene(9, 1500, center=(0.0, 0.0, I.IMAGING_RANGE))
+    tx_all, rx_all = I.mimo_square_array()
+    tx, rx = tx_all[::16], rx_all[::16]
+    grid = I.RayGrid(48, 48, math.radians(20.0), math.radians(20.0))
+    vol = I.Volume(-0.03, -0.03, 0.29, 3e-3, 3e-3, 4e-3, 21, 21, 9)
+    ctx.scene_upload(79, s.V, s.F, None)
+    ctx.build_bvh(79)
+    base, imgs = {}, {}
+    for al in (0.0, 1.0, 0.3):
+        base[al] = _buf(len(tx), len(rx), NF, 2)
+        ctx.mimo_sfcw(79, grid, tx, rx, base[al], F0, DF, NF, alpha=al)
+        imgs[al] = _buf(vol.nz, vol.ny, vol.nx, 2)
+        ctx.backproject(base[al], tx, rx, F0, DF, NF, vol, imgs[al])
+    mb = torch.empty_like(base[0.3])
+    mi = torch.empty_like(imgs[0.3])
+    ctx.alpha_mix(base[0.0], base[1.0], 0.3, mb)
+    ctx.alpha_mix(imgs[0.0], imgs[1.0], 0.3, mi)
+    ctx.sync()
+    assert np.linalg.norm(to_complex(base[0.0]) - to_complex(base[1.0])) > 0
+    assert rel_l2(to_complex(mb), to_complex(base[0.3])) <= 1e-5
+    assert rel_l2(to_complex(mi), to_complex(imgs[0.3])) <= 1e-5
